@@ -1,0 +1,221 @@
+/*
+ * pm.h -- C ABI of libpm, the B300 (sm_103a) implementation of the per-frame
+ * hot path of "Real-Time Polygonal Semantic Mapping for Humanoid Robot Stair
+ * Climbing" (arXiv 2411.01919):
+ *
+ *   depth image --(Sec. III-C, Eq. 1, Alg. 1)--> anisotropic diffusion
+ *               --(Sec. III-C, Eq. 2, Alg. 1)--> back-projection + normal image
+ *               --(Sec. III-D, Eq. 3, Alg. 2)--> sequential multi-plane RANSAC
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Images are row-major, pixel (u, v) = column u, row v, u in [0, w), v in [0, h).
+ * - Depth is camera-frame Z in metres.  A depth that is 0, negative or not
+ *   finite (u16: the value 0) is a hole.  Holes stay holes: diffusion neither
+ *   fills them nor conducts across them, and they yield no points.
+ * - "Device" pointers are CUDA device (or managed) memory on the current
+ *   device; "host" pointers are ordinary CPU memory.  The caller owns every
+ *   buffer it passes; the library owns only the scratch inside a pm_ctx.
+ * - Every call is asynchronous on `stream` (a cudaStream_t passed as void*,
+ *   NULL = the legacy default stream) unless it returns results in host
+ *   memory, in which case it synchronises `stream` before returning.
+ * - Errors: a bad argument returns PM_ERR_ARG before anything is launched; a
+ *   CUDA failure returns PM_ERR_CUDA; nothing aborts the process.  The text
+ *   of the last error of the calling thread is pm_last_error().
+ * - A pm_ctx is not thread-safe and must not be used from two host threads at
+ *   once; use one context per host thread or per stream.
+ */
+#ifndef PM_H
+#define PM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PM_OK = 0,
+    PM_ERR_ARG = 1,      /* invalid argument; nothing was launched */
+    PM_ERR_OOM = 2,      /* device or pinned-host allocation failed */
+    PM_ERR_CUDA = 3,     /* a CUDA call failed; see pm_last_error() */
+    PM_ERR_TIMEOUT = 4,  /* a bounded device-side wait expired */
+    PM_ERR_STATE = 5     /* call not valid in the context's current state */
+} pm_status;
+
+typedef enum {
+    PM_U16_MM = 0,       /* uint16 in units of depth_scale metres (sensor millimetres) */
+    PM_F16_M = 1,        /* IEEE binary16 metres (FP16 storage; computation is FP32) */
+    PM_F32_M = 2         /* IEEE binary32 metres */
+} pm_dtype;
+
+/* Pinhole intrinsics K (Alg. 1 and Alg. 2 "camera intrinsic matrix").
+ * A pixel (u, v) back-projects to z * ((u - cx)/fx, (v - cy)/fy, 1). */
+typedef struct {
+    double fx, fy, cx, cy;
+} pm_intrinsics;
+
+/* Alg. 1 parameters.  mode 0 (PM4) is the 4-neighbour discretisation of Eq. 1,
+ *   I'_p = I_p + lambda * sum_{q in N,S,W,E} g(I_q - I_p) (I_q - I_p),
+ *   g(x) = exp(-(x/K)^2);
+ * mode 1 (ALG1) is Alg. 1 read literally: one conductance per pixel from the
+ *   central-difference gradient magnitude times the 4-neighbour Laplacian.
+ * lambda (Alg. 1's gamma) must lie in (0, 0.25] (stability of the explicit
+ * scheme); K (Alg. 1's k) is in metres.  iters_per_launch is the temporal
+ * blocking depth (iterations fused in one launch); 0 lets the library choose. */
+typedef struct {
+    int iters;
+    float lambda;
+    float K;
+    int mode;
+    int iters_per_launch;
+} pm_diffusion_params;
+
+/* Alg. 2 parameters (whole-frame sequential form).  Each plane round draws
+ * `hypotheses` 3-point samples from Philox4x64-10 (key = (seed, 0), counter =
+ * (hypothesis, round, frame_idx, 0)), scores every hypothesis against every
+ * candidate point in FP32 (inlier: squared residual below thr_m^2), keeps the
+ * hypothesis with the most inliers (ties: lowest index), labels its inliers,
+ * refits the plane in FP64 by PCA over the inliers whose normal lies within
+ * refit_normal_gate_deg of the hypothesis normal, and repeats on the points
+ * not yet labelled.  It stops after max_planes planes or when the best
+ * hypothesis has fewer than min_inliers inliers (min_inliers >= 3).
+ * hypotheses must lie in [1, 2048]; max_planes in [1, 64]. */
+typedef struct {
+    int hypotheses;
+    float thr_m;
+    int max_planes;
+    int min_inliers;
+    unsigned long long seed;
+    float refit_normal_gate_deg;
+} pm_ransac_params;
+
+/* normal_stencil: 0 = central differences of back-projected points,
+ * 1 = the same differences with Sobel (1,2,1) weights (Alg. 1).
+ * depth_scale: metres per unit of PM_U16_MM input (0.001 for millimetres). */
+typedef struct {
+    int normal_stencil;
+    float depth_scale;
+} pm_misc_params;
+
+/* One extracted plane n . X + d = 0 in the camera frame, |n| = 1, oriented
+ * towards the camera (d > 0).  n_inliers: inliers of the winning hypothesis
+ * (these pixels carry the plane's label); n_refit: points used by the refit;
+ * rms: RMS distance of the refit points to the plane (metres); hyp_index:
+ * index of the winning hypothesis in its round. */
+typedef struct {
+    double n[3];
+    double d;
+    int n_inliers;
+    int n_refit;
+    float rms;
+    int hyp_index;
+} pm_plane;
+
+/* One frame of a batch (pm_process_batch).  depth: device pointer, `pitch`
+ * bytes between rows; labels: device int16 [h*w] or NULL (-1 = no plane,
+ * k = plane k); depth_out: device float [h*w] receiving the diffused depth, or
+ * NULL; iters: diffusion iterations for this frame (< 0: the context's). */
+typedef struct {
+    const void *depth;
+    int dtype;
+    int w, h;
+    int pitch;
+    pm_intrinsics K;
+    unsigned long long frame_idx;
+    int iters;
+    short *labels;
+    float *depth_out;
+} pm_frame;
+
+typedef struct pm_ctx pm_ctx;
+
+/* Create a context on the current CUDA device whose scratch holds up to
+ * `max_frames` frames of at most max_w x max_h pixels each.  The parameters
+ * are copied.  Returns PM_ERR_ARG for out-of-range parameters, PM_ERR_OOM if
+ * the scratch cannot be allocated.  *out is set only on success. */
+pm_status pm_create(const pm_diffusion_params *dp, const pm_ransac_params *rp,
+                    const pm_misc_params *mp, int max_w, int max_h, int max_frames,
+                    pm_ctx **out);
+
+/* Synchronise the context's work and free its scratch.  NULL is a no-op. */
+void pm_destroy(pm_ctx *ctx);
+
+/* Alg. 1, first loop (Eq. 1): decode `depth` (dtype, pitch in bytes, w x h)
+ * and run the context's diffusion for dp->iters iterations; write the FP32
+ * result (metres, holes = 0, row pitch w) to device `out`. */
+pm_status pm_diffuse(pm_ctx *ctx, const void *depth, int dtype, int w, int h, int pitch,
+                     float *out, void *stream);
+
+/* Alg. 1, second loop (Eq. 2) and Alg. 2 line 3: from FP32 device depth [h*w]
+ * compute points P = z K^-1 (u, v, 1) and unit normals (SoA, device float
+ * [3][h*w] each; holes get 0) and the validity byte per pixel (device
+ * uint8 [h*w]: bit 0 = point valid, bit 1 = normal valid).  Normals point
+ * towards the camera; they are invalid on the image border, next to a hole,
+ * or where the tangent cross product vanishes. */
+pm_status pm_normals(pm_ctx *ctx, const float *depth, int w, int h, const pm_intrinsics *K,
+                     float *points, float *normals, unsigned char *valid, void *stream);
+
+/* Alg. 2 (Eq. 3), whole frame: sequential RANSAC over the valid points of
+ * `points` (device SoA [3][h*w]) with `valid` (device [h*w], bits as above);
+ * `normals` (device SoA, or NULL: no refit gate).  Writes up to
+ * min(max_planes, rp->max_planes) planes to host `planes`, their number to
+ * host *n_planes, and, if `labels` is not NULL, the per-pixel plane index to
+ * device int16 labels [h*w] (-1 = none).  Synchronises `stream`. */
+pm_status pm_ransac_planes(pm_ctx *ctx, const float *points, const float *normals,
+                           const unsigned char *valid, int w, int h,
+                           unsigned long long frame_idx, pm_plane *planes, int max_planes,
+                           int *n_planes, short *labels, void *stream);
+
+/* The whole path for one frame on device input: decode, diffusion, normals,
+ * RANSAC.  Outputs as in pm_ransac_planes.  Synchronises `stream`. */
+pm_status pm_process_frame(pm_ctx *ctx, const void *depth, int dtype, int w, int h, int pitch,
+                           const pm_intrinsics *K, unsigned long long frame_idx,
+                           pm_plane *planes, int max_planes, int *n_planes, short *labels,
+                           void *stream);
+
+/* As pm_process_frame, with the depth and the labels (may be NULL) in HOST
+ * memory: the call copies the depth in and the planes and labels out on
+ * `stream`.  Synchronises `stream`. */
+pm_status pm_process_frame_host(pm_ctx *ctx, const void *depth_host, int dtype, int w, int h,
+                                int pitch, const pm_intrinsics *K, unsigned long long frame_idx,
+                                pm_plane *planes, int max_planes, int *n_planes,
+                                short *labels_host, void *stream);
+
+/* Batched form: the whole path for n frames of mixed sizes and iteration
+ * counts in one pass (shared launches; per-frame results identical to
+ * pm_process_frame).  planes: host [n * ctx max_planes]; n_planes: host [n].
+ * If use_graph is non-zero the launch sequence is captured once per batch
+ * shape and replayed as a CUDA graph.  Synchronises `stream`. */
+pm_status pm_process_batch(pm_ctx *ctx, const pm_frame *frames, int n, pm_plane *planes,
+                           int *n_planes, int use_graph, void *stream);
+
+/* Asynchronous batched form for request loops: enqueue the batch on `stream`
+ * and return; the planes land in the context's pinned host staging and are
+ * read with pm_batch_collect after `stream` (or the event recorded by the
+ * caller after this call) has completed.  A context holds one batch in flight. */
+pm_status pm_process_batch_async(pm_ctx *ctx, const pm_frame *frames, int n, int use_graph,
+                                 void *stream);
+pm_status pm_batch_collect(pm_ctx *ctx, pm_plane *planes, int *n_planes, int n);
+
+/* Device bytes of scratch a context created with these limits allocates. */
+long long pm_scratch_bytes(int max_w, int max_h, int max_frames, int hypotheses, int max_planes);
+
+/* Instrumentation.  pm_set_timing(ctx, 1): CUDA events between the stages of
+ * each call; pm_stage_times then returns the device time (ms) of the last
+ * call's [0] diffusion, [1] normals, [2] RANSAC.  pm_set_timing(ctx, 2):
+ * events around every scoring launch (captured into graphs too);
+ * pm_kernel_stats then returns the scoring kernels' summed device time (ms),
+ * the hypothesis-point pairs they scored and their launch count.  In every
+ * mode pm_kernel_stats returns in *launches the number of kernels the last
+ * call launched.  Any output pointer may be NULL. */
+pm_status pm_set_timing(pm_ctx *ctx, int on);
+pm_status pm_stage_times(pm_ctx *ctx, float ms[3]);
+pm_status pm_kernel_stats(pm_ctx *ctx, float *score_ms, long long *score_pairs,
+                          int *score_launches, long long *launches);
+
+/* Text of the calling thread's last error ("" if none). */
+const char *pm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PM_H */

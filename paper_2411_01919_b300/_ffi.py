@@ -1,0 +1,103 @@
+"""ctypes declarations of libpm's C ABI (include/pm.h).  Marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, 'libpm.so')
+
+PM_OK, PM_ERR_ARG, PM_ERR_OOM, PM_ERR_CUDA, PM_ERR_TIMEOUT, PM_ERR_STATE = range(6)
+STATUS = {0: 'PM_OK', 1: 'PM_ERR_ARG', 2: 'PM_ERR_OOM', 3: 'PM_ERR_CUDA', 4: 'PM_ERR_TIMEOUT',
+          5: 'PM_ERR_STATE'}
+PM_U16_MM, PM_F16_M, PM_F32_M = 0, 1, 2
+
+
+class Intrinsics(ctypes.Structure):
+    _fields_ = [('fx', ctypes.c_double), ('fy', ctypes.c_double),
+                ('cx', ctypes.c_double), ('cy', ctypes.c_double)]
+
+
+class DiffusionParams(ctypes.Structure):
+    _fields_ = [('iters', ctypes.c_int), ('lambda_', ctypes.c_float), ('K', ctypes.c_float),
+                ('mode', ctypes.c_int), ('iters_per_launch', ctypes.c_int)]
+
+
+class RansacParams(ctypes.Structure):
+    _fields_ = [('hypotheses', ctypes.c_int), ('thr_m', ctypes.c_float),
+                ('max_planes', ctypes.c_int), ('min_inliers', ctypes.c_int),
+                ('seed', ctypes.c_ulonglong), ('refit_normal_gate_deg', ctypes.c_float)]
+
+
+class MiscParams(ctypes.Structure):
+    _fields_ = [('normal_stencil', ctypes.c_int), ('depth_scale', ctypes.c_float)]
+
+
+class Plane(ctypes.Structure):
+    _fields_ = [('n', ctypes.c_double * 3), ('d', ctypes.c_double),
+                ('n_inliers', ctypes.c_int), ('n_refit', ctypes.c_int),
+                ('rms', ctypes.c_float), ('hyp_index', ctypes.c_int)]
+
+
+class Frame(ctypes.Structure):
+    _fields_ = [('depth', ctypes.c_void_p), ('dtype', ctypes.c_int), ('w', ctypes.c_int),
+                ('h', ctypes.c_int), ('pitch', ctypes.c_int), ('K', Intrinsics),
+                ('frame_idx', ctypes.c_ulonglong), ('iters', ctypes.c_int),
+                ('labels', ctypes.c_void_p), ('depth_out', ctypes.c_void_p)]
+
+
+EXPORTS = ['pm_create', 'pm_destroy', 'pm_diffuse', 'pm_normals', 'pm_ransac_planes',
+           'pm_process_frame', 'pm_process_frame_host', 'pm_process_batch',
+           'pm_process_batch_async', 'pm_batch_collect', 'pm_scratch_bytes', 'pm_set_timing',
+           'pm_stage_times', 'pm_kernel_stats', 'pm_last_error']
+
+_lib = None
+
+
+class PmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__('%s: %s' % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libpm.so.  Raises if the library is missing: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError('libpm.so not found at %s; build it with '
+                          '`python -m paper_2411_01919_b300.build`' % path)
+    L = ctypes.CDLL(path)
+    vp, i, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_ulonglong
+    P = ctypes.POINTER
+    sigs = {
+        'pm_create': ([P(DiffusionParams), P(RansacParams), P(MiscParams), i, i, i, P(vp)], i),
+        'pm_destroy': ([vp], None),
+        'pm_diffuse': ([vp, vp, i, i, i, i, vp, vp], i),
+        'pm_normals': ([vp, vp, i, i, P(Intrinsics), vp, vp, vp, vp], i),
+        'pm_ransac_planes': ([vp, vp, vp, vp, i, i, u64, P(Plane), i, P(i), vp, vp], i),
+        'pm_process_frame': ([vp, vp, i, i, i, i, P(Intrinsics), u64, P(Plane), i, P(i), vp, vp], i),
+        'pm_process_frame_host': ([vp, vp, i, i, i, i, P(Intrinsics), u64, P(Plane), i, P(i), vp,
+                                   vp], i),
+        'pm_process_batch': ([vp, P(Frame), i, P(Plane), P(i), i, vp], i),
+        'pm_process_batch_async': ([vp, P(Frame), i, i, vp], i),
+        'pm_batch_collect': ([vp, P(Plane), P(i), i], i),
+        'pm_scratch_bytes': ([i, i, i, i, i], ctypes.c_longlong),
+        'pm_set_timing': ([vp, i], i),
+        'pm_stage_times': ([vp, P(ctypes.c_float)], i),
+        'pm_kernel_stats': ([vp, P(ctypes.c_float), P(ctypes.c_longlong), P(i),
+                             P(ctypes.c_longlong)], i),
+        'pm_last_error': ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def check(status: int):
+    if status != PM_OK:
+        raise PmError(status, load().pm_last_error().decode(errors='replace'))

@@ -1,0 +1,247 @@
+// diffuse.cu -- anisotropic diffusion of the depth image (Sec. III-C, Eq. 1,
+// Alg. 1 first loop) for sm_103a.
+//
+// Numerics.  Where neighbouring depths differ by more than K/sqrt(2) the
+// Perona-Malik flux g(x) x decreases with |x| (backward diffusion), and a
+// rounding error of the iterate grows from one iteration to the next: a plain
+// FP32 iterate drifts 2e-5 m (640x480 staircase, 30 iterations) to 1.5e-4 m
+// (far spiral floor, 40 iterations) away from exact arithmetic.  The iterate
+// is therefore carried as a compensated pair of FP32 numbers (hi, lo) with
+// I = hi + lo: the u16 decode is split exactly (two-product), neighbour
+// differences include the lo parts, and the update I + lambda * s is added
+// with an error-free two-sum.  All arithmetic stays on the FP32 pipes.
+//
+// Two kernels share one per-pixel update (so their results are bit-identical):
+//  * k_diffuse_tiles: temporal blocking.  A CTA loads a (DX+2T) x (DY+2T) tile
+//    with a T-pixel halo into shared memory, runs T Jacobi iterations there on
+//    a shrinking region, and writes the DX x DY interior.  Tiles of every
+//    frame of a batch form one grid (a frame table maps tile -> frame).
+//  * k_diffuse_stream: one iteration per launch over one frame, one pass over
+//    HBM.
+// Holes and pixels outside the image are 0 in every buffer; the flux across a
+// link is 0 when either end is 0, which is the ghost rule J_q = I_p of the
+// oracle.  The first launch decodes the sensor encoding on the fly; the last
+// writes FP32 depth (the hi part, which is hi + lo rounded to nearest).
+#include "pm_internal.cuh"
+
+namespace pm {
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// q - p for two compensated values (exactly antisymmetric in p, q).
+__device__ __forceinline__ float pair_diff(float2 q, float2 p)
+{
+    return __fadd_rn(__fsub_rn(q.x, p.x), __fsub_rn(q.y, p.y));
+}
+
+// (hi, lo) + a, renormalised: two-sum of hi and a, the error folded into lo,
+// then a fast two-sum so that |lo| <= ulp(hi)/2.
+__device__ __forceinline__ float2 pair_add(float2 p, float a)
+{
+    const float s = __fadd_rn(p.x, a);
+    const float bb = __fsub_rn(s, p.x);
+    const float e = __fadd_rn(__fsub_rn(p.x, __fsub_rn(s, bb)), __fsub_rn(a, bb));
+    const float l = __fadd_rn(p.y, e);
+    const float h2 = __fadd_rn(s, l);
+    return make_float2(h2, __fsub_rn(l, __fsub_rn(h2, s)));
+}
+
+// Flux into p from neighbour q across one link: g(x) x with x = I_q - I_p and
+// g(x) = exp(-(x/K)^2) = 2^(x^2 * c), c = -log2(e)/K^2.  Exactly antisymmetric
+// in (p, q).  0 when q is a hole or outside the image.
+__device__ __forceinline__ float link_flux(float2 Ip, float2 Iq, float c)
+{
+    const float x = pair_diff(Iq, Ip);
+    const float g = ex2_approx(__fmul_rn(__fmul_rn(x, x), c));
+    const float f = __fmul_rn(g, x);
+    return (Iq.x == 0.0f) ? 0.0f : f;
+}
+
+// mode 0 (PM4): I' = I + lambda * (((f_N + f_S) + f_W) + f_E)
+__device__ __forceinline__ float2 update_pm4(float2 Ip, float2 In, float2 Is, float2 Iw,
+                                             float2 Ie, float lam, float c)
+{
+    if (Ip.x == 0.0f)
+        return make_float2(0.0f, 0.0f);
+    const float s = __fadd_rn(__fadd_rn(__fadd_rn(link_flux(Ip, In, c), link_flux(Ip, Is, c)),
+                                        link_flux(Ip, Iw, c)), link_flux(Ip, Ie, c));
+    return pair_add(Ip, __fmul_rn(lam, s));
+}
+
+// mode 1 (ALG1): c_p from the central-difference gradient of the ghosted
+// values, times the 4-neighbour Laplacian.
+__device__ __forceinline__ float2 update_alg1(float2 Ip, float2 In, float2 Is, float2 Iw,
+                                              float2 Ie, float lam, float c)
+{
+    if (Ip.x == 0.0f)
+        return make_float2(0.0f, 0.0f);
+    const float2 Jn = In.x == 0.0f ? Ip : In, Js = Is.x == 0.0f ? Ip : Is;
+    const float2 Jw = Iw.x == 0.0f ? Ip : Iw, Je = Ie.x == 0.0f ? Ip : Ie;
+    const float gx = __fmul_rn(pair_diff(Je, Jw), 0.5f);
+    const float gy = __fmul_rn(pair_diff(Js, Jn), 0.5f);
+    const float g2 = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
+    const float cp = ex2_approx(__fmul_rn(g2, c));
+    const float lap = __fadd_rn(__fadd_rn(__fadd_rn(pair_diff(Jn, Ip), pair_diff(Js, Ip)),
+                                          pair_diff(Jw, Ip)), pair_diff(Je, Ip));
+    return pair_add(Ip, __fmul_rn(__fmul_rn(lam, cp), lap));
+}
+
+template <int MODE>
+__device__ __forceinline__ float2 update(float2 Ip, float2 In, float2 Is, float2 Iw, float2 Ie,
+                                         float lam, float c)
+{
+    return MODE == 0 ? update_pm4(Ip, In, Is, Iw, Ie, lam, c)
+                     : update_alg1(Ip, In, Is, Iw, Ie, lam, c);
+}
+
+// Source pixel -> compensated metres; holes (0, negative, non-finite) -> 0.
+// u16: q * scale split exactly (q has at most 16 significant bits, so the
+// product fits in 40 bits and the fused multiply-add returns its exact tail).
+__device__ __forceinline__ float2 load_px(const void *src, int dtype, long long pitch, int x,
+                                          int y, float scale)
+{
+    const char *row = (const char *)src + (long long)y * pitch;
+    float v;
+    if (dtype == SRC_PAIR) {
+        return __ldg((const float2 *)row + x);
+    } else if (dtype == PM_U16_MM) {
+        const unsigned short q = __ldg((const unsigned short *)row + x);
+        if (!q)
+            return make_float2(0.0f, 0.0f);
+        const float qf = (float)q;
+        const float hi = __fmul_rn(qf, scale);
+        return make_float2(hi, __fmaf_rn(qf, scale, -hi));
+    } else if (dtype == PM_F16_M) {
+        v = __half2float(__ldg((const __half *)row + x));
+    } else {
+        v = __ldg((const float *)row + x);
+    }
+    return make_float2((v > 0.0f && v < __int_as_float(0x7f800000)) ? v : 0.0f, 0.0f);
+}
+
+__device__ __forceinline__ void store_px(const DiffFrame &f, long long i, float2 v)
+{
+    if (f.dst_pair)
+        reinterpret_cast<float2 *>(f.dst)[i] = v;
+    else
+        reinterpret_cast<float *>(f.dst)[i] = v.x;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restrict__ frames,
+                                                       int n_frames, int T, float lam, float c)
+{
+    extern __shared__ float2 sm2[];
+    const int tile = blockIdx.x;
+    int lo = 0, hi = n_frames - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (frames[mid].tile_begin <= tile)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const DiffFrame f = frames[lo];
+    const int tl = tile - f.tile_begin;
+    const int tx0 = (tl % f.tiles_x) * DX;
+    const int ty0 = (tl / f.tiles_x) * DY;
+    const int SX = DX + 2 * T, SY = DY + 2 * T;
+    float2 *A = sm2;
+    float2 *B = sm2 + SX * SY;
+
+    for (int i = threadIdx.x; i < SX * SY; i += blockDim.x) {
+        int sy = i / SX, sx = i - sy * SX;
+        int gx = tx0 - T + sx, gy = ty0 - T + sy;
+        float2 v = make_float2(0.0f, 0.0f);
+        if (gx >= 0 && gx < f.w && gy >= 0 && gy < f.h)
+            v = load_px(f.src, f.src_dtype, f.src_pitch, gx, gy, f.scale);
+        A[i] = v;
+    }
+    __syncthreads();
+    for (int it = 0; it < f.n_iters; ++it) {
+        const int r0 = it + 1;
+        const int RW = SX - 2 * r0, RH = SY - 2 * r0;
+        for (int i = threadIdx.x; i < RW * RH; i += blockDim.x) {
+            int ry = i / RW, rx = i - ry * RW;
+            int k = (ry + r0) * SX + rx + r0;
+            B[k] = update<MODE>(A[k], A[k - SX], A[k + SX], A[k - 1], A[k + 1], lam, c);
+        }
+        __syncthreads();
+        float2 *t = A; A = B; B = t;
+    }
+    for (int i = threadIdx.x; i < DX * DY; i += blockDim.x) {
+        int oy = i / DX, ox = i - oy * DX;
+        int gx = tx0 + ox, gy = ty0 + oy;
+        if (gx < f.w && gy < f.h)
+            store_px(f, (long long)gy * f.w + gx, A[(oy + T) * SX + ox + T]);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_diffuse_stream(DiffFrame f, float lam, float c)
+{
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= f.w || y >= f.h)
+        return;
+    const float2 Z = make_float2(0.0f, 0.0f);
+    const float2 Ip = load_px(f.src, f.src_dtype, f.src_pitch, x, y, f.scale);
+    const float2 In = y > 0 ? load_px(f.src, f.src_dtype, f.src_pitch, x, y - 1, f.scale) : Z;
+    const float2 Is = y + 1 < f.h ? load_px(f.src, f.src_dtype, f.src_pitch, x, y + 1, f.scale) : Z;
+    const float2 Iw = x > 0 ? load_px(f.src, f.src_dtype, f.src_pitch, x - 1, y, f.scale) : Z;
+    const float2 Ie = x + 1 < f.w ? load_px(f.src, f.src_dtype, f.src_pitch, x + 1, y, f.scale) : Z;
+    const float2 out = f.n_iters > 0 ? update<MODE>(Ip, In, Is, Iw, Ie, lam, c) : Ip;
+    store_px(f, (long long)y * f.w + x, out);
+}
+
+static inline float conductance_scale(float K)
+{
+    // exp(-(x/K)^2) = 2^(x^2 * c) with c = -log2(e) / K^2
+    return (float)(-1.4426950408889634 / ((double)K * (double)K));
+}
+
+size_t diffuse_tiles_smem(int T) { return 2ull * (DX + 2 * T) * (DY + 2 * T) * sizeof(float2); }
+
+cudaError_t diffuse_init()
+{
+    const int mx = (int)diffuse_tiles_smem(DT_MAX);
+    cudaError_t e = cudaFuncSetAttribute(k_diffuse_tiles<0>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_diffuse_tiles<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 mx);
+    return e;
+}
+
+cudaError_t launch_diffuse_tiles(const DiffFrame *d_frames, int n_frames, int total_tiles, int T,
+                                 float lambda, float K, int mode, cudaStream_t s)
+{
+    if (T < 0 || T > DT_MAX)
+        return cudaErrorInvalidValue;
+    const size_t smem = diffuse_tiles_smem(T);
+    const float c = conductance_scale(K);
+    if (mode == 0)
+        k_diffuse_tiles<0><<<total_tiles, 256, smem, s>>>(d_frames, n_frames, T, lambda, c);
+    else
+        k_diffuse_tiles<1><<<total_tiles, 256, smem, s>>>(d_frames, n_frames, T, lambda, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diffuse_stream(const DiffFrame &f, float lambda, float K, int mode,
+                                  cudaStream_t s)
+{
+    dim3 grid((f.w + 31) / 32, (f.h + 7) / 8);
+    const float c = conductance_scale(K);
+    if (mode == 0)
+        k_diffuse_stream<0><<<grid, dim3(32, 8), 0, s>>>(f, lambda, c);
+    else
+        k_diffuse_stream<1><<<grid, dim3(32, 8), 0, s>>>(f, lambda, c);
+    return cudaGetLastError();
+}
+
+}  // namespace pm

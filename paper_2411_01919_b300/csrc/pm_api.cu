@@ -1,0 +1,861 @@
+// pm_api.cu -- the C ABI of libpm (include/pm.h): contexts, argument checks,
+// scratch arena, launch orchestration, CUDA-graph capture of batches.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pm_internal.cuh"
+
+using namespace pm;
+
+namespace {
+
+thread_local std::string g_err;
+
+pm_status fail(pm_status s, const std::string &m)
+{
+    g_err = m;
+    return s;
+}
+
+#define PM_CK(call)                                                                            \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? PM_ERR_OOM : PM_ERR_CUDA,            \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int elem_size(int dtype) { return dtype == PM_F32_M ? 4 : 2; }
+
+// Layout of the device scratch arena: every region is 256-byte aligned.
+struct Layout {
+    size_t buf[2], depth, P, N, valid, labels, cidx[2], cpt[2], input;
+    size_t hyp, hyp_p0, counts, kept, keepbits, partial, state, planes, chunk_base;
+    size_t total;
+};
+
+Layout make_layout(long long npx, int frames, int H, int max_chunks)
+{
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t F = (size_t)frames, P = (size_t)npx;
+    L.buf[0] = take(F * P * 8);   // compensated iterate (float2)
+    L.buf[1] = take(F * P * 8);
+    L.depth = take(F * P * 4);
+    L.P = take(F * P * 12);
+    L.N = take(F * P * 12);
+    L.valid = take(F * P);
+    L.labels = take(F * P * 2);
+    L.cidx[0] = take(F * P * 4);
+    L.cidx[1] = take(F * P * 4);
+    L.cpt[0] = take(F * P * 16);
+    L.cpt[1] = take(F * P * 16);
+    L.input = take(F * P * 4);
+    L.hyp = take(F * H * 16);
+    L.hyp_p0 = take(F * H * 16);
+    L.counts = take(F * H * 4);
+    L.kept = take(F * max_chunks * 4);
+    L.keepbits = take(F * max_chunks * CHUNK_WORDS * 4);
+    L.partial = take(F * max_chunks * PART_WORDS * 4);
+    L.state = take(F * sizeof(RState));
+    L.planes = take(F * MAX_PLANES * sizeof(pm_plane));
+    L.chunk_base = take((F + 1) * 4);
+    L.total = off;
+    return L;
+}
+
+struct GraphEntry {
+    std::vector<long long> sig;
+    cudaGraphExec_t exec;
+    long long launches;   // kernels in the graph
+};
+
+}  // namespace
+
+struct pm_ctx {
+    pm_diffusion_params dp;
+    pm_ransac_params rp;
+    pm_misc_params mp;
+    int max_w, max_h, max_frames;
+    long long max_npx;
+    int max_chunks;
+    int sms;
+    int device;
+    Layout lay;
+    char *arena = nullptr;
+    char *d_tables = nullptr;
+    char *h_tables = nullptr;
+    size_t tables_cap = 0;
+    RState *h_state = nullptr;
+    pm_plane *h_planes = nullptr;
+    std::vector<GraphEntry> graphs;
+    int timing = 0;                       // 0 off, 1 stage events, 2 scoring-kernel events
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t kev[2 * MAX_PLANES] = {};
+    float stage_ms[3] = {0, 0, 0};
+    int pending_n = 0;
+    long long launches = 0;               // kernels launched by the last call
+    int last_n = 0;                       // frames of the last call
+
+    template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(arena + off); }
+};
+
+namespace {
+
+// A frame resolved against the context: pointers, sizes and iteration count.
+struct FrameJob {
+    const void *src;
+    int dtype, w, h;
+    long long pitch;
+    float fx, fy, cx, cy;
+    unsigned long long frame_idx;
+    int iters;
+    short *labels;
+    float *depth_out;
+};
+
+pm_status check_params(const pm_diffusion_params *dp, const pm_ransac_params *rp,
+                       const pm_misc_params *mp)
+{
+    if (!dp || !rp || !mp)
+        return fail(PM_ERR_ARG, "null parameter struct");
+    if (dp->iters < 0 || dp->iters > 100000)
+        return fail(PM_ERR_ARG, "diffusion iters out of range [0, 100000]");
+    if (!(dp->lambda > 0.0f) || dp->lambda > 0.25f)
+        return fail(PM_ERR_ARG, "diffusion lambda must lie in (0, 0.25]");
+    if (!(dp->K > 0.0f) || !std::isfinite(dp->K))
+        return fail(PM_ERR_ARG, "diffusion K must be positive");
+    if (dp->mode != 0 && dp->mode != 1)
+        return fail(PM_ERR_ARG, "diffusion mode must be 0 (PM4) or 1 (ALG1)");
+    if (dp->iters_per_launch < 0 || dp->iters_per_launch > DT_MAX)
+        return fail(PM_ERR_ARG, "iters_per_launch must lie in [0, 8]");
+    if (rp->hypotheses < 1 || rp->hypotheses > MAX_HYP)
+        return fail(PM_ERR_ARG, "hypotheses must lie in [1, 2048]");
+    if (!(rp->thr_m > 0.0f) || !std::isfinite(rp->thr_m))
+        return fail(PM_ERR_ARG, "thr_m must be positive");
+    if (rp->max_planes < 1 || rp->max_planes > MAX_PLANES)
+        return fail(PM_ERR_ARG, "max_planes must lie in [1, 64]");
+    if (rp->min_inliers < 3)
+        return fail(PM_ERR_ARG, "min_inliers must be >= 3");
+    if (!(rp->refit_normal_gate_deg >= 0.0f) || rp->refit_normal_gate_deg > 180.0f)
+        return fail(PM_ERR_ARG, "refit_normal_gate_deg must lie in [0, 180]");
+    if (mp->normal_stencil != 0 && mp->normal_stencil != 1)
+        return fail(PM_ERR_ARG, "normal_stencil must be 0 (central) or 1 (Sobel)");
+    if (!(mp->depth_scale > 0.0f) || !std::isfinite(mp->depth_scale))
+        return fail(PM_ERR_ARG, "depth_scale must be positive");
+    return PM_OK;
+}
+
+pm_status check_frame(const pm_ctx *ctx, const void *depth, int dtype, int w, int h,
+                      long long pitch, const pm_intrinsics *K)
+{
+    if (!depth)
+        return fail(PM_ERR_ARG, "null depth pointer");
+    if (dtype != PM_U16_MM && dtype != PM_F16_M && dtype != PM_F32_M)
+        return fail(PM_ERR_ARG, "unknown depth dtype");
+    if (w < 1 || h < 1)
+        return fail(PM_ERR_ARG, "image size must be at least 1x1");
+    if ((long long)w * h > ctx->max_npx)
+        return fail(PM_ERR_ARG, "image larger than the context's max_w * max_h");
+    if (pitch < (long long)w * elem_size(dtype) || pitch % elem_size(dtype) != 0)
+        return fail(PM_ERR_ARG, "pitch smaller than a row or not a multiple of the element size");
+    if (K && (!(K->fx > 0) || !(K->fy > 0) || !std::isfinite(K->fx) || !std::isfinite(K->fy) ||
+              !std::isfinite(K->cx) || !std::isfinite(K->cy)))
+        return fail(PM_ERR_ARG, "intrinsics must be finite with fx, fy > 0");
+    return PM_OK;
+}
+
+int choose_T(const pm_ctx *ctx) { return ctx->dp.iters_per_launch > 0 ? ctx->dp.iters_per_launch : DT_MAX; }
+
+pm_status ensure_tables(pm_ctx *ctx, size_t bytes)
+{
+    if (bytes <= ctx->tables_cap)
+        return PM_OK;
+    size_t cap = align_up(bytes * 2, 4096);
+    if (ctx->d_tables)
+        cudaFree(ctx->d_tables);
+    if (ctx->h_tables)
+        cudaFreeHost(ctx->h_tables);
+    ctx->d_tables = nullptr;
+    ctx->h_tables = nullptr;
+    ctx->tables_cap = 0;
+    PM_CK(cudaMalloc(&ctx->d_tables, cap));
+    PM_CK(cudaMallocHost(&ctx->h_tables, cap));
+    ctx->tables_cap = cap;
+    return PM_OK;
+}
+
+// What the launch sequence of a batch depends on (the graph cache key).
+std::vector<long long> signature(const std::vector<FrameJob> &jobs, int T, bool ransac)
+{
+    std::vector<long long> s;
+    s.push_back((long long)jobs.size());
+    s.push_back(T);
+    s.push_back(ransac ? 1 : 0);
+    for (const FrameJob &j : jobs) {
+        s.push_back(j.w);
+        s.push_back(j.h);
+        s.push_back(j.iters);
+    }
+    return s;
+}
+
+struct Plan {
+    size_t bytes = 0;
+    std::vector<size_t> diff_off;     // table offset of each diffusion launch
+    std::vector<int> diff_n, diff_tiles;
+    size_t norm_off = 0, rframe_off = 0;
+    int max_w = 0, max_h = 0;
+    long long total_chunks = 0;
+};
+
+// Fill the pinned host tables for a batch (descriptor contents only; the
+// launch sequence depends on the signature alone).
+Plan build_tables(pm_ctx *ctx, const std::vector<FrameJob> &jobs, int T, bool ransac,
+                  bool write)
+{
+    Plan pl;
+    const int n = (int)jobs.size();
+    std::vector<int> L(n);
+    int Lmax = 0;
+    for (int f = 0; f < n; ++f) {
+        L[f] = jobs[f].iters == 0 ? 1 : (jobs[f].iters + T - 1) / T;
+        Lmax = L[f] > Lmax ? L[f] : Lmax;
+        pl.max_w = jobs[f].w > pl.max_w ? jobs[f].w : pl.max_w;
+        pl.max_h = jobs[f].h > pl.max_h ? jobs[f].h : pl.max_h;
+        pl.total_chunks += ((long long)jobs[f].w * jobs[f].h + CHUNK - 1) / CHUNK;
+    }
+    size_t off = 0;
+    for (int k = 0; k < Lmax; ++k) {
+        DiffFrame *tab = reinterpret_cast<DiffFrame *>(ctx->h_tables + off);
+        pl.diff_off.push_back(off);
+        int cnt = 0, tiles = 0;
+        for (int f = 0; f < n; ++f) {
+            if (k >= L[f])
+                continue;
+            const FrameJob &j = jobs[f];
+            const long long slot = (long long)f * ctx->max_npx;
+            const int tx = (j.w + DX - 1) / DX, ty = (j.h + DY - 1) / DY;
+            if (write) {
+                DiffFrame d;
+                const bool first = k == 0, lastk = k == L[f] - 1;
+                d.src = first ? j.src : (const void *)(ctx->at<float2>(ctx->lay.buf[(k - 1) & 1]) + slot);
+                d.src_dtype = first ? j.dtype : SRC_PAIR;
+                d.src_pitch = first ? j.pitch : (long long)j.w * 8;
+                d.w = j.w;
+                d.h = j.h;
+                d.dst = lastk ? (void *)j.depth_out : (void *)(ctx->at<float2>(ctx->lay.buf[k & 1]) + slot);
+                d.dst_pair = lastk ? 0 : 1;
+                int rem = j.iters - k * T;
+                d.n_iters = rem < T ? (rem > 0 ? rem : 0) : T;
+                d.tiles_x = tx;
+                d.tile_begin = tiles;
+                d.scale = ctx->mp.depth_scale;
+                tab[cnt] = d;
+            }
+            tiles += tx * ty;
+            ++cnt;
+        }
+        pl.diff_n.push_back(cnt);
+        pl.diff_tiles.push_back(tiles);
+        off += align_up(cnt * sizeof(DiffFrame), 256);
+    }
+    pl.norm_off = off;
+    if (write) {
+        NormFrame *nt = reinterpret_cast<NormFrame *>(ctx->h_tables + off);
+        for (int f = 0; f < n; ++f) {
+            const FrameJob &j = jobs[f];
+            const long long slot = (long long)f * ctx->max_npx;
+            nt[f] = NormFrame{j.depth_out, ctx->at<float>(ctx->lay.P) + 3 * slot,
+                              ctx->at<float>(ctx->lay.N) + 3 * slot,
+                              ctx->at<unsigned char>(ctx->lay.valid) + slot, j.w, j.h,
+                              j.fx, j.fy, j.cx, j.cy};
+        }
+    }
+    off += align_up(n * sizeof(NormFrame), 256);
+    pl.rframe_off = off;
+    if (write && ransac) {
+        RFrame *rt = reinterpret_cast<RFrame *>(ctx->h_tables + off);
+        for (int f = 0; f < n; ++f) {
+            const FrameJob &j = jobs[f];
+            const long long slot = (long long)f * ctx->max_npx;
+            const Layout &Ly = ctx->lay;
+            RFrame r;
+            r.P = ctx->at<float>(Ly.P) + 3 * slot;
+            r.N = ctx->at<float>(Ly.N) + 3 * slot;
+            r.valid = ctx->at<unsigned char>(Ly.valid) + slot;
+            r.labels = j.labels;
+            r.w = j.w;
+            r.h = j.h;
+            r.npx = j.w * j.h;
+            r.frame_idx = j.frame_idx;
+            for (int b = 0; b < 2; ++b) {
+                r.cidx[b] = ctx->at<int>(Ly.cidx[b]) + slot;
+                r.cpt[b] = ctx->at<float4>(Ly.cpt[b]) + slot;
+            }
+            r.hyp = ctx->at<float4>(Ly.hyp) + (size_t)f * ctx->rp.hypotheses;
+            r.hyp_p0 = ctx->at<float4>(Ly.hyp_p0) + (size_t)f * ctx->rp.hypotheses;
+            r.counts = ctx->at<int>(Ly.counts) + (size_t)f * ctx->rp.hypotheses;
+            r.kept = ctx->at<int>(Ly.kept) + (size_t)f * ctx->max_chunks;
+            r.keepbits = ctx->at<unsigned>(Ly.keepbits) + (size_t)f * ctx->max_chunks * CHUNK_WORDS;
+            r.partial = ctx->at<float>(Ly.partial) + (size_t)f * ctx->max_chunks * PART_WORDS;
+            r.st = ctx->at<RState>(Ly.state) + f;
+            r.planes = ctx->at<pm_plane>(Ly.planes) + (size_t)f * MAX_PLANES;
+            rt[f] = r;
+        }
+    }
+    off += align_up(n * sizeof(RFrame), 256);
+    pl.bytes = off;
+    return pl;
+}
+
+RParams ransac_params(const pm_ctx *ctx)
+{
+    RParams p;
+    p.H = ctx->rp.hypotheses;
+    p.thr2 = ctx->rp.thr_m * ctx->rp.thr_m;
+    p.max_planes = ctx->rp.max_planes;
+    p.min_inliers = ctx->rp.min_inliers;
+    p.seed = ctx->rp.seed;
+    p.cos_gate = (float)std::cos((double)ctx->rp.refit_normal_gate_deg * M_PI / 180.0);
+    return p;
+}
+
+// Enqueue the RANSAC rounds for n frames whose RFrame table is at d_rframes.
+pm_status enqueue_ransac(pm_ctx *ctx, RFrame *d_rframes, int n, long long total_chunks,
+                         cudaStream_t s)
+{
+    RansacLaunch L;
+    L.d_frames = d_rframes;
+    L.n = n;
+    L.d_chunk_base = ctx->at<int>(ctx->lay.chunk_base);
+    L.max_total_chunks = (int)total_chunks;
+    L.prm = ransac_params(ctx);
+    long long sb = (long long)ctx->sms * 8, cb = (long long)ctx->sms * 4;
+    L.score_blocks = (int)(total_chunks < sb ? total_chunks : sb);
+    L.chunk_blocks = (int)(total_chunks < cb ? total_chunks : cb);
+    if (L.score_blocks < 1)
+        L.score_blocks = 1;
+    if (L.chunk_blocks < 1)
+        L.chunk_blocks = 1;
+    PM_CK(ransac_init(L, s));
+    ctx->launches += RANSAC_INIT_LAUNCHES;
+    for (int r = 0; r < ctx->rp.max_planes; ++r) {
+        const bool last = r + 1 == ctx->rp.max_planes;
+        cudaEvent_t a = ctx->timing == 2 ? ctx->kev[2 * r] : nullptr;
+        cudaEvent_t b = ctx->timing == 2 ? ctx->kev[2 * r + 1] : nullptr;
+        PM_CK(ransac_round(L, r, last, s, a, b));
+        ctx->launches += RANSAC_ROUND_LAUNCHES - (last ? 1 : 0);
+    }
+    return PM_OK;
+}
+
+// The launch sequence of a batch after its tables are written: upload,
+// diffusion, normals, RANSAC, result download.
+pm_status enqueue_batch(pm_ctx *ctx, const Plan &pl, int n, int T, bool ransac, bool timed,
+                        cudaStream_t s)
+{
+    PM_CK(cudaMemcpyAsync(ctx->d_tables, ctx->h_tables, pl.bytes, cudaMemcpyHostToDevice, s));
+    if (timed)
+        PM_CK(cudaEventRecord(ctx->ev[0], s));
+    for (size_t k = 0; k < pl.diff_off.size(); ++k) {
+        if (pl.diff_n[k] == 0)
+            continue;
+        int Tk = T;
+        PM_CK(launch_diffuse_tiles(reinterpret_cast<const DiffFrame *>(ctx->d_tables + pl.diff_off[k]),
+                                   pl.diff_n[k], pl.diff_tiles[k], Tk, ctx->dp.lambda, ctx->dp.K,
+                                   ctx->dp.mode, s));
+        ctx->launches += 1;
+    }
+    if (timed)
+        PM_CK(cudaEventRecord(ctx->ev[1], s));
+    if (!ransac)
+        return PM_OK;
+    PM_CK(launch_normals_batch(ctx->d_tables + pl.norm_off, n, pl.max_w, pl.max_h,
+                               ctx->mp.normal_stencil, s));
+    ctx->launches += 1;
+    if (timed)
+        PM_CK(cudaEventRecord(ctx->ev[2], s));
+    pm_status st = enqueue_ransac(ctx, reinterpret_cast<RFrame *>(ctx->d_tables + pl.rframe_off),
+                                  n, pl.total_chunks, s);
+    if (st != PM_OK)
+        return st;
+    if (timed)
+        PM_CK(cudaEventRecord(ctx->ev[3], s));
+    PM_CK(cudaMemcpyAsync(ctx->h_state, ctx->at<RState>(ctx->lay.state), n * sizeof(RState),
+                          cudaMemcpyDeviceToHost, s));
+    PM_CK(cudaMemcpyAsync(ctx->h_planes, ctx->at<pm_plane>(ctx->lay.planes),
+                          (size_t)n * MAX_PLANES * sizeof(pm_plane), cudaMemcpyDeviceToHost, s));
+    return PM_OK;
+}
+
+pm_status run_batch(pm_ctx *ctx, std::vector<FrameJob> &jobs, bool ransac, bool use_graph,
+                    cudaStream_t s)
+{
+    const int n = (int)jobs.size();
+    if (ctx->pending_n)
+        return fail(PM_ERR_STATE, "an asynchronous batch is still pending on this context");
+    const int T = choose_T(ctx);
+    for (int f = 0; f < n; ++f) {
+        const long long slot = (long long)f * ctx->max_npx;
+        if (!jobs[f].depth_out)
+            jobs[f].depth_out = ctx->at<float>(ctx->lay.depth) + slot;
+        if (!jobs[f].labels)
+            jobs[f].labels = ctx->at<short>(ctx->lay.labels) + slot;
+    }
+    ctx->launches = 0;
+    ctx->last_n = n;
+    Plan pl = build_tables(ctx, jobs, T, ransac, false);
+    pm_status st = ensure_tables(ctx, pl.bytes);
+    if (st != PM_OK)
+        return st;
+    build_tables(ctx, jobs, T, ransac, true);
+    if (use_graph && s != nullptr) {
+        std::vector<long long> sig = signature(jobs, T, ransac);
+        sig.push_back(ctx->timing);
+        cudaGraphExec_t exec = nullptr;
+        long long glaunch = 0;
+        for (GraphEntry &g : ctx->graphs)
+            if (g.sig == sig) {
+                exec = g.exec;
+                glaunch = g.launches;
+            }
+        if (!exec) {
+            PM_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            st = enqueue_batch(ctx, pl, n, T, ransac, ctx->timing == 1, s);
+            glaunch = ctx->launches;
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(s, &graph);
+            if (st != PM_OK) {
+                if (graph)
+                    cudaGraphDestroy(graph);
+                return st;
+            }
+            PM_CK(e);
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            PM_CK(e);
+            if (ctx->graphs.size() >= 16) {
+                cudaGraphExecDestroy(ctx->graphs.front().exec);
+                ctx->graphs.erase(ctx->graphs.begin());
+            }
+            ctx->graphs.push_back(GraphEntry{sig, exec, glaunch});
+        }
+        PM_CK(cudaGraphLaunch(exec, s));
+        ctx->launches = glaunch;
+        return PM_OK;
+    }
+    return enqueue_batch(ctx, pl, n, T, ransac, ctx->timing == 1, s);
+}
+
+pm_status finish_timing(pm_ctx *ctx, bool ransac)
+{
+    if (ctx->timing != 1)
+        return PM_OK;
+    PM_CK(cudaEventElapsedTime(&ctx->stage_ms[0], ctx->ev[0], ctx->ev[1]));
+    if (ransac) {
+        PM_CK(cudaEventElapsedTime(&ctx->stage_ms[1], ctx->ev[1], ctx->ev[2]));
+        PM_CK(cudaEventElapsedTime(&ctx->stage_ms[2], ctx->ev[2], ctx->ev[3]));
+    }
+    return PM_OK;
+}
+
+pm_status copy_planes(pm_ctx *ctx, int f, pm_plane *planes, int max_planes, int *n_planes)
+{
+    int np = ctx->h_state[f].n_planes;
+    if (np < 0 || np > MAX_PLANES)
+        return fail(PM_ERR_CUDA, "corrupt plane count read back from the device");
+    int k = np < max_planes ? np : max_planes;
+    if (planes && k > 0)
+        std::memcpy(planes, ctx->h_planes + (size_t)f * MAX_PLANES, k * sizeof(pm_plane));
+    if (n_planes)
+        *n_planes = k;
+    return PM_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// exported entry points
+// ===========================================================================
+extern "C" {
+
+long long pm_scratch_bytes(int max_w, int max_h, int max_frames, int hypotheses, int max_planes)
+{
+    (void)max_planes;
+    if (max_w < 1 || max_h < 1 || max_frames < 1 || hypotheses < 1)
+        return -1;
+    long long npx = (long long)max_w * max_h;
+    int max_chunks = (int)((npx + CHUNK - 1) / CHUNK);
+    return (long long)make_layout(npx, max_frames, hypotheses, max_chunks).total;
+}
+
+pm_status pm_create(const pm_diffusion_params *dp, const pm_ransac_params *rp,
+                    const pm_misc_params *mp, int max_w, int max_h, int max_frames, pm_ctx **out)
+{
+    if (!out)
+        return fail(PM_ERR_ARG, "null output pointer");
+    pm_status st = check_params(dp, rp, mp);
+    if (st != PM_OK)
+        return st;
+    if (max_w < 1 || max_h < 1 || max_frames < 1 || max_frames > 1024)
+        return fail(PM_ERR_ARG, "max_w, max_h >= 1 and max_frames in [1, 1024] required");
+    if ((long long)max_w * max_h >= (1ll << 31) / 2)
+        return fail(PM_ERR_ARG, "max_w * max_h too large for 32-bit pixel indices");
+    pm_ctx *ctx = new pm_ctx();
+    ctx->dp = *dp;
+    ctx->rp = *rp;
+    ctx->mp = *mp;
+    ctx->max_w = max_w;
+    ctx->max_h = max_h;
+    ctx->max_frames = max_frames;
+    ctx->max_npx = (long long)max_w * max_h;
+    ctx->max_chunks = (int)((ctx->max_npx + CHUNK - 1) / CHUNK);
+    ctx->lay = make_layout(ctx->max_npx, max_frames, rp->hypotheses, ctx->max_chunks);
+    auto bail = [&](pm_status s) {
+        pm_destroy(ctx);
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess)
+        e = diffuse_init();
+    if (e != cudaSuccess)
+        return bail(fail(PM_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e)));
+    e = cudaMalloc(&ctx->arena, ctx->lay.total);
+    if (e != cudaSuccess) {
+        ctx->arena = nullptr;
+        cudaGetLastError();
+        return bail(fail(PM_ERR_OOM, "scratch arena of " + std::to_string(ctx->lay.total) +
+                                         " bytes: " + cudaGetErrorString(e)));
+    }
+    e = cudaMallocHost(&ctx->h_state, max_frames * sizeof(RState));
+    if (e == cudaSuccess)
+        e = cudaMallocHost(&ctx->h_planes, (size_t)max_frames * MAX_PLANES * sizeof(pm_plane));
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+        e = cudaEventCreate(&ctx->ev[i]);
+    for (int i = 0; i < 2 * MAX_PLANES && e == cudaSuccess; ++i)
+        e = cudaEventCreate(&ctx->kev[i]);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(PM_ERR_OOM, std::string("pinned host staging: ") + cudaGetErrorString(e)));
+    }
+    st = ensure_tables(ctx, 64 * 1024);
+    if (st != PM_OK)
+        return bail(st);
+    *out = ctx;
+    return PM_OK;
+}
+
+void pm_destroy(pm_ctx *ctx)
+{
+    if (!ctx)
+        return;
+    cudaDeviceSynchronize();
+    for (GraphEntry &g : ctx->graphs)
+        cudaGraphExecDestroy(g.exec);
+    for (int i = 0; i < 4; ++i)
+        if (ctx->ev[i])
+            cudaEventDestroy(ctx->ev[i]);
+    for (int i = 0; i < 2 * MAX_PLANES; ++i)
+        if (ctx->kev[i])
+            cudaEventDestroy(ctx->kev[i]);
+    if (ctx->arena)
+        cudaFree(ctx->arena);
+    if (ctx->d_tables)
+        cudaFree(ctx->d_tables);
+    if (ctx->h_tables)
+        cudaFreeHost(ctx->h_tables);
+    if (ctx->h_state)
+        cudaFreeHost(ctx->h_state);
+    if (ctx->h_planes)
+        cudaFreeHost(ctx->h_planes);
+    delete ctx;
+}
+
+pm_status pm_diffuse(pm_ctx *ctx, const void *depth, int dtype, int w, int h, int pitch,
+                     float *out, void *stream)
+{
+    if (!ctx || !out)
+        return fail(PM_ERR_ARG, "null context or output");
+    pm_status st = check_frame(ctx, depth, dtype, w, h, pitch, nullptr);
+    if (st != PM_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->dp.iters_per_launch == 1) {
+        // one iteration per launch: the streaming kernel, ping-pong in scratch
+        const int it = ctx->dp.iters;
+        const long long npx = (long long)w * h;
+        for (int k = 0; k < (it > 0 ? it : 1); ++k) {
+            DiffFrame d{};
+            const bool lastk = k == (it > 0 ? it : 1) - 1;
+            d.src = k == 0 ? depth : (const void *)(ctx->at<float2>(ctx->lay.buf[(k - 1) & 1]));
+            d.src_dtype = k == 0 ? dtype : SRC_PAIR;
+            d.src_pitch = k == 0 ? pitch : (long long)w * 8;
+            d.w = w;
+            d.h = h;
+            d.dst = lastk ? (void *)out : (void *)ctx->at<float2>(ctx->lay.buf[k & 1]);
+            d.dst_pair = lastk ? 0 : 1;
+            d.n_iters = it > 0 ? 1 : 0;
+            d.scale = ctx->mp.depth_scale;
+            (void)npx;
+            PM_CK(launch_diffuse_stream(d, ctx->dp.lambda, ctx->dp.K, ctx->dp.mode, s));
+        }
+        return PM_OK;
+    }
+    std::vector<FrameJob> jobs(1);
+    jobs[0] = FrameJob{depth, dtype, w, h, pitch, 1, 1, 0, 0, 0, ctx->dp.iters, nullptr, out};
+    return run_batch(ctx, jobs, false, false, s);
+}
+
+pm_status pm_normals(pm_ctx *ctx, const float *depth, int w, int h, const pm_intrinsics *K,
+                     float *points, float *normals, unsigned char *valid, void *stream)
+{
+    if (!ctx || !K || !points || !normals || !valid)
+        return fail(PM_ERR_ARG, "null argument");
+    pm_status st = check_frame(ctx, depth, PM_F32_M, w, h, (long long)w * 4, K);
+    if (st != PM_OK)
+        return st;
+    PM_CK(launch_normals(depth, w, h, (float)K->fx, (float)K->fy, (float)K->cx, (float)K->cy,
+                         ctx->mp.normal_stencil, points, normals, valid, (cudaStream_t)stream));
+    return PM_OK;
+}
+
+pm_status pm_ransac_planes(pm_ctx *ctx, const float *points, const float *normals,
+                           const unsigned char *valid, int w, int h, unsigned long long frame_idx,
+                           pm_plane *planes, int max_planes, int *n_planes, short *labels,
+                           void *stream)
+{
+    if (!ctx || !points || !valid || !planes || !n_planes || max_planes < 0)
+        return fail(PM_ERR_ARG, "null argument");
+    if (w < 1 || h < 1 || (long long)w * h > ctx->max_npx)
+        return fail(PM_ERR_ARG, "image size out of range for this context");
+    if (ctx->pending_n)
+        return fail(PM_ERR_STATE, "an asynchronous batch is still pending on this context");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Layout &Ly = ctx->lay;
+    RFrame r;
+    r.P = points;
+    r.N = normals;
+    r.valid = valid;
+    r.labels = labels ? labels : ctx->at<short>(Ly.labels);
+    r.w = w;
+    r.h = h;
+    r.npx = w * h;
+    r.frame_idx = frame_idx;
+    for (int b = 0; b < 2; ++b) {
+        r.cidx[b] = ctx->at<int>(Ly.cidx[b]);
+        r.cpt[b] = ctx->at<float4>(Ly.cpt[b]);
+    }
+    r.hyp = ctx->at<float4>(Ly.hyp);
+    r.hyp_p0 = ctx->at<float4>(Ly.hyp_p0);
+    r.counts = ctx->at<int>(Ly.counts);
+    r.kept = ctx->at<int>(Ly.kept);
+    r.keepbits = ctx->at<unsigned>(Ly.keepbits);
+    r.partial = ctx->at<float>(Ly.partial);
+    r.st = ctx->at<RState>(Ly.state);
+    r.planes = ctx->at<pm_plane>(Ly.planes);
+    std::memcpy(ctx->h_tables, &r, sizeof(RFrame));
+    ctx->launches = 0;
+    ctx->last_n = 1;
+    PM_CK(cudaMemcpyAsync(ctx->d_tables, ctx->h_tables, sizeof(RFrame), cudaMemcpyHostToDevice, s));
+    pm_status st = enqueue_ransac(ctx, reinterpret_cast<RFrame *>(ctx->d_tables), 1,
+                                  ((long long)w * h + CHUNK - 1) / CHUNK, s);
+    if (st != PM_OK)
+        return st;
+    PM_CK(cudaMemcpyAsync(ctx->h_state, ctx->at<RState>(Ly.state), sizeof(RState),
+                          cudaMemcpyDeviceToHost, s));
+    PM_CK(cudaMemcpyAsync(ctx->h_planes, ctx->at<pm_plane>(Ly.planes), MAX_PLANES * sizeof(pm_plane),
+                          cudaMemcpyDeviceToHost, s));
+    PM_CK(cudaStreamSynchronize(s));
+    return copy_planes(ctx, 0, planes, max_planes, n_planes);
+}
+
+pm_status pm_process_frame(pm_ctx *ctx, const void *depth, int dtype, int w, int h, int pitch,
+                           const pm_intrinsics *K, unsigned long long frame_idx, pm_plane *planes,
+                           int max_planes, int *n_planes, short *labels, void *stream)
+{
+    if (!ctx || !K || !planes || !n_planes || max_planes < 0)
+        return fail(PM_ERR_ARG, "null argument");
+    pm_status st = check_frame(ctx, depth, dtype, w, h, pitch, K);
+    if (st != PM_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<FrameJob> jobs(1);
+    jobs[0] = FrameJob{depth, dtype, w, h, pitch, (float)K->fx, (float)K->fy, (float)K->cx,
+                       (float)K->cy, frame_idx, ctx->dp.iters, labels, nullptr};
+    st = run_batch(ctx, jobs, true, false, s);
+    if (st != PM_OK)
+        return st;
+    PM_CK(cudaStreamSynchronize(s));
+    st = finish_timing(ctx, true);
+    if (st != PM_OK)
+        return st;
+    return copy_planes(ctx, 0, planes, max_planes, n_planes);
+}
+
+pm_status pm_process_frame_host(pm_ctx *ctx, const void *depth_host, int dtype, int w, int h,
+                                int pitch, const pm_intrinsics *K, unsigned long long frame_idx,
+                                pm_plane *planes, int max_planes, int *n_planes,
+                                short *labels_host, void *stream)
+{
+    if (!ctx || !K || !planes || !n_planes || max_planes < 0)
+        return fail(PM_ERR_ARG, "null argument");
+    pm_status st = check_frame(ctx, depth_host, dtype, w, h, pitch, K);
+    if (st != PM_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int es = elem_size(dtype);
+    void *d_in = ctx->at<char>(ctx->lay.input);
+    PM_CK(cudaMemcpy2DAsync(d_in, (size_t)w * es, depth_host, pitch, (size_t)w * es, h,
+                            cudaMemcpyHostToDevice, s));
+    short *d_lab = ctx->at<short>(ctx->lay.labels);
+    std::vector<FrameJob> jobs(1);
+    jobs[0] = FrameJob{d_in, dtype, w, h, (long long)w * es, (float)K->fx, (float)K->fy,
+                       (float)K->cx, (float)K->cy, frame_idx, ctx->dp.iters, d_lab, nullptr};
+    st = run_batch(ctx, jobs, true, false, s);
+    if (st != PM_OK)
+        return st;
+    if (labels_host)
+        PM_CK(cudaMemcpyAsync(labels_host, d_lab, (size_t)w * h * 2, cudaMemcpyDeviceToHost, s));
+    PM_CK(cudaStreamSynchronize(s));
+    return copy_planes(ctx, 0, planes, max_planes, n_planes);
+}
+
+static pm_status batch_jobs(pm_ctx *ctx, const pm_frame *frames, int n,
+                            std::vector<FrameJob> &jobs)
+{
+    if (!ctx || !frames || n < 1)
+        return fail(PM_ERR_ARG, "null context/frames or empty batch");
+    if (n > ctx->max_frames)
+        return fail(PM_ERR_ARG, "batch larger than the context's max_frames");
+    jobs.resize(n);
+    for (int f = 0; f < n; ++f) {
+        const pm_frame &fr = frames[f];
+        pm_status st = check_frame(ctx, fr.depth, fr.dtype, fr.w, fr.h, fr.pitch, &fr.K);
+        if (st != PM_OK)
+            return fail(st, "frame " + std::to_string(f) + ": " + g_err);
+        const int it = fr.iters < 0 ? ctx->dp.iters : fr.iters;
+        if (it > 100000)
+            return fail(PM_ERR_ARG, "frame " + std::to_string(f) + ": iters out of range");
+        jobs[f] = FrameJob{fr.depth, fr.dtype, fr.w, fr.h, fr.pitch, (float)fr.K.fx, (float)fr.K.fy,
+                           (float)fr.K.cx, (float)fr.K.cy, fr.frame_idx, it, fr.labels,
+                           fr.depth_out};
+    }
+    return PM_OK;
+}
+
+pm_status pm_process_batch(pm_ctx *ctx, const pm_frame *frames, int n, pm_plane *planes,
+                           int *n_planes, int use_graph, void *stream)
+{
+    if (!planes || !n_planes)
+        return fail(PM_ERR_ARG, "null output");
+    std::vector<FrameJob> jobs;
+    pm_status st = batch_jobs(ctx, frames, n, jobs);
+    if (st != PM_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = run_batch(ctx, jobs, true, use_graph != 0, s);
+    if (st != PM_OK)
+        return st;
+    PM_CK(cudaStreamSynchronize(s));
+    st = finish_timing(ctx, true);
+    if (st != PM_OK)
+        return st;
+    for (int f = 0; f < n; ++f) {
+        st = copy_planes(ctx, f, planes + (size_t)f * ctx->rp.max_planes, ctx->rp.max_planes,
+                         n_planes + f);
+        if (st != PM_OK)
+            return st;
+    }
+    return PM_OK;
+}
+
+pm_status pm_process_batch_async(pm_ctx *ctx, const pm_frame *frames, int n, int use_graph,
+                                 void *stream)
+{
+    std::vector<FrameJob> jobs;
+    pm_status st = batch_jobs(ctx, frames, n, jobs);
+    if (st != PM_OK)
+        return st;
+    st = run_batch(ctx, jobs, true, use_graph != 0, (cudaStream_t)stream);
+    if (st != PM_OK)
+        return st;
+    ctx->pending_n = n;
+    return PM_OK;
+}
+
+pm_status pm_batch_collect(pm_ctx *ctx, pm_plane *planes, int *n_planes, int n)
+{
+    if (!ctx || !planes || !n_planes)
+        return fail(PM_ERR_ARG, "null argument");
+    if (ctx->pending_n == 0 || n != ctx->pending_n)
+        return fail(PM_ERR_STATE, "no pending batch of that size");
+    ctx->pending_n = 0;
+    for (int f = 0; f < n; ++f) {
+        pm_status st = copy_planes(ctx, f, planes + (size_t)f * ctx->rp.max_planes,
+                                   ctx->rp.max_planes, n_planes + f);
+        if (st != PM_OK)
+            return st;
+    }
+    return PM_OK;
+}
+
+pm_status pm_set_timing(pm_ctx *ctx, int on)
+{
+    if (!ctx || on < 0 || on > 2)
+        return fail(PM_ERR_ARG, "null context or timing mode not in {0, 1, 2}");
+    ctx->timing = on;
+    return PM_OK;
+}
+
+pm_status pm_kernel_stats(pm_ctx *ctx, float *score_ms, long long *score_pairs,
+                          int *score_launches, long long *launches)
+{
+    if (!ctx)
+        return fail(PM_ERR_ARG, "null context");
+    if (launches)
+        *launches = ctx->launches;
+    if (ctx->timing != 2)
+        return PM_OK;
+    float tot = 0.0f;
+    long long pairs = 0;
+    for (int r = 0; r < ctx->rp.max_planes; ++r) {
+        float ms = 0.0f;
+        PM_CK(cudaEventElapsedTime(&ms, ctx->kev[2 * r], ctx->kev[2 * r + 1]));
+        tot += ms;
+        for (int f = 0; f < ctx->last_n; ++f)
+            pairs += (long long)ctx->rp.hypotheses * ctx->h_state[f].m_hist[r];
+    }
+    if (score_ms)
+        *score_ms = tot;
+    if (score_pairs)
+        *score_pairs = pairs;
+    if (score_launches)
+        *score_launches = ctx->rp.max_planes;
+    return PM_OK;
+}
+
+pm_status pm_stage_times(pm_ctx *ctx, float ms[3])
+{
+    if (!ctx || !ms)
+        return fail(PM_ERR_ARG, "null argument");
+    for (int i = 0; i < 3; ++i)
+        ms[i] = ctx->stage_ms[i];
+    return PM_OK;
+}
+
+const char *pm_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,173 @@
+// pm_internal.cuh -- device-side structures and helpers shared by the libpm
+// kernels (diffusion, normals, RANSAC) and the C-ABI layer.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/pm.h"
+
+namespace pm {
+
+// ---------------------------------------------------------------------------
+// compile-time layout constants
+// ---------------------------------------------------------------------------
+constexpr int CHUNK = 1024;              // candidates per chunk (RANSAC work unit)
+constexpr int CHUNK_WORDS = CHUNK / 32;  // keep-bitmask words per chunk
+constexpr int MAX_HYP = 2048;            // hypotheses per round (score kernel register budget)
+constexpr int MAX_PLANES = 64;
+constexpr int NMOM = 9;                  // Sx Sy Sz Sxx Sxy Sxz Syy Syz Szz
+// per-chunk moment record: gated set then all-inlier set, each NMOM (sum, comp)
+// float pairs, then two int counts (stored as float bit patterns), padded to 40
+constexpr int PART_WORDS = 40;
+
+// Diffusion tile (temporal blocking): output tile DX x DY, halo T <= DT_MAX
+constexpr int DX = 64;
+constexpr int DY = 32;
+constexpr int DT_MAX = 8;
+
+// ---------------------------------------------------------------------------
+// per-frame descriptors
+// ---------------------------------------------------------------------------
+
+// Source encoding of a diffusion launch: the three sensor encodings of
+// pm_dtype, or the library's compensated iterate (float2 hi/lo per pixel).
+constexpr int SRC_PAIR = 3;
+
+// One frame in one diffusion launch.
+struct DiffFrame {
+    const void *src;      // encoded input (first launch) or float2 iterate
+    int src_dtype;        // PM_U16_MM / PM_F16_M / PM_F32_M / SRC_PAIR
+    int w, h;
+    long long src_pitch;  // bytes
+    void *dst;            // float [h*w] (final) or float2 [h*w] (intermediate)
+    int dst_pair;         // 1: write the float2 iterate, 0: write FP32 depth
+    int n_iters;          // iterations this launch (0 = decode only)
+    int tiles_x;
+    int tile_begin;       // first global tile of this frame
+    float scale;          // metres per u16 unit
+};
+
+// Per-frame RANSAC state on the device.
+struct RState {
+    int M;            // candidates in the current list
+    int M_next;       // candidates kept for the next round (written by compaction)
+    int done;         // 1 once the frame stopped
+    int n_planes;
+    int nchunks;      // chunks of the current list (0 when done)
+    int chunk_base;   // first global work item of this frame in the current round
+    int best_h;
+    int best_count;
+    float4 best_plane;
+    float4 p0;        // first sample point of the winner (moment origin)
+    int m_hist[MAX_PLANES];  // candidates scored in each round (0 once stopped)
+};
+
+struct RFrame {
+    const float *P;           // SoA points [3][npx]
+    const float *N;           // SoA normals [3][npx] or nullptr
+    const unsigned char *valid;
+    short *labels;            // [npx]
+    int w, h, npx;
+    unsigned long long frame_idx;
+    int *cidx[2];             // candidate pixel indices
+    float4 *cpt[2];           // candidate points (x, y, z, 0)
+    float4 *hyp;              // [H] hypothesis planes (nx, ny, nz, d); d = NaN when degenerate
+    float4 *hyp_p0;           // [H] first sample point
+    int *counts;              // [H]
+    int *kept;                // [max_chunks]
+    unsigned *keepbits;       // [max_chunks * CHUNK_WORDS]
+    float *partial;           // [max_chunks * PART_WORDS]
+    RState *st;
+    pm_plane *planes;         // device [MAX_PLANES]
+};
+
+struct RParams {
+    int H;
+    float thr2;          // thr*thr rounded to FP32
+    int max_planes;
+    int min_inliers;
+    unsigned long long seed;
+    float cos_gate;
+};
+
+// ---------------------------------------------------------------------------
+// Exactly specified FP32 arithmetic.  The inlier decision decides integers
+// (counts, argmax, labels), so it is spelled out operation by operation with
+// round-to-nearest intrinsics that the compiler never contracts or reorders.
+// ---------------------------------------------------------------------------
+
+// Hypothesis plane through p0, p1, p2: n = (p1-p0) x (p2-p0), |n|^2 summed
+// as (x^2 + y^2) + z^2, degenerate if |n|^2 <= 1e-18, n /= sqrt(|n|^2),
+// d = -((n.x p0.x + n.y p0.y) + n.z p0.z).
+__device__ __forceinline__ bool hyp_plane(float3 a, float3 b, float3 c, float4 &out)
+{
+    float e1x = __fsub_rn(b.x, a.x), e1y = __fsub_rn(b.y, a.y), e1z = __fsub_rn(b.z, a.z);
+    float e2x = __fsub_rn(c.x, a.x), e2y = __fsub_rn(c.y, a.y), e2z = __fsub_rn(c.z, a.z);
+    float nx = __fsub_rn(__fmul_rn(e1y, e2z), __fmul_rn(e1z, e2y));
+    float ny = __fsub_rn(__fmul_rn(e1z, e2x), __fmul_rn(e1x, e2z));
+    float nz = __fsub_rn(__fmul_rn(e1x, e2y), __fmul_rn(e1y, e2x));
+    float nn = __fadd_rn(__fadd_rn(__fmul_rn(nx, nx), __fmul_rn(ny, ny)), __fmul_rn(nz, nz));
+    if (!(nn > 1e-18f)) {
+        out = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fc00000));
+        return false;
+    }
+    float s = __fsqrt_rn(nn);
+    nx = __fdiv_rn(nx, s);
+    ny = __fdiv_rn(ny, s);
+    nz = __fdiv_rn(nz, s);
+    float dot = __fadd_rn(__fadd_rn(__fmul_rn(nx, a.x), __fmul_rn(ny, a.y)), __fmul_rn(nz, a.z));
+    out = make_float4(nx, ny, nz, -dot);
+    return true;
+}
+
+// Residual r = fma(nz, pz, fma(ny, py, fma(nx, px, d))); inlier iff
+// fma(r, r, -thr2) < 0 (the square is exact inside the fused operation).
+__device__ __forceinline__ bool is_inlier(float4 pl, float px, float py, float pz, float thr2)
+{
+    float r = __fmaf_rn(pl.x, px, pl.w);
+    r = __fmaf_rn(pl.y, py, r);
+    r = __fmaf_rn(pl.z, pz, r);
+    return __fmaf_rn(r, r, -thr2) < 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files); all return cudaGetLastError()
+// ---------------------------------------------------------------------------
+cudaError_t launch_diffuse_tiles(const DiffFrame *d_frames, int n_frames, int total_tiles,
+                                 int T, float lambda, float K, int mode, cudaStream_t s);
+cudaError_t launch_diffuse_stream(const DiffFrame &f, float lambda, float K, int mode,
+                                  cudaStream_t s);
+cudaError_t diffuse_init();   // opt the tile kernels into > 48 KB of shared memory
+cudaError_t launch_normals(const float *depth, int w, int h, float fx, float fy, float cx,
+                           float cy, int stencil, float *P, float *N, unsigned char *valid,
+                           cudaStream_t s);
+cudaError_t launch_normals_batch(const void *d_desc, int n_frames, int max_w, int max_h,
+                                 int stencil, cudaStream_t s);
+
+struct NormFrame {
+    const float *depth;
+    float *P, *N;
+    unsigned char *valid;
+    int w, h;
+    float fx, fy, cx, cy;
+};
+
+// RANSAC round structure (ransac.cu)
+struct RansacLaunch {
+    RFrame *d_frames;     // device array [n]
+    int n;
+    int *d_chunk_base;    // device [n + 1] (prefix of chunk counts, [n] = total)
+    int max_total_chunks; // bound for persistent grids
+    RParams prm;
+    int score_blocks;     // persistent grid sizes
+    int chunk_blocks;
+};
+cudaError_t ransac_init(const RansacLaunch &L, cudaStream_t s);
+// ev_score: optional event pair recorded around the scoring launch.
+cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream_t s,
+                         cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
+constexpr int RANSAC_INIT_LAUNCHES = 3;
+constexpr int RANSAC_ROUND_LAUNCHES = 7;   // the last round skips compaction
+
+}  // namespace pm

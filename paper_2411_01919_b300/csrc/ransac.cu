@@ -1,0 +1,681 @@
+// ransac.cu -- sequential multi-plane RANSAC (Sec. III-D, Eq. 3, Alg. 2) for
+// sm_103a, batched over frames.
+//
+// Per plane round r, for every frame f still running:
+//   k_plan    : candidate count -> chunk count; cross-frame prefix of chunks
+//   k_hyp     : Philox4x64-10 -> three candidate indices -> FP32 plane (Alg. 2
+//               "select random subset of 3 points", "fit plane model")
+//   k_score   : every hypothesis against every candidate on FP32 CUDA cores
+//               (Alg. 2 inner parallel loop); per-thread integer counters,
+//               one atomic add per (CTA, hypothesis)
+//   k_select  : block argmax with the integer key (count, -index)
+//   k_remove  : label the winner's inliers, keep-bitmask of the rest,
+//               compensated-FP32 moments of the inliers (gated by normal and all)
+//   k_refit   : FP64 reduction of the per-chunk moments in a fixed order and
+//               FP64 3x3 eigen-solve -> plane
+//   k_compact : order-preserving compaction of the kept candidates
+// Work is split into chunks of CHUNK candidates; a frame's chunking never
+// depends on the other frames of the batch, and every reduction runs in a
+// fixed order, so a frame's result is bit-identical alone and in a batch.
+#include "pm_internal.cuh"
+
+namespace pm {
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
+                                              unsigned long long k1)
+{
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        unsigned long long lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
+        unsigned long long lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
+        unsigned long long n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += W0; k1 += W1;
+    }
+}
+
+// Frame owning global work item `wi` (chunk_base has n + 1 entries).
+__device__ __forceinline__ int frame_of(const int *__restrict__ base, int n, int wi)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= wi)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// round planning
+// ---------------------------------------------------------------------------
+
+// Exclusive scan of per-frame chunk counts over one block (n <= 1024).
+__device__ void scan_chunks(int *chunk_base, int n, int my)
+{
+    __shared__ int warp_tot[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = my;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    if (lane == 31)
+        warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o)
+                t += y;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    int incl = x + (wid > 0 ? warp_tot[wid - 1] : 0);
+    if ((int)threadIdx.x < n)
+        chunk_base[threadIdx.x] = incl - my;
+    if ((int)threadIdx.x == n - 1)
+        chunk_base[n] = incl;
+}
+
+// Initial plan: chunks over pixels; reset the per-frame state.
+__global__ void __launch_bounds__(1024) k_plan0(RFrame *frames, int n, int *chunk_base)
+{
+    int my = 0;
+    if ((int)threadIdx.x < n) {
+        RFrame &F = frames[threadIdx.x];
+        RState *st = F.st;
+        st->M = 0;
+        st->M_next = 0;
+        st->done = 0;
+        st->n_planes = 0;
+        st->best_h = -1;
+        st->best_count = -1;
+        for (int r = 0; r < MAX_PLANES; ++r)
+            st->m_hist[r] = 0;
+        my = (F.npx + CHUNK - 1) / CHUNK;
+        st->nchunks = my;
+    }
+    scan_chunks(chunk_base, n, my);
+}
+
+__global__ void __launch_bounds__(1024) k_plan(RFrame *frames, int n, int *chunk_base,
+                                               int min_inliers, int round)
+{
+    int my = 0;
+    if ((int)threadIdx.x < n) {
+        RState *st = frames[threadIdx.x].st;
+        if (!st->done) {
+            st->M = st->M_next;
+            if (st->M < 3 || st->M < min_inliers)
+                st->done = 1;
+        }
+        my = st->done ? 0 : (st->M + CHUNK - 1) / CHUNK;
+        st->nchunks = my;
+        st->m_hist[round] = st->done ? 0 : st->M;
+    }
+    scan_chunks(chunk_base, n, my);
+}
+
+// ---------------------------------------------------------------------------
+// round 0 candidate list: valid pixels in row-major order
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mark0(RFrame *frames, int n, const int *chunk_base)
+{
+    const int total = chunk_base[n];
+    for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
+        const int f = frame_of(chunk_base, n, wi);
+        const RFrame &F = frames[f];
+        const int c = wi - chunk_base[f];
+        const int base = c * CHUNK;
+        int kept = 0;
+        for (int j = threadIdx.x; j < CHUNK; j += blockDim.x) {
+            const int pix = base + j;
+            bool keep = false;
+            if (pix < F.npx) {
+                keep = (F.valid[pix] & 1) != 0;
+                F.labels[pix] = -1;
+            }
+            unsigned word = __ballot_sync(0xffffffffu, keep);
+            if ((threadIdx.x & 31) == 0) {
+                F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)] = word;
+                kept += __popc(word);
+            }
+        }
+        __shared__ int wsum[8];
+        if ((threadIdx.x & 31) == 0)
+            wsum[threadIdx.x >> 5] = kept;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int s = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                s += wsum[w];
+            F.kept[c] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Order-preserving compaction of chunk c of the source list into list `dst`.
+// src_image: the source is the pixel array itself (round 0).
+__device__ void compact_chunk(const RFrame &F, int c, int nchunks, int src, int dst,
+                              bool src_image)
+{
+    __shared__ int s_off;
+    __shared__ int s_wpre[CHUNK_WORDS + 1];
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        int s = 0;
+        for (int k = lane; k < c; k += 32)
+            s += F.kept[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+        unsigned wbits = F.keepbits[(long long)c * CHUNK_WORDS + lane];
+        int x = __popc(wbits);
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        s_wpre[lane] = incl - x;
+        if (lane == 31)
+            s_wpre[CHUNK_WORDS] = incl;
+        if (lane == 0)
+            s_off = s;
+    }
+    __syncthreads();
+    const int off = s_off;
+    const long long base = (long long)c * CHUNK;
+    const long long npx = F.npx;
+    for (int j = threadIdx.x; j < CHUNK; j += blockDim.x) {
+        unsigned word = F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)];
+        if (word >> (j & 31) & 1u) {
+            int pos = off + s_wpre[j >> 5] + __popc(word & ((1u << (j & 31)) - 1u));
+            int pix;
+            float4 pt;
+            if (src_image) {
+                pix = (int)(base + j);
+                pt = make_float4(F.P[pix], F.P[npx + pix], F.P[2 * npx + pix], 0.0f);
+            } else {
+                pix = F.cidx[src][base + j];
+                pt = F.cpt[src][base + j];
+            }
+            F.cidx[dst][pos] = pix;
+            F.cpt[dst][pos] = pt;
+        }
+    }
+    if (threadIdx.x == 0 && c == nchunks - 1)
+        F.st->M_next = off + s_wpre[CHUNK_WORDS];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_compact0(RFrame *frames, int n, const int *chunk_base)
+{
+    const int total = chunk_base[n];
+    for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
+        const int f = frame_of(chunk_base, n, wi);
+        const RFrame &F = frames[f];
+        compact_chunk(F, wi - chunk_base[f], F.st->nchunks, 0, 0, true);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_compact(RFrame *frames, int n, const int *chunk_base,
+                                                 int round)
+{
+    const int total = chunk_base[n];
+    const int src = round & 1, dst = src ^ 1;
+    for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
+        const int f = frame_of(chunk_base, n, wi);
+        const RFrame &F = frames[f];
+        if (F.st->done)
+            continue;
+        compact_chunk(F, wi - chunk_base[f], F.st->nchunks, src, dst, false);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// hypotheses
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_hyp(RFrame *frames, RParams prm, int round)
+{
+    const RFrame &F = frames[blockIdx.y];
+    const RState *st = F.st;
+    if (st->done)
+        return;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= prm.H)
+        return;
+    const unsigned long long M = (unsigned long long)st->M;
+    unsigned long long c[4] = {(unsigned long long)h, (unsigned long long)round, F.frame_idx, 0ull};
+    philox4x64_10(c, prm.seed, 0ull);
+    const float4 *pts = F.cpt[round & 1];
+    float4 q0 = pts[__umul64hi(c[0], M)];
+    float4 q1 = pts[__umul64hi(c[1], M)];
+    float4 q2 = pts[__umul64hi(c[2], M)];
+    float4 pl;
+    bool ok = hyp_plane(make_float3(q0.x, q0.y, q0.z), make_float3(q1.x, q1.y, q1.z),
+                        make_float3(q2.x, q2.y, q2.z), pl);
+    F.hyp[h] = pl;
+    F.hyp_p0[h] = q0;
+    F.counts[h] = ok ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// scoring: HPT hypotheses per thread in registers, candidate chunk in smem
+// ---------------------------------------------------------------------------
+template <int HPT>
+__global__ void __launch_bounds__(128) k_score(RFrame *frames, int n, const int *chunk_base,
+                                               RParams prm, int round)
+{
+    __shared__ float4 pts[CHUNK];
+    const int total = chunk_base[n];
+    const float thr2 = prm.thr2;
+    for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
+        const int f = frame_of(chunk_base, n, wi);
+        const RFrame &F = frames[f];
+        const int c = wi - chunk_base[f];
+        const int M = F.st->M;
+        const int base = c * CHUNK;
+        const int cnt = min(CHUNK, M - base);
+        const float4 *src = F.cpt[round & 1] + base;
+        __syncthreads();
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x)
+            pts[j] = src[j];
+        float4 pl[HPT];
+#pragma unroll
+        for (int k = 0; k < HPT; ++k) {
+            const int h = k * blockDim.x + threadIdx.x;
+            pl[k] = h < prm.H ? F.hyp[h] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fc00000));
+        }
+        __syncthreads();
+        int acc[HPT];
+#pragma unroll
+        for (int k = 0; k < HPT; ++k)
+            acc[k] = 0;
+        for (int j = 0; j < cnt; ++j) {
+            const float4 p = pts[j];
+#pragma unroll
+            for (int k = 0; k < HPT; ++k)
+                acc[k] += is_inlier(pl[k], p.x, p.y, p.z, thr2) ? 1 : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < HPT; ++k) {
+            const int h = k * blockDim.x + threadIdx.x;
+            if (h < prm.H && acc[k] > 0)
+                atomicAdd(F.counts + h, acc[k]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// selection: argmax of (count, -h)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_select(RFrame *frames, RParams prm)
+{
+    const RFrame &F = frames[blockIdx.x];
+    RState *st = F.st;
+    if (st->done)
+        return;
+    unsigned long long key = 0;
+    for (int h = threadIdx.x; h < prm.H; h += blockDim.x) {
+        unsigned long long k = ((unsigned long long)(unsigned)(F.counts[h] + 1) << 32) |
+                               (unsigned long long)(0xffffffffu - (unsigned)h);
+        key = k > key ? k : key;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long y = __shfl_xor_sync(0xffffffffu, key, o);
+        key = y > key ? y : key;
+    }
+    __shared__ unsigned long long wk[32];
+    if ((threadIdx.x & 31) == 0)
+        wk[threadIdx.x >> 5] = key;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            key = wk[w] > key ? wk[w] : key;
+        const int best_h = (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
+        const int best_count = (int)(key >> 32) - 1;
+        if (best_count < prm.min_inliers || best_count < 3) {
+            st->done = 1;
+        } else {
+            st->best_h = best_h;
+            st->best_count = best_count;
+            st->best_plane = F.hyp[best_h];
+            st->p0 = F.hyp_p0[best_h];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// removal + compensated moments
+// ---------------------------------------------------------------------------
+
+// Neumaier compensated accumulation in FP32.
+__device__ __forceinline__ void nadd(float &s, float &c, float x)
+{
+    float t = __fadd_rn(s, x);
+    if (fabsf(s) >= fabsf(x))
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, t), x));
+    else
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(x, t), s));
+    s = t;
+}
+
+struct Mom {
+    float s[2][NMOM], c[2][NMOM];
+    int n[2];
+};
+
+__device__ __forceinline__ void mom_add(Mom &m, int set, float x, float y, float z)
+{
+    const float v[NMOM] = {x, y, z, __fmul_rn(x, x), __fmul_rn(x, y), __fmul_rn(x, z),
+                           __fmul_rn(y, y), __fmul_rn(y, z), __fmul_rn(z, z)};
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k)
+        nadd(m.s[set][k], m.c[set][k], v[k]);
+    m.n[set] += 1;
+}
+
+__device__ __forceinline__ void mom_merge(Mom &a, const float *os, const float *oc, const int *on)
+{
+#pragma unroll
+    for (int set = 0; set < 2; ++set) {
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) {
+            nadd(a.s[set][k], a.c[set][k], os[set * NMOM + k]);
+            a.c[set][k] = __fadd_rn(a.c[set][k], oc[set * NMOM + k]);
+        }
+        a.n[set] += on[set];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_remove(RFrame *frames, int n, const int *chunk_base,
+                                                RParams prm, int round)
+{
+    __shared__ float sh_s[8][2 * NMOM], sh_c[8][2 * NMOM];
+    __shared__ int sh_n[8][2], sh_kept[8];
+    const int total = chunk_base[n];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
+        const int f = frame_of(chunk_base, n, wi);
+        const RFrame &F = frames[f];
+        const RState *st = F.st;
+        if (st->done)
+            continue;
+        const int c = wi - chunk_base[f];
+        const int M = st->M;
+        const int base = c * CHUNK;
+        const int cnt = min(CHUNK, M - base);
+        const float4 pl = st->best_plane;
+        const float4 p0 = st->p0;
+        const int cur = round & 1;
+        const long long npx = F.npx;
+        Mom m;
+#pragma unroll
+        for (int set = 0; set < 2; ++set) {
+#pragma unroll
+            for (int k = 0; k < NMOM; ++k)
+                m.s[set][k] = m.c[set][k] = 0.0f;
+            m.n[set] = 0;
+        }
+        int kept = 0;
+        for (int j = threadIdx.x; j < CHUNK; j += blockDim.x) {
+            bool keep = false;
+            if (j < cnt) {
+                const float4 p = F.cpt[cur][base + j];
+                if (is_inlier(pl, p.x, p.y, p.z, prm.thr2)) {
+                    const int pix = F.cidx[cur][base + j];
+                    F.labels[pix] = (short)round;
+                    const float qx = __fsub_rn(p.x, p0.x), qy = __fsub_rn(p.y, p0.y),
+                                qz = __fsub_rn(p.z, p0.z);
+                    mom_add(m, 1, qx, qy, qz);
+                    if (F.N && (F.valid[pix] & 2)) {
+                        const float nx = F.N[pix], ny = F.N[npx + pix], nz = F.N[2 * npx + pix];
+                        const float dot = nx * pl.x + ny * pl.y + nz * pl.z;
+                        if (fabsf(dot) >= prm.cos_gate)
+                            mom_add(m, 0, qx, qy, qz);
+                    }
+                } else {
+                    keep = true;
+                }
+            }
+            const unsigned word = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) {
+                F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)] = word;
+                kept += __popc(word);
+            }
+        }
+        // warp reduction in a fixed order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float os[2 * NMOM], oc[2 * NMOM];
+            int on[2];
+#pragma unroll
+            for (int set = 0; set < 2; ++set) {
+#pragma unroll
+                for (int k = 0; k < NMOM; ++k) {
+                    os[set * NMOM + k] = __shfl_down_sync(0xffffffffu, m.s[set][k], o);
+                    oc[set * NMOM + k] = __shfl_down_sync(0xffffffffu, m.c[set][k], o);
+                }
+                on[set] = __shfl_down_sync(0xffffffffu, m.n[set], o);
+            }
+            if (lane < o)
+                mom_merge(m, os, oc, on);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int set = 0; set < 2; ++set) {
+#pragma unroll
+                for (int k = 0; k < NMOM; ++k) {
+                    sh_s[wid][set * NMOM + k] = m.s[set][k];
+                    sh_c[wid][set * NMOM + k] = m.c[set][k];
+                }
+                sh_n[wid][set] = m.n[set];
+            }
+            sh_kept[wid] = kept;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int kk = sh_kept[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                mom_merge(m, sh_s[w], sh_c[w], sh_n[w]);
+                kk += sh_kept[w];
+            }
+            float *rec = F.partial + (long long)c * PART_WORDS;
+#pragma unroll
+            for (int set = 0; set < 2; ++set) {
+#pragma unroll
+                for (int k = 0; k < NMOM; ++k) {
+                    rec[2 * (set * NMOM + k)] = m.s[set][k];
+                    rec[2 * (set * NMOM + k) + 1] = m.c[set][k];
+                }
+            }
+            rec[36] = __int_as_float(m.n[0]);
+            rec[37] = __int_as_float(m.n[1]);
+            F.kept[c] = kk;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// refit: FP64 reduction + 3x3 symmetric eigen-solve (cyclic Jacobi with the
+// rotation angle from atan2)
+// ---------------------------------------------------------------------------
+__device__ void eig_sym3(double a[3][3], double v[3][3])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            v[i][j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
+        const double scale = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]);
+        if (off <= 1e-22 * scale || off == 0.0)
+            break;
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = pq == 2 ? 1 : 0;
+            const int q = pq == 0 ? 1 : 2;
+            if (a[p][q] == 0.0)
+                continue;
+            const double th = 0.5 * atan2(2.0 * a[p][q], a[q][q] - a[p][p]);
+            const double cs = cos(th), sn = sin(th);
+            // columns p, q of a and v: x_p' = c x_p - s x_q, x_q' = s x_p + c x_q
+            for (int k = 0; k < 3; ++k) {
+                const double xp = a[k][p], xq = a[k][q];
+                a[k][p] = cs * xp - sn * xq;
+                a[k][q] = sn * xp + cs * xq;
+            }
+            for (int k = 0; k < 3; ++k) {
+                const double xp = a[p][k], xq = a[q][k];
+                a[p][k] = cs * xp - sn * xq;
+                a[q][k] = sn * xp + cs * xq;
+            }
+            for (int k = 0; k < 3; ++k) {
+                const double xp = v[k][p], xq = v[k][q];
+                v[k][p] = cs * xp - sn * xq;
+                v[k][q] = sn * xp + cs * xq;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_refit(RFrame *frames, RParams prm, int round)
+{
+    const RFrame &F = frames[blockIdx.x];
+    RState *st = F.st;
+    if (st->done)
+        return;
+    const int nchunks = st->nchunks;
+    double acc[2 * NMOM];
+    long long cnt[2] = {0, 0};
+#pragma unroll
+    for (int k = 0; k < 2 * NMOM; ++k)
+        acc[k] = 0.0;
+    for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
+        const float *rec = F.partial + (long long)c * PART_WORDS;
+#pragma unroll
+        for (int k = 0; k < 2 * NMOM; ++k)
+            acc[k] += (double)rec[2 * k] + (double)rec[2 * k + 1];
+        cnt[0] += __float_as_int(rec[36]);
+        cnt[1] += __float_as_int(rec[37]);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 2 * NMOM; ++k)
+            acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+        cnt[0] += __shfl_down_sync(0xffffffffu, cnt[0], o);
+        cnt[1] += __shfl_down_sync(0xffffffffu, cnt[1], o);
+    }
+    __shared__ double sacc[8][2 * NMOM];
+    __shared__ long long scnt[8][2];
+    if (lane == 0) {
+        for (int k = 0; k < 2 * NMOM; ++k)
+            sacc[wid][k] = acc[k];
+        scnt[wid][0] = cnt[0];
+        scnt[wid][1] = cnt[1];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0)
+        return;
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        for (int k = 0; k < 2 * NMOM; ++k)
+            acc[k] += sacc[w][k];
+        cnt[0] += scnt[w][0];
+        cnt[1] += scnt[w][1];
+    }
+    const int set = cnt[0] >= 3 ? 0 : 1;
+    const double nn = (double)cnt[set];
+    const double *S = acc + set * NMOM;
+    const double mx = S[0] / nn, my = S[1] / nn, mz = S[2] / nn;
+    double a[3][3], v[3][3];
+    a[0][0] = S[3] / nn - mx * mx;
+    a[0][1] = a[1][0] = S[4] / nn - mx * my;
+    a[0][2] = a[2][0] = S[5] / nn - mx * mz;
+    a[1][1] = S[6] / nn - my * my;
+    a[1][2] = a[2][1] = S[7] / nn - my * mz;
+    a[2][2] = S[8] / nn - mz * mz;
+    eig_sym3(a, v);
+    int kmin = 0;
+    for (int k = 1; k < 3; ++k)
+        if (a[k][k] < a[kmin][kmin])
+            kmin = k;
+    double n0 = v[0][kmin], n1 = v[1][kmin], n2 = v[2][kmin];
+    const double ln = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    n0 /= ln; n1 /= ln; n2 /= ln;
+    const float4 p0 = st->p0;
+    const double cx = (double)p0.x + mx, cy = (double)p0.y + my, cz = (double)p0.z + mz;
+    double d = -(n0 * cx + n1 * cy + n2 * cz);
+    if (d < 0.0) {
+        n0 = -n0; n1 = -n1; n2 = -n2; d = -d;
+    }
+    pm_plane &out = F.planes[st->n_planes];
+    out.n[0] = n0;
+    out.n[1] = n1;
+    out.n[2] = n2;
+    out.d = d;
+    out.n_inliers = st->best_count;
+    out.n_refit = (int)cnt[set];
+    out.rms = (float)sqrt(fmax(a[kmin][kmin], 0.0));
+    out.hyp_index = st->best_h;
+    st->n_planes += 1;
+    if (round + 1 >= prm.max_planes)
+        st->done = 1;
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+cudaError_t ransac_init(const RansacLaunch &L, cudaStream_t s)
+{
+    k_plan0<<<1, 1024, 0, s>>>(L.d_frames, L.n, L.d_chunk_base);
+    k_mark0<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base);
+    k_compact0<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base);
+    return cudaGetLastError();
+}
+
+cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream_t s,
+                         cudaEvent_t ev_before, cudaEvent_t ev_after)
+{
+    const RParams &p = L.prm;
+    k_plan<<<1, 1024, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p.min_inliers, round);
+    k_hyp<<<dim3((p.H + 127) / 128, L.n), 128, 0, s>>>(L.d_frames, p, round);
+    if (ev_before)
+        cudaEventRecord(ev_before, s);
+    const int hpt = (p.H + 127) / 128;
+    if (hpt <= 2)
+        k_score<2><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
+    else if (hpt <= 4)
+        k_score<4><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
+    else if (hpt <= 8)
+        k_score<8><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
+    else
+        k_score<16><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
+    if (ev_after)
+        cudaEventRecord(ev_after, s);
+    k_select<<<L.n, 1024, 0, s>>>(L.d_frames, p);
+    k_remove<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
+    k_refit<<<L.n, 256, 0, s>>>(L.d_frames, p, round);
+    if (!last)
+        k_compact<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, round);
+    return cudaGetLastError();
+}
+
+}  // namespace pm

@@ -341,14 +341,21 @@ def _edge_bands(depth_clean, jump=0.05, radius=2):
     return out
 
 
-def sense(scene: Scene, cam: Camera, rng: np.random.Generator, sigma_coeff: float,
-          hole_frac: float, edge_bands: bool, dtype: str, depth_scale=0.001,
-          meta=None) -> Frame:
+def render_gt(scene: Scene, cam: Camera):
+    """Noise-free depth, per-pixel GT plane index and the camera-frame planes."""
     depth_clean, fid = scene.render(cam)
     planes, remap = scene.camera_planes(cam)
     pid = np.full(fid.shape, -1, dtype=np.int32)
     for i, j in remap.items():
         pid[fid == i] = j
+    return depth_clean, pid, planes
+
+
+def sense(scene: Scene, cam: Camera, rng: np.random.Generator, sigma_coeff: float,
+          hole_frac: float, edge_bands: bool, dtype: str, depth_scale=0.001,
+          meta=None, rendered=None) -> Frame:
+    depth_clean, pid, planes = rendered if rendered is not None else render_gt(scene, cam)
+    pid = pid.copy()
     valid = depth_clean > 0
     z = depth_clean + rng.standard_normal(depth_clean.shape) * (sigma_coeff * depth_clean ** 2)
     z = np.where(valid, np.maximum(z, 1e-3), 0.0)
@@ -381,13 +388,20 @@ def frame_c1(seed: int) -> Frame:
     return sense(sc, cam, rng, 0.0015, 0.01, False, 'f32', meta={'config': 'c1', 'seed': seed})
 
 
+_C2_CACHE = {}
+
+
 def frame_c2(seed: int) -> Frame:
     """640x480 u16-mm straight staircase: 6 steps + floor + landing,
-    sigma = 0.002 z^2, 2% random holes plus 5-pixel bands at depth edges."""
+    sigma = 0.002 z^2, 2% random holes plus 5-pixel bands at depth edges.
+    The geometry does not depend on the seed; noise and holes do."""
     rng = np.random.Generator(np.random.PCG64(seed))
     cam = make_camera(640, 480, 385.0, 385.0, 320.0, 240.0, [0.0, 0.0, 1.0], 0.0, np.pi / 4)
     sc = straight_staircase(6, 0.15, 0.28, 1.0, first_riser_y=0.8)
-    return sense(sc, cam, rng, 0.002, 0.02, True, 'u16', meta={'config': 'c2', 'seed': seed})
+    if 'gt' not in _C2_CACHE:
+        _C2_CACHE['gt'] = render_gt(sc, cam)
+    return sense(sc, cam, rng, 0.002, 0.02, True, 'u16', meta={'config': 'c2', 'seed': seed},
+                 rendered=_C2_CACHE['gt'])
 
 
 def _spiral_camera(rng, w, h, fx, fy, cx, cy, height=1.2):

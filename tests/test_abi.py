@@ -1,0 +1,75 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+function include/pm.h declares, struct layouts match, and argument errors are
+reported before anything touches the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2411_01919_b300 as pm
+from paper_2411_01919_b300 import _ffi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, 'include', 'pm.h')
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r'/\*.*?\*/', '', src, flags=re.S)
+    names = re.findall(r'^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*?[\s\*]+(pm_[a-z_0-9]+)\s*\(',
+                       src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_function():
+    lib = pm.load_library()
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(_ffi.EXPORTS) == names
+
+
+def test_struct_sizes():
+    assert ctypes.sizeof(_ffi.Plane) == 48
+    assert ctypes.sizeof(_ffi.Intrinsics) == 32
+    assert ctypes.sizeof(_ffi.RansacParams) == 32
+    assert ctypes.sizeof(_ffi.Frame) == 88
+
+
+def test_last_error_initially_empty_or_text():
+    assert isinstance(pm.load_library().pm_last_error(), bytes)
+
+
+def _create(**kw):
+    lib = pm.load_library()
+    dp = _ffi.DiffusionParams(kw.get('iters', 10), kw.get('lam', 0.2), kw.get('K', 0.02),
+                              kw.get('mode', 0), kw.get('ipl', 0))
+    rp = _ffi.RansacParams(kw.get('H', 256), kw.get('thr', 0.01), kw.get('mp', 4),
+                           kw.get('mi', 100), 0, 20.0)
+    mp = _ffi.MiscParams(kw.get('stencil', 0), 0.001)
+    h = ctypes.c_void_p()
+    st = lib.pm_create(ctypes.byref(dp), ctypes.byref(rp), ctypes.byref(mp), kw.get('w', 64),
+                       kw.get('h', 48), kw.get('frames', 1), ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize('kw', [dict(lam=0.3), dict(lam=0.0), dict(K=-1.0), dict(mode=2),
+                                dict(ipl=9), dict(H=0), dict(H=4096), dict(thr=0.0),
+                                dict(mp=0), dict(mp=65), dict(mi=2), dict(stencil=3),
+                                dict(w=0), dict(frames=0), dict(frames=2000),
+                                dict(iters=-1)])
+def test_create_rejects_bad_parameters_before_touching_the_device(kw):
+    st, h = _create(**kw)
+    assert st == _ffi.PM_ERR_ARG
+    assert h.value is None
+    assert len(pm.load_library().pm_last_error()) > 0
+
+
+def test_scratch_bytes_is_monotone():
+    a = pm.scratch_bytes(640, 480, 1, 1024, 12)
+    b = pm.scratch_bytes(640, 480, 2, 1024, 12)
+    c = pm.scratch_bytes(1280, 720, 1, 1024, 12)
+    assert 0 < a < b and a < c
+    assert pm.scratch_bytes(0, 480, 1, 1024, 12) == -1

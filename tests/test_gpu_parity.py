@@ -1,0 +1,348 @@
+"""GPU parity: every libpm entry point against the FP64 oracle on the same
+seeded inputs, plus form-equivalence (temporal blocking, batch vs single,
+graph vs stream launches, host vs device entry).
+
+Tolerances (spec bar, written here):
+  diffusion            <= 1e-5 m max abs (FP32 and FP16-storage paths alike)
+  normals              <= 0.05 deg
+  plane normal/offset  <= 0.1 deg / 1 mm
+  inlier labels        bit-exact (the inlier decision is FP32 on both sides)
+"""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2411_01919_b300 import Params, Pipeline, PmError
+
+pytestmark = pytest.mark.gpu
+
+DIFF_TOL = 1e-5
+NORMAL_TOL_DEG = 0.05
+PLANE_DEG, PLANE_OFF = 0.1, 1e-3
+DEV = 'cuda:0'
+
+
+def F32(x):
+    """A parameter as the library receives it (the C ABI carries FP32)."""
+    return float(np.float32(x))
+
+
+LAM, KC, SCALE = F32(0.2), F32(0.02), F32(0.001)
+
+CFG = {
+    'c1': dict(frame=lambda s: synth.frame_c1(s), iters=10, H=256, max_planes=4),
+    'c2': dict(frame=lambda s: synth.frame_c2(s), iters=30, H=1024, max_planes=12),
+    'c3': dict(frame=lambda s: synth.frame_c3(s), iters=40, H=2048, max_planes=16),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def frame(name, seed=0):
+    return CFG[name]['frame'](seed)
+
+
+def params(name, **kw):
+    c = CFG[name]
+    p = Params(iters=c['iters'], hypotheses=c['H'], max_planes=c['max_planes'],
+               min_inliers=100, seed=11)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def ang_deg(a, b):
+    c = np.clip(np.abs(np.sum(a * b, axis=0)), 0.0, 1.0)
+    return np.degrees(np.arccos(c))
+
+
+# ---------------------------------------------------------------------------
+# diffusion (Eq. 1, Alg. 1)
+# ---------------------------------------------------------------------------
+
+@functools.lru_cache(maxsize=None)
+def oracle_diffused(name, mode=0, seed=0):
+    fr = frame(name, seed)
+    return oracle.diffuse(oracle.decode(fr.encoded, fr.dtype, SCALE), CFG[name]['iters'], LAM, KC,
+                          mode)
+
+
+@pytest.mark.parametrize('name', ['c1', 'c2', 'c3'])
+@pytest.mark.parametrize('mode', [0, 1])
+def test_diffuse_matches_oracle(name, mode):
+    fr = frame(name)
+    p = params(name, mode=mode)
+    with Pipeline(p, fr.w, fr.h) as pipe:
+        z = pipe.diffuse(to_dev(fr.encoded)).cpu().numpy().astype(np.float64)
+    ref = oracle_diffused(name, mode)
+    err = np.abs(z - ref).max()
+    print('%s mode %d: max |gpu - oracle| = %.3e m' % (name, mode, err))
+    assert err <= DIFF_TOL
+    assert np.array_equal(z == 0, ref == 0)
+
+
+def _random_depth(h, w, seed, holes=0.05, dtype='f32'):
+    rng = np.random.default_rng(seed)
+    z = 1.0 + 0.5 * rng.random() + 0.01 * rng.standard_normal((h, w))
+    z += 0.1 * (np.arange(w)[None, :] > w // 3)
+    z[rng.random((h, w)) < holes] = 0.0
+    enc = {'f32': z.astype(np.float32), 'f16': z.astype(np.float16),
+           'u16': np.rint(z * 1000).astype(np.uint16)}[dtype]
+    return enc
+
+
+@pytest.mark.parametrize('shape', [(1, 1), (1, 37), (37, 1), (33, 65), (97, 129), (200, 3),
+                                   (31, 300)])
+@pytest.mark.parametrize('dtype', ['f32', 'u16', 'f16'])
+@pytest.mark.parametrize('T', [0, 1, 3])
+def test_diffuse_ragged_shapes(shape, dtype, T):
+    h, w = shape
+    enc = _random_depth(h, w, h * 1000 + w, dtype=dtype)
+    p = Params(iters=13, iters_per_launch=T)
+    with Pipeline(p, w, h) as pipe:
+        z = pipe.diffuse(to_dev(enc)).cpu().numpy().astype(np.float64)
+    ref = oracle.diffuse(oracle.decode(enc, dtype, SCALE), 13, LAM, KC, 0)
+    assert np.abs(z - ref).max() <= DIFF_TOL
+
+
+def test_diffuse_all_holes_and_zero_iterations():
+    enc = np.zeros((40, 50), dtype=np.float32)
+    with Pipeline(Params(iters=5), 50, 40) as pipe:
+        assert torch.count_nonzero(pipe.diffuse(to_dev(enc))).item() == 0
+    enc = _random_depth(40, 50, 3)
+    with Pipeline(Params(iters=0), 50, 40) as pipe:
+        z = pipe.diffuse(to_dev(enc)).cpu().numpy()
+    assert np.array_equal(z, np.where(enc > 0, enc, 0))
+
+
+@pytest.mark.parametrize('mode', [0, 1])
+def test_temporal_blocking_is_bit_exact(mode):
+    fr = frame('c2')
+    outs = []
+    for T in (1, 2, 3, 5, 8):
+        with Pipeline(params('c2', mode=mode, iters_per_launch=T), fr.w, fr.h) as pipe:
+            outs.append(pipe.diffuse(to_dev(fr.encoded)).cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o.view(np.uint32), outs[0].view(np.uint32))
+
+
+def test_fp16_storage_path_within_bar():
+    fr = frame('c3')
+    with Pipeline(params('c3'), fr.w, fr.h) as pipe:
+        z = pipe.diffuse(to_dev(fr.encoded)).cpu().numpy().astype(np.float64)
+    err = np.abs(z - oracle_diffused('c3')).max()
+    assert err <= 5e-4 and err <= DIFF_TOL
+
+
+# ---------------------------------------------------------------------------
+# normals (Eq. 2 reading, Alg. 1 second loop)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize('name', ['c1', 'c2', 'c3'])
+@pytest.mark.parametrize('stencil', [0, 1])
+def test_normals_match_oracle(name, stencil):
+    fr = frame(name)
+    z32 = oracle_diffused(name).astype(np.float32)
+    with Pipeline(params(name, stencil=stencil), fr.w, fr.h) as pipe:
+        P, N, V = pipe.normals(to_dev(z32), fr.cam.intrinsics)
+        P, N, V = P.cpu().numpy(), N.cpu().numpy(), V.cpu().numpy()
+    Po, No, Vo = oracle.normals(z32.astype(np.float64), fr.cam.intrinsics, stencil)
+    assert np.array_equal(V, Vo)
+    ok = (V & 2) > 0
+    err = ang_deg(N[:, ok].astype(np.float64), No[:, ok]).max()
+    print('%s stencil %d: normals max angle %.2e deg over %d px' % (name, stencil, err, ok.sum()))
+    assert err <= NORMAL_TOL_DEG
+    assert np.abs(P.astype(np.float64) - Po).max() <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# RANSAC (Eq. 3, Alg. 2), same FP32 points on both sides
+# ---------------------------------------------------------------------------
+
+@functools.lru_cache(maxsize=None)
+def ransac_inputs(name):
+    fr = frame(name)
+    P, N, V = oracle.normals(oracle_diffused(name), fr.cam.intrinsics, 0)
+    return P.astype(np.float32), N.astype(np.float32), V
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_ransac(name, frame_idx=0):
+    P, N, V = ransac_inputs(name)
+    p = params(name)
+    return oracle.ransac(P, N, V, p.hypotheses, p.thr, p.max_planes, p.min_inliers, p.seed,
+                         p.gate_deg, frame_idx)
+
+
+def compare_planes(gpu, orc, exact_labels=True):
+    assert len(gpu.planes) == len(orc.planes)
+    assert np.array_equal(gpu.hyp_index, orc.hyp_index)
+    assert np.array_equal(gpu.n_inliers, orc.n_inliers)
+    for k in range(len(orc.planes)):
+        a, b = gpu.planes[k], orc.planes[k]
+        assert ang_deg(a[:3, None], b[:3, None])[0] <= PLANE_DEG
+        assert abs(a[3] - b[3]) <= PLANE_OFF
+        assert a[3] > 0
+        # the gate decision is FP32 on the GPU, FP64 in the oracle
+        assert abs(int(gpu.n_refit[k]) - int(orc.n_refit[k])) <= max(2, orc.n_refit[k] // 1000)
+
+
+@pytest.mark.parametrize('name', ['c1', 'c2', 'c3'])
+def test_ransac_stage_bit_exact_labels(name):
+    fr = frame(name)
+    P, N, V = ransac_inputs(name)
+    orc = oracle_ransac(name)
+    with Pipeline(params(name), fr.w, fr.h) as pipe:
+        g = pipe.ransac_planes(to_dev(P), to_dev(N), to_dev(V), frame_idx=0)
+        lab = g.labels.cpu().numpy()
+    print('%s: %d planes, near-threshold band counts %s' % (name, len(orc.planes), orc.band))
+    compare_planes(g, orc)
+    assert np.array_equal(lab, orc.labels)
+
+
+def test_ransac_frame_index_changes_hypotheses():
+    fr = frame('c1')
+    P, N, V = ransac_inputs('c1')
+    orc = oracle_ransac('c1', 5)
+    with Pipeline(params('c1'), fr.w, fr.h) as pipe:
+        g = pipe.ransac_planes(to_dev(P), to_dev(N), to_dev(V), frame_idx=5)
+        assert np.array_equal(g.labels.cpu().numpy(), orc.labels)
+    compare_planes(g, orc)
+
+
+def test_ransac_without_normals_uses_all_inliers():
+    fr = frame('c1')
+    P, _, V = ransac_inputs('c1')
+    p = params('c1')
+    orc = oracle.ransac(P, None, V, p.hypotheses, p.thr, p.max_planes, p.min_inliers, p.seed,
+                        p.gate_deg, 0)
+    with Pipeline(p, fr.w, fr.h) as pipe:
+        g = pipe.ransac_planes(to_dev(P), None, to_dev(V), frame_idx=0)
+        assert np.array_equal(g.labels.cpu().numpy(), orc.labels)
+    compare_planes(g, orc)
+    assert np.array_equal(g.n_refit, orc.n_refit)
+
+
+# ---------------------------------------------------------------------------
+# the whole path
+# ---------------------------------------------------------------------------
+
+def match_planes(gpu_pl, orc_pl, min_count):
+    """Every oracle plane with at least min_count inliers has a GPU plane within
+    the plane tolerance (extraction order may differ once an inlier decision
+    near the threshold differs upstream)."""
+    ok = 0
+    for k in range(len(orc_pl.planes)):
+        if orc_pl.n_inliers[k] < min_count:
+            continue
+        o = orc_pl.planes[k]
+        d = [(ang_deg(g[:3, None], o[:3, None])[0], abs(g[3] - o[3])) for g in gpu_pl.planes]
+        assert any(a <= PLANE_DEG and b <= PLANE_OFF for a, b in d), (k, o, d)
+        ok += 1
+    return ok
+
+
+@pytest.mark.parametrize('name', ['c1', 'c2'])
+def test_process_frame_matches_oracle(name):
+    fr = frame(name)
+    p = params(name)
+    out = torch.empty((fr.h, fr.w), dtype=torch.float32, device=DEV)
+    lab = torch.empty((fr.h, fr.w), dtype=torch.int16, device=DEV)
+    with Pipeline(p, fr.w, fr.h) as pipe:
+        g = pipe.process_batch([dict(depth=to_dev(fr.encoded), K=fr.cam.intrinsics, frame_idx=0,
+                                     labels=lab, depth_out=out)], use_graph=False)[0]
+        single = pipe.process_frame(to_dev(fr.encoded), fr.cam.intrinsics, frame_idx=0)
+    res = oracle.process_frame(fr.encoded, fr.dtype, fr.cam.intrinsics, p.iters, LAM, KC,
+                               hypotheses=p.hypotheses, max_planes=p.max_planes,
+                               min_inliers=p.min_inliers, seed=p.seed, frame_idx=0,
+                               depth_scale=SCALE)
+    assert np.abs(out.cpu().numpy().astype(np.float64) - res.depth).max() <= DIFF_TOL
+    n = match_planes(g, res.ransac, 4 * p.min_inliers)
+    assert n >= 3
+    agree = (lab.cpu().numpy() == res.ransac.labels).mean()
+    print('%s: end-to-end %d planes (oracle %d), label agreement %.5f'
+          % (name, len(g.planes), len(res.ransac.planes), agree))
+    assert np.array_equal(single.planes, g.planes)
+    assert np.array_equal(single.labels.cpu().numpy(), lab.cpu().numpy())
+
+
+# ---------------------------------------------------------------------------
+# forms: batch vs single, graph vs stream launches, host vs device
+# ---------------------------------------------------------------------------
+
+def test_batch_and_graph_equal_single_frames():
+    frames = [synth.frame_c4(3, i) for i in range(5)] + [frame('c1'), frame('c2')]
+    p = Params(iters=25, hypotheses=512, max_planes=6, min_inliers=100, seed=3)
+    mw = max(f.w for f in frames)
+    mh = max(f.h for f in frames)
+    dev = [to_dev(f.encoded) for f in frames]
+    iters = [f.meta.get('iters', 25) for f in frames]
+    with Pipeline(p, mw, mh, len(frames)) as pipe:
+        singles = []
+        for i, f in enumerate(frames):
+            pipe1 = Pipeline(Params(**{**p.__dict__, 'iters': iters[i]}), mw, mh, 1)
+            singles.append(pipe1.process_frame(dev[i], f.cam.intrinsics, frame_idx=100 + i))
+            pipe1.close()
+        for use_graph in (False, True, True):
+            labs = [torch.empty((f.h, f.w), dtype=torch.int16, device=DEV) for f in frames]
+            res = pipe.process_batch([dict(depth=dev[i], K=f.cam.intrinsics, frame_idx=100 + i,
+                                           iters=iters[i], labels=labs[i])
+                                      for i, f in enumerate(frames)], use_graph=use_graph)
+            for i in range(len(frames)):
+                assert np.array_equal(res[i].planes, singles[i].planes)
+                assert np.array_equal(res[i].n_inliers, singles[i].n_inliers)
+                assert torch.equal(labs[i], singles[i].labels)
+
+
+def test_host_entry_equals_device_entry():
+    fr = frame('c2')
+    p = params('c2')
+    with Pipeline(p, fr.w, fr.h) as pipe:
+        d = pipe.process_frame(to_dev(fr.encoded), fr.cam.intrinsics, frame_idx=9)
+        lab = np.empty((fr.h, fr.w), dtype=np.int16)
+        h = pipe.process_frame_host(fr.encoded, fr.cam.intrinsics, frame_idx=9, labels=lab)
+    assert np.array_equal(d.planes, h.planes)
+    assert np.array_equal(d.labels.cpu().numpy(), lab)
+
+
+# ---------------------------------------------------------------------------
+# degenerate inputs and argument errors
+# ---------------------------------------------------------------------------
+
+def test_degenerate_frames():
+    p = Params(iters=3, hypotheses=64, max_planes=3, min_inliers=10)
+    K = (50.0, 50.0, 10.0, 10.0)
+    with Pipeline(p, 64, 64) as pipe:
+        z = torch.zeros((20, 20), dtype=torch.float32, device=DEV)
+        r = pipe.process_frame(z, K)
+        assert len(r.planes) == 0 and bool((r.labels == -1).all())
+        z = torch.zeros((20, 20), dtype=torch.float32, device=DEV)
+        z[5, 5] = 1.0
+        z[6, 6] = 1.1
+        r = pipe.process_frame(z, K)
+        assert len(r.planes) == 0
+        z = torch.full((1, 64), 1.5, dtype=torch.float32, device=DEV)
+        r = pipe.process_frame(z, K)
+        assert len(r.planes) == 0
+        f = synth.plane_frame(64, 64, 50.0, 50.0, 31.5, 31.5, [0.2, -0.5, -1.0], 1.2)
+        r = pipe.process_frame(to_dev(f.encoded), f.cam.intrinsics)
+        assert len(r.planes) == 1
+        assert ang_deg(r.planes[0, :3, None], f.planes[0, :3, None])[0] < 0.01
+        assert abs(r.planes[0, 3] - f.planes[0, 3]) < 1e-4
+
+
+def test_argument_errors_raise():
+    with Pipeline(Params(iters=2), 32, 32) as pipe:
+        with pytest.raises(PmError):
+            pipe.diffuse(torch.zeros((40, 40), dtype=torch.float32, device=DEV))
+        with pytest.raises(ValueError):
+            pipe.diffuse(torch.zeros((4, 4), dtype=torch.float64, device=DEV))
+        with pytest.raises(PmError):
+            pipe.process_batch([dict(depth=torch.zeros((4, 4), device=DEV), K=(0, 1, 0, 0))])
