@@ -212,6 +212,28 @@ pm_status pm_stage_times(pm_ctx *ctx, float ms[3]);
 pm_status pm_kernel_stats(pm_ctx *ctx, float *score_ms, long long *score_pairs,
                           int *score_launches, long long *launches);
 
+/* Allocation-free diffusion.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc, e.g. a hard real-time
+ * control loop (cudaMalloc and cudaFree can synchronise the whole device and
+ * take unbounded time) or a plug-in running inside a host framework whose own
+ * allocator owns the device memory.  It needs no pm_ctx and allocates nothing:
+ * the caller passes the input and the output, and the library keeps the
+ * compensated iterate in a fixed array of device memory that every GPU which
+ * loads libpm holds until the process exits (2 x PM_NOALLOC_MAX_PIXELS x 8
+ * bytes = 8 MiB).  Same arguments and result as pm_diffuse with
+ * iters_per_launch = 1 (dp->iters_per_launch is ignored); w * h above
+ * PM_NOALLOC_MAX_PIXELS returns PM_ERR_ARG.  The first call on a device looks
+ * up the array's device address (with that device current); make that first
+ * call before any stream capture.  All calls share the one array: calls whose
+ * GPU work overlaps (on different streams, or from different host threads
+ * without ordering) race and corrupt each other's results.  Every pixel of
+ * the array that a call reads was written earlier in the same call, so no
+ * state carries over from one call to the next. */
+#define PM_NOALLOC_MAX_PIXELS (1 << 19)
+pm_status pm_diffuse_noalloc(const void *depth, int dtype, int w, int h, int pitch,
+                             const pm_diffusion_params *dp, float depth_scale, float *out,
+                             void *stream);
+
 /* Text of the calling thread's last error ("" if none). */
 const char *pm_last_error(void);
 

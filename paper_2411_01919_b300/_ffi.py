@@ -11,6 +11,7 @@ PM_OK, PM_ERR_ARG, PM_ERR_OOM, PM_ERR_CUDA, PM_ERR_TIMEOUT, PM_ERR_STATE = range
 STATUS = {0: 'PM_OK', 1: 'PM_ERR_ARG', 2: 'PM_ERR_OOM', 3: 'PM_ERR_CUDA', 4: 'PM_ERR_TIMEOUT',
           5: 'PM_ERR_STATE'}
 PM_U16_MM, PM_F16_M, PM_F32_M = 0, 1, 2
+PM_NOALLOC_MAX_PIXELS = 1 << 19
 
 
 class Intrinsics(ctypes.Structure):
@@ -49,7 +50,7 @@ class Frame(ctypes.Structure):
 EXPORTS = ['pm_create', 'pm_destroy', 'pm_diffuse', 'pm_normals', 'pm_ransac_planes',
            'pm_process_frame', 'pm_process_frame_host', 'pm_process_batch',
            'pm_process_batch_async', 'pm_batch_collect', 'pm_scratch_bytes', 'pm_set_timing',
-           'pm_stage_times', 'pm_kernel_stats', 'pm_last_error']
+           'pm_stage_times', 'pm_kernel_stats', 'pm_diffuse_noalloc', 'pm_last_error']
 
 _lib = None
 
@@ -88,6 +89,7 @@ def load(path: str = LIB_PATH):
         'pm_stage_times': ([vp, P(ctypes.c_float)], i),
         'pm_kernel_stats': ([vp, P(ctypes.c_float), P(ctypes.c_longlong), P(i),
                              P(ctypes.c_longlong)], i),
+        'pm_diffuse_noalloc': ([vp, i, i, i, i, P(DiffusionParams), ctypes.c_float, vp, vp], i),
         'pm_last_error': ([], ctypes.c_char_p),
     }
     for name, (args, res) in sigs.items():

@@ -1,0 +1,94 @@
+// noalloc.cu -- pm_diffuse_noalloc: diffusion for callers that cannot
+// allocate device memory (see include/pm.h).  The ping-pong iterate lives in
+// a file-scope device array, so a call needs no pm_ctx and makes no
+// allocation; host code reaches the array through the address that
+// cudaGetSymbolAddress returns for the current device.
+#include <cmath>
+#include <mutex>
+
+#include "pm_internal.cuh"
+
+namespace {
+
+constexpr long long kMaxPixels = PM_NOALLOC_MAX_PIXELS;
+
+// Two compensated (hi, lo) iterates of up to kMaxPixels pixels each: 8 MiB,
+// held by every device that loads the library until the process exits.
+static __device__ __align__(256) float2 g_iterate[2 * kMaxPixels];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+float2 *g_addr[kMaxDevices] = {};
+
+// Device address of g_iterate on the current device (looked up once per
+// device, with that device current).
+pm_status iterate_address(float2 **out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return pm::set_last_error(PM_ERR_CUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices)
+        return pm::set_last_error(PM_ERR_ARG, "device ordinal beyond the supported 64");
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_iterate);
+        if (e != cudaSuccess || !p)
+            return pm::set_last_error(PM_ERR_CUDA, e != cudaSuccess ? cudaGetErrorString(e)
+                                                                   : "null symbol address");
+        g_addr[dev] = static_cast<float2 *>(p);
+    }
+    *out = g_addr[dev];
+    return PM_OK;
+}
+
+}  // namespace
+
+extern "C" pm_status pm_diffuse_noalloc(const void *depth, int dtype, int w, int h, int pitch,
+                                        const pm_diffusion_params *dp, float depth_scale,
+                                        float *out, void *stream)
+{
+    using pm::set_last_error;
+    if (!depth || !out || !dp)
+        return set_last_error(PM_ERR_ARG, "null depth, output or parameters");
+    if (dtype != PM_U16_MM && dtype != PM_F16_M && dtype != PM_F32_M)
+        return set_last_error(PM_ERR_ARG, "unknown depth dtype");
+    if (w < 1 || h < 1)
+        return set_last_error(PM_ERR_ARG, "image size must be at least 1x1");
+    if ((long long)w * h > kMaxPixels)
+        return set_last_error(PM_ERR_ARG,
+                              "image larger than PM_NOALLOC_MAX_PIXELS (524288 pixels)");
+    const int es = dtype == PM_F32_M ? 4 : 2;
+    if (pitch < w * es || pitch % es != 0)
+        return set_last_error(PM_ERR_ARG, "pitch smaller than a row or not a multiple of the "
+                                          "element size");
+    if (dp->iters < 0 || dp->iters > 100000 || !(dp->lambda > 0.0f) || dp->lambda > 0.25f ||
+        !(dp->K > 0.0f) || !std::isfinite(dp->K) || (dp->mode != 0 && dp->mode != 1))
+        return set_last_error(PM_ERR_ARG, "diffusion parameters out of range");
+    if (!(depth_scale > 0.0f) || !std::isfinite(depth_scale))
+        return set_last_error(PM_ERR_ARG, "depth_scale must be positive");
+    float2 *it = nullptr;
+    pm_status st = iterate_address(&it);
+    if (st != PM_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = dp->iters > 0 ? dp->iters : 1;
+    for (int k = 0; k < L; ++k) {
+        const bool last = k == L - 1;
+        pm::DiffFrame d{};
+        d.src = k == 0 ? depth : (const void *)(it + ((k - 1) & 1) * kMaxPixels);
+        d.src_dtype = k == 0 ? dtype : pm::SRC_PAIR;
+        d.src_pitch = k == 0 ? pitch : (long long)w * 8;
+        d.w = w;
+        d.h = h;
+        d.dst = last ? (void *)out : (void *)(it + (k & 1) * kMaxPixels);
+        d.dst_pair = last ? 0 : 1;
+        d.n_iters = dp->iters > 0 ? 1 : 0;
+        d.scale = depth_scale;
+        cudaError_t e = pm::launch_diffuse_stream(d, dp->lambda, dp->K, dp->mode, s);
+        if (e != cudaSuccess)
+            return set_last_error(PM_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return PM_OK;
+}

@@ -82,6 +82,11 @@ struct GraphEntry {
 
 }  // namespace
 
+namespace pm {
+// Record `msg` as the calling thread's pm_last_error() text and return `s`.
+pm_status set_last_error(pm_status s, const char *msg) { return fail(s, msg); }
+}  // namespace pm
+
 struct pm_ctx {
     pm_diffusion_params dp;
     pm_ransac_params rp;

@@ -139,6 +139,7 @@ cudaError_t launch_diffuse_tiles(const DiffFrame *d_frames, int n_frames, int to
 cudaError_t launch_diffuse_stream(const DiffFrame &f, float lambda, float K, int mode,
                                   cudaStream_t s);
 cudaError_t diffuse_init();   // opt the tile kernels into > 48 KB of shared memory
+pm_status set_last_error(pm_status s, const char *msg);
 cudaError_t launch_normals(const float *depth, int w, int h, float fx, float fy, float cx,
                            float cy, int stencil, float *P, float *N, unsigned char *valid,
                            cudaStream_t s);

@@ -1,0 +1,62 @@
+"""pm_diffuse_noalloc: diffusion for callers that cannot allocate device memory.
+
+Some callers cannot call cudaMalloc at all -- a hard real-time control loop,
+where cudaMalloc/cudaFree can stall the whole device for an unbounded time, or
+a plug-in inside a host framework whose own allocator owns the device memory.
+For them libpm offers one entry point that needs no context and allocates
+nothing: its working iterate lives in a fixed device array inside the library.
+These tests call it through the C ABI and compare its output with the regular
+pm_diffuse on two calls in a row (the second call reuses the array the first
+one left behind), and check that an oversize image is refused.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from paper_2411_01919_b300 import Params, Pipeline, _ffi
+
+pytestmark = pytest.mark.gpu
+
+DIFF_TOL = 1e-5          # the diffusion tolerance of the other parity tests
+CODES = {'u16': _ffi.PM_U16_MM, 'f16': _ffi.PM_F16_M, 'f32': _ffi.PM_F32_M}
+
+
+def noalloc_diffuse(depth: torch.Tensor, dtype: str, p: Params, out: torch.Tensor) -> int:
+    lib = _ffi.load()
+    dp = _ffi.DiffusionParams(p.iters, p.lam, p.K, p.mode, 0)
+    h, w = depth.shape
+    pitch = depth.stride(0) * depth.element_size()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return lib.pm_diffuse_noalloc(ctypes.c_void_p(depth.data_ptr()), CODES[dtype], w, h, pitch,
+                                  ctypes.byref(dp), p.depth_scale,
+                                  ctypes.c_void_p(out.data_ptr()), stream)
+
+
+def test_noalloc_matches_pm_diffuse_on_two_calls_in_a_row():
+    # a larger frame first, then a smaller one, so stale iterate data from
+    # the first call sits in the shared array when the second one runs
+    cases = [(synth.frame_c3(2), Params(iters=40)), (synth.frame_c2(7), Params(iters=30)),
+             (synth.frame_c1(3), Params(iters=10, mode=1))]
+    for fr, p in cases:
+        d = torch.from_numpy(fr.encoded).cuda()
+        with Pipeline(p, fr.w, fr.h) as pipe:
+            ref = pipe.diffuse(d).clone()
+        out = torch.full((fr.h, fr.w), -1.0, dtype=torch.float32, device='cuda')
+        _ffi.check(noalloc_diffuse(d, fr.dtype, p, out))
+        torch.cuda.synchronize()
+        err = (out.double() - ref.double()).abs().max().item()
+        assert err <= DIFF_TOL, (fr.meta, err)
+        assert torch.equal(out == 0, ref == 0)
+
+
+def test_noalloc_refuses_images_above_its_limit():
+    p = Params(iters=2)
+    side = int(np.ceil(np.sqrt(_ffi.PM_NOALLOC_MAX_PIXELS))) + 1
+    d = torch.ones((side, side), dtype=torch.float32, device='cuda')
+    out = torch.empty_like(d)
+    st = noalloc_diffuse(d, 'f32', p, out)
+    assert st == _ffi.PM_ERR_ARG
+    assert b'PM_NOALLOC_MAX_PIXELS' in _ffi.load().pm_last_error()
