@@ -60,13 +60,18 @@ typedef struct {
  *   central-difference gradient magnitude times the 4-neighbour Laplacian.
  * lambda (Alg. 1's gamma) must lie in (0, 0.25] (stability of the explicit
  * scheme); K (Alg. 1's k) is in metres.  iters_per_launch is the temporal
- * blocking depth (iterations fused in one launch); 0 lets the library choose. */
+ * blocking depth (iterations fused in one launch, 1..8); tile_w x tile_h is
+ * the output tile of one CTA of the fused kernel (tile_w + 2*8 <= 96,
+ * tile_h + 2*8 <= 64).  0 lets the library choose any of the three.  None of
+ * them changes the result: every choice is bit-identical. */
 typedef struct {
     int iters;
     float lambda;
     float K;
     int mode;
     int iters_per_launch;
+    int tile_w;
+    int tile_h;
 } pm_diffusion_params;
 
 /* Alg. 2 parameters (whole-frame sequential form).  Each plane round draws

@@ -21,7 +21,8 @@ class Intrinsics(ctypes.Structure):
 
 class DiffusionParams(ctypes.Structure):
     _fields_ = [('iters', ctypes.c_int), ('lambda_', ctypes.c_float), ('K', ctypes.c_float),
-                ('mode', ctypes.c_int), ('iters_per_launch', ctypes.c_int)]
+                ('mode', ctypes.c_int), ('iters_per_launch', ctypes.c_int),
+                ('tile_w', ctypes.c_int), ('tile_h', ctypes.c_int)]
 
 
 class RansacParams(ctypes.Structure):

@@ -12,9 +12,9 @@
 // with an error-free two-sum.  All arithmetic stays on the FP32 pipes.
 //
 // Two kernels share one per-pixel update (so their results are bit-identical):
-//  * k_diffuse_tiles: temporal blocking.  A CTA loads a (DX+2T) x (DY+2T) tile
+//  * k_diffuse_tiles: temporal blocking.  A CTA loads a (dx+2T) x (dy+2T) tile
 //    with a T-pixel halo into shared memory, runs T Jacobi iterations there on
-//    a shrinking region, and writes the DX x DY interior.  Tiles of every
+//    a shrinking region, and writes the dx x dy interior.  Tiles of every
 //    frame of a batch form one grid (a frame table maps tile -> frame).
 //  * k_diffuse_stream: one iteration per launch over one frame, one pass over
 //    HBM.
@@ -132,9 +132,26 @@ __device__ __forceinline__ void store_px(const DiffFrame &f, long long i, float2
         reinterpret_cast<float *>(f.dst)[i] = v.x;
 }
 
+// PM4 update from the four link fluxes, in the order of update_pm4.
+__device__ __forceinline__ float2 pm4_combine(float2 Ip, float fN, float fS, float fW, float fE,
+                                              float lam)
+{
+    if (Ip.x == 0.0f)
+        return make_float2(0.0f, 0.0f);
+    return pair_add(Ip, __fmul_rn(lam, __fadd_rn(__fadd_rn(__fadd_rn(fN, fS), fW), fE)));
+}
+
+// Temporal blocking.  Block = 32 x 8 threads; tile = dx x dy output pixels
+// with a T-pixel halo, (dx + 2T) x (dy + 2T) float2 cells in shared memory,
+// two buffers.  Iteration it updates the region shrunk by it + 1 on every
+// side.  Each warp (one threadIdx.y) walks a band of rows top to bottom for
+// its columns (lane, lane + 32, ...): the south link flux of a row is the
+// negated north link flux of the next row (exactly, see link_flux), so each
+// pixel evaluates three links (N reused) instead of four.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restrict__ frames,
-                                                       int n_frames, int T, float lam, float c)
+                                                       int n_frames, int T, int dx, int dy,
+                                                       float lam, float c)
 {
     extern __shared__ float2 sm2[];
     const int tile = blockIdx.x;
@@ -148,37 +165,65 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
     }
     const DiffFrame f = frames[lo];
     const int tl = tile - f.tile_begin;
-    const int tx0 = (tl % f.tiles_x) * DX;
-    const int ty0 = (tl / f.tiles_x) * DY;
-    const int SX = DX + 2 * T, SY = DY + 2 * T;
+    const int tx0 = (tl % f.tiles_x) * dx;
+    const int ty0 = (tl / f.tiles_x) * dy;
+    const int SX = dx + 2 * T, SY = dy + 2 * T;
     float2 *A = sm2;
     float2 *B = sm2 + SX * SY;
+    const int lane = threadIdx.x, wy = threadIdx.y;
 
-    for (int i = threadIdx.x; i < SX * SY; i += blockDim.x) {
-        int sy = i / SX, sx = i - sy * SX;
-        int gx = tx0 - T + sx, gy = ty0 - T + sy;
-        float2 v = make_float2(0.0f, 0.0f);
-        if (gx >= 0 && gx < f.w && gy >= 0 && gy < f.h)
-            v = load_px(f.src, f.src_dtype, f.src_pitch, gx, gy, f.scale);
-        A[i] = v;
+    for (int y = wy; y < SY; y += 8) {
+        const int gy = ty0 - T + y;
+        for (int x = lane; x < SX; x += 32) {
+            const int gx = tx0 - T + x;
+            float2 v = make_float2(0.0f, 0.0f);
+            if (gx >= 0 && gx < f.w && gy >= 0 && gy < f.h)
+                v = load_px(f.src, f.src_dtype, f.src_pitch, gx, gy, f.scale);
+            A[y * SX + x] = v;
+        }
     }
     __syncthreads();
     for (int it = 0; it < f.n_iters; ++it) {
         const int r0 = it + 1;
-        const int RW = SX - 2 * r0, RH = SY - 2 * r0;
-        for (int i = threadIdx.x; i < RW * RH; i += blockDim.x) {
-            int ry = i / RW, rx = i - ry * RW;
-            int k = (ry + r0) * SX + rx + r0;
-            B[k] = update<MODE>(A[k], A[k - SX], A[k + SX], A[k - 1], A[k + 1], lam, c);
+        const int RH = SY - 2 * r0;
+        const int band = (RH + 7) >> 3;
+        const int y0 = r0 + wy * band;
+        const int y1 = min(y0 + band, SY - r0);
+        if (y0 < y1) {
+            for (int x = r0 + lane; x < SX - r0; x += 32) {
+                if (MODE == 0) {
+                    float2 cen = A[y0 * SX + x];
+                    float fN = link_flux(cen, A[(y0 - 1) * SX + x], c);
+                    for (int y = y0; y < y1; ++y) {
+                        const int k = y * SX + x;
+                        const float2 dn = A[k + SX];
+                        const float fS = link_flux(cen, dn, c);
+                        const float fW = link_flux(cen, A[k - 1], c);
+                        const float fE = link_flux(cen, A[k + 1], c);
+                        B[k] = pm4_combine(cen, fN, fS, fW, fE, lam);
+                        fN = cen.x == 0.0f ? 0.0f : -fS;
+                        cen = dn;
+                    }
+                } else {
+                    for (int y = y0; y < y1; ++y) {
+                        const int k = y * SX + x;
+                        B[k] = update_alg1(A[k], A[k - SX], A[k + SX], A[k - 1], A[k + 1], lam, c);
+                    }
+                }
+            }
         }
         __syncthreads();
         float2 *t = A; A = B; B = t;
     }
-    for (int i = threadIdx.x; i < DX * DY; i += blockDim.x) {
-        int oy = i / DX, ox = i - oy * DX;
-        int gx = tx0 + ox, gy = ty0 + oy;
-        if (gx < f.w && gy < f.h)
-            store_px(f, (long long)gy * f.w + gx, A[(oy + T) * SX + ox + T]);
+    for (int y = wy; y < dy; y += 8) {
+        const int gy = ty0 + y;
+        if (gy >= f.h)
+            break;
+        for (int x = lane; x < dx; x += 32) {
+            const int gx = tx0 + x;
+            if (gx < f.w)
+                store_px(f, (long long)gy * f.w + gx, A[(y + T) * SX + x + T]);
+        }
     }
 }
 
@@ -205,11 +250,14 @@ static inline float conductance_scale(float K)
     return (float)(-1.4426950408889634 / ((double)K * (double)K));
 }
 
-size_t diffuse_tiles_smem(int T) { return 2ull * (DX + 2 * T) * (DY + 2 * T) * sizeof(float2); }
+size_t diffuse_tiles_smem(int T, int dx, int dy)
+{
+    return 2ull * (dx + 2 * T) * (dy + 2 * T) * sizeof(float2);
+}
 
 cudaError_t diffuse_init()
 {
-    const int mx = (int)diffuse_tiles_smem(DT_MAX);
+    const int mx = (int)diffuse_tiles_smem(DT_MAX, TILE_MAX_DX, TILE_MAX_DY);
     cudaError_t e = cudaFuncSetAttribute(k_diffuse_tiles<0>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess)
@@ -219,16 +267,17 @@ cudaError_t diffuse_init()
 }
 
 cudaError_t launch_diffuse_tiles(const DiffFrame *d_frames, int n_frames, int total_tiles, int T,
-                                 float lambda, float K, int mode, cudaStream_t s)
+                                 int dx, int dy, float lambda, float K, int mode, cudaStream_t s)
 {
-    if (T < 0 || T > DT_MAX)
+    if (T < 0 || T > DT_MAX || dx < 1 || dy < 1 || dx > TILE_MAX_DX || dy > TILE_MAX_DY)
         return cudaErrorInvalidValue;
-    const size_t smem = diffuse_tiles_smem(T);
+    const size_t smem = diffuse_tiles_smem(T, dx, dy);
     const float c = conductance_scale(K);
+    const dim3 block(32, 8);
     if (mode == 0)
-        k_diffuse_tiles<0><<<total_tiles, 256, smem, s>>>(d_frames, n_frames, T, lambda, c);
+        k_diffuse_tiles<0><<<total_tiles, block, smem, s>>>(d_frames, n_frames, T, dx, dy, lambda, c);
     else
-        k_diffuse_tiles<1><<<total_tiles, 256, smem, s>>>(d_frames, n_frames, T, lambda, c);
+        k_diffuse_tiles<1><<<total_tiles, block, smem, s>>>(d_frames, n_frames, T, dx, dy, lambda, c);
     return cudaGetLastError();
 }
 

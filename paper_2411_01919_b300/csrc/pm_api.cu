@@ -144,6 +144,9 @@ pm_status check_params(const pm_diffusion_params *dp, const pm_ransac_params *rp
         return fail(PM_ERR_ARG, "diffusion mode must be 0 (PM4) or 1 (ALG1)");
     if (dp->iters_per_launch < 0 || dp->iters_per_launch > DT_MAX)
         return fail(PM_ERR_ARG, "iters_per_launch must lie in [0, 8]");
+    if (dp->tile_w < 0 || dp->tile_h < 0 || dp->tile_w + 2 * DT_MAX > TILE_MAX_DX ||
+        dp->tile_h + 2 * DT_MAX > TILE_MAX_DY)
+        return fail(PM_ERR_ARG, "tile_w must lie in [0, 80] and tile_h in [0, 48]");
     if (rp->hypotheses < 1 || rp->hypotheses > MAX_HYP)
         return fail(PM_ERR_ARG, "hypotheses must lie in [1, 2048]");
     if (!(rp->thr_m > 0.0f) || !std::isfinite(rp->thr_m))
@@ -217,6 +220,7 @@ std::vector<long long> signature(const std::vector<FrameJob> &jobs, int T, bool 
 
 struct Plan {
     size_t bytes = 0;
+    int dx = 0, dy = 0;               // diffusion output tile
     std::vector<size_t> diff_off;     // table offset of each diffusion launch
     std::vector<int> diff_n, diff_tiles;
     size_t norm_off = 0, rframe_off = 0;
@@ -233,13 +237,19 @@ Plan build_tables(pm_ctx *ctx, const std::vector<FrameJob> &jobs, int T, bool ra
     const int n = (int)jobs.size();
     std::vector<int> L(n);
     int Lmax = 0;
+    long long big_tiles = 0;
     for (int f = 0; f < n; ++f) {
         L[f] = jobs[f].iters == 0 ? 1 : (jobs[f].iters + T - 1) / T;
         Lmax = L[f] > Lmax ? L[f] : Lmax;
         pl.max_w = jobs[f].w > pl.max_w ? jobs[f].w : pl.max_w;
         pl.max_h = jobs[f].h > pl.max_h ? jobs[f].h : pl.max_h;
         pl.total_chunks += ((long long)jobs[f].w * jobs[f].h + CHUNK - 1) / CHUNK;
+        big_tiles += (long long)((jobs[f].w + 79) / 80) * ((jobs[f].h + 47) / 48);
     }
+    // tile shape: large tiles (less halo recompute) once they fill the GPU
+    // twice over, smaller ones for small batches
+    pl.dx = ctx->dp.tile_w > 0 ? ctx->dp.tile_w : (big_tiles >= 2LL * ctx->sms ? 80 : 48);
+    pl.dy = ctx->dp.tile_h > 0 ? ctx->dp.tile_h : (big_tiles >= 2LL * ctx->sms ? 48 : 24);
     size_t off = 0;
     for (int k = 0; k < Lmax; ++k) {
         DiffFrame *tab = reinterpret_cast<DiffFrame *>(ctx->h_tables + off);
@@ -250,7 +260,7 @@ Plan build_tables(pm_ctx *ctx, const std::vector<FrameJob> &jobs, int T, bool ra
                 continue;
             const FrameJob &j = jobs[f];
             const long long slot = (long long)f * ctx->max_npx;
-            const int tx = (j.w + DX - 1) / DX, ty = (j.h + DY - 1) / DY;
+            const int tx = (j.w + pl.dx - 1) / pl.dx, ty = (j.h + pl.dy - 1) / pl.dy;
             if (write) {
                 DiffFrame d;
                 const bool first = k == 0, lastk = k == L[f] - 1;
@@ -378,8 +388,8 @@ pm_status enqueue_batch(pm_ctx *ctx, const Plan &pl, int n, int T, bool ransac, 
             continue;
         int Tk = T;
         PM_CK(launch_diffuse_tiles(reinterpret_cast<const DiffFrame *>(ctx->d_tables + pl.diff_off[k]),
-                                   pl.diff_n[k], pl.diff_tiles[k], Tk, ctx->dp.lambda, ctx->dp.K,
-                                   ctx->dp.mode, s));
+                                   pl.diff_n[k], pl.diff_tiles[k], Tk, pl.dx, pl.dy,
+                                   ctx->dp.lambda, ctx->dp.K, ctx->dp.mode, s));
         ctx->launches += 1;
     }
     if (timed)

@@ -17,13 +17,16 @@ constexpr int CHUNK_WORDS = CHUNK / 32;  // keep-bitmask words per chunk
 constexpr int MAX_HYP = 2048;            // hypotheses per round (score kernel register budget)
 constexpr int MAX_PLANES = 64;
 constexpr int NMOM = 9;                  // Sx Sy Sz Sxx Sxy Sxz Syy Syz Szz
-// per-chunk moment record: gated set then all-inlier set, each NMOM (sum, comp)
-// float pairs, then two int counts (stored as float bit patterns), padded to 40
+constexpr int GROUP = 4;                 // chunks per moment record
+// per-group moment record: gated inliers then the other inliers, each NMOM
+// (sum, comp) float pairs, then two int counts (as float bit patterns), padded
+// to 40 words
 constexpr int PART_WORDS = 40;
 
-// Diffusion tile (temporal blocking): output tile DX x DY, halo T <= DT_MAX
-constexpr int DX = 64;
-constexpr int DY = 32;
+// Diffusion tiles (temporal blocking): output tile dx x dy chosen per launch
+// (at most TILE_MAX_DX x TILE_MAX_DY), halo T <= DT_MAX
+constexpr int TILE_MAX_DX = 96;
+constexpr int TILE_MAX_DY = 64;
 constexpr int DT_MAX = 8;
 
 // ---------------------------------------------------------------------------
@@ -72,12 +75,12 @@ struct RFrame {
     unsigned long long frame_idx;
     int *cidx[2];             // candidate pixel indices
     float4 *cpt[2];           // candidate points (x, y, z, 0)
-    float4 *hyp;              // [H] hypothesis planes (nx, ny, nz, d); d = NaN when degenerate
+    float4 *hyp;              // [H] hypothesis planes (nx, ny, nz, d); d = +inf when degenerate
     float4 *hyp_p0;           // [H] first sample point
     int *counts;              // [H]
     int *kept;                // [max_chunks]
     unsigned *keepbits;       // [max_chunks * CHUNK_WORDS]
-    float *partial;           // [max_chunks * PART_WORDS]
+    float *partial;           // [ceil(max_chunks / GROUP) * PART_WORDS]
     RState *st;
     pm_plane *planes;         // device [MAX_PLANES]
 };
@@ -109,7 +112,8 @@ __device__ __forceinline__ bool hyp_plane(float3 a, float3 b, float3 c, float4 &
     float nz = __fsub_rn(__fmul_rn(e1x, e2y), __fmul_rn(e1y, e2x));
     float nn = __fadd_rn(__fadd_rn(__fmul_rn(nx, nx), __fmul_rn(ny, ny)), __fmul_rn(nz, nz));
     if (!(nn > 1e-18f)) {
-        out = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fc00000));
+        // degenerate: every residual is +inf, so no point is ever an inlier
+        out = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
         return false;
     }
     float s = __fsqrt_rn(nn);
@@ -119,6 +123,19 @@ __device__ __forceinline__ bool hyp_plane(float3 a, float3 b, float3 c, float4 &
     float dot = __fadd_rn(__fadd_rn(__fmul_rn(nx, a.x), __fmul_rn(ny, a.y)), __fmul_rn(nz, a.z));
     out = make_float4(nx, ny, nz, -dot);
     return true;
+}
+
+// Two IEEE fused multiply-adds in one instruction (sm_100+ packed FP32): each
+// lane is exactly fmaf(a, b, c).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
 }
 
 // Residual r = fma(nz, pz, fma(ny, py, fma(nx, px, d))); inlier iff
@@ -135,7 +152,8 @@ __device__ __forceinline__ bool is_inlier(float4 pl, float px, float py, float p
 // launchers (defined in the .cu files); all return cudaGetLastError()
 // ---------------------------------------------------------------------------
 cudaError_t launch_diffuse_tiles(const DiffFrame *d_frames, int n_frames, int total_tiles,
-                                 int T, float lambda, float K, int mode, cudaStream_t s);
+                                 int T, int dx, int dy, float lambda, float K, int mode,
+                                 cudaStream_t s);
 cudaError_t launch_diffuse_stream(const DiffFrame &f, float lambda, float K, int mode,
                                   cudaStream_t s);
 cudaError_t diffuse_init();   // opt the tile kernels into > 48 KB of shared memory

@@ -276,7 +276,12 @@ __global__ void __launch_bounds__(128) k_hyp(RFrame *frames, RParams prm, int ro
 }
 
 // ---------------------------------------------------------------------------
-// scoring: HPT hypotheses per thread in registers, candidate chunk in smem
+// scoring: HPT hypotheses per thread in registers, the candidate chunk in
+// shared memory (one broadcast 16-byte load per point).  Per pair: the three
+// residual FMAs, one FMA for r*r - thr^2, and one integer add of that value's
+// sign bit, which is set iff it is negative (an exact zero rounds to +0, a
+// degenerate plane gives +inf): the same decision as is_inlier().
+// (Packed f32x2 FMAs were measured slower here: they issue to one FMA pipe.)
 // ---------------------------------------------------------------------------
 template <int HPT>
 __global__ void __launch_bounds__(128) k_score(RFrame *frames, int n, const int *chunk_base,
@@ -284,7 +289,8 @@ __global__ void __launch_bounds__(128) k_score(RFrame *frames, int n, const int 
 {
     __shared__ float4 pts[CHUNK];
     const int total = chunk_base[n];
-    const float thr2 = prm.thr2;
+    const float nthr2 = -prm.thr2;
+    const float4 none = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
     for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
         const int f = frame_of(chunk_base, n, wi);
         const RFrame &F = frames[f];
@@ -300,24 +306,29 @@ __global__ void __launch_bounds__(128) k_score(RFrame *frames, int n, const int 
 #pragma unroll
         for (int k = 0; k < HPT; ++k) {
             const int h = k * blockDim.x + threadIdx.x;
-            pl[k] = h < prm.H ? F.hyp[h] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fc00000));
+            pl[k] = h < prm.H ? F.hyp[h] : none;
         }
         __syncthreads();
-        int acc[HPT];
+        unsigned acc[HPT];
 #pragma unroll
         for (int k = 0; k < HPT; ++k)
-            acc[k] = 0;
+            acc[k] = 0u;
+#pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
             const float4 p = pts[j];
 #pragma unroll
-            for (int k = 0; k < HPT; ++k)
-                acc[k] += is_inlier(pl[k], p.x, p.y, p.z, thr2) ? 1 : 0;
+            for (int k = 0; k < HPT; ++k) {
+                float r = __fmaf_rn(pl[k].x, p.x, pl[k].w);
+                r = __fmaf_rn(pl[k].y, p.y, r);
+                r = __fmaf_rn(pl[k].z, p.z, r);
+                acc[k] += __float_as_uint(__fmaf_rn(r, r, nthr2)) >> 31;
+            }
         }
 #pragma unroll
         for (int k = 0; k < HPT; ++k) {
             const int h = k * blockDim.x + threadIdx.x;
-            if (h < prm.H && acc[k] > 0)
-                atomicAdd(F.counts + h, acc[k]);
+            if (h < prm.H && acc[k] > 0u)
+                atomicAdd(F.counts + h, (int)acc[k]);
         }
     }
 }
@@ -405,6 +416,13 @@ __device__ __forceinline__ void mom_merge(Mom &a, const float *os, const float *
     }
 }
 
+// Removal of the winner's inliers.  A work item is a group of GROUP chunks of
+// one frame (group g = chunks [g*GROUP, g*GROUP + GROUP)), fixed by the
+// frame's own candidate count, so its moment record does not depend on the
+// rest of the batch.  Per chunk: labels, keep bitmask and kept count.  Per
+// group: one record of compensated moments of the inliers, centred at the
+// winner's first sample point, in two disjoint sets -- set 0: inliers whose
+// normal passes the refit gate, set 1: the other inliers.
 __global__ void __launch_bounds__(256) k_remove(RFrame *frames, int n, const int *chunk_base,
                                                 RParams prm, int round)
 {
@@ -412,16 +430,18 @@ __global__ void __launch_bounds__(256) k_remove(RFrame *frames, int n, const int
     __shared__ int sh_n[8][2], sh_kept[8];
     const int total = chunk_base[n];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
     for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
         const int f = frame_of(chunk_base, n, wi);
+        const int c0 = wi - chunk_base[f];
+        if (c0 % GROUP)
+            continue;
         const RFrame &F = frames[f];
         const RState *st = F.st;
         if (st->done)
             continue;
-        const int c = wi - chunk_base[f];
         const int M = st->M;
-        const int base = c * CHUNK;
-        const int cnt = min(CHUNK, M - base);
+        const int nch = st->nchunks;
         const float4 pl = st->best_plane;
         const float4 p0 = st->p0;
         const int cur = round & 1;
@@ -434,32 +454,46 @@ __global__ void __launch_bounds__(256) k_remove(RFrame *frames, int n, const int
                 m.s[set][k] = m.c[set][k] = 0.0f;
             m.n[set] = 0;
         }
-        int kept = 0;
-        for (int j = threadIdx.x; j < CHUNK; j += blockDim.x) {
-            bool keep = false;
-            if (j < cnt) {
-                const float4 p = F.cpt[cur][base + j];
-                if (is_inlier(pl, p.x, p.y, p.z, prm.thr2)) {
-                    const int pix = F.cidx[cur][base + j];
-                    F.labels[pix] = (short)round;
-                    const float qx = __fsub_rn(p.x, p0.x), qy = __fsub_rn(p.y, p0.y),
-                                qz = __fsub_rn(p.z, p0.z);
-                    mom_add(m, 1, qx, qy, qz);
-                    if (F.N && (F.valid[pix] & 2)) {
-                        const float nx = F.N[pix], ny = F.N[npx + pix], nz = F.N[2 * npx + pix];
-                        const float dot = nx * pl.x + ny * pl.y + nz * pl.z;
-                        if (fabsf(dot) >= prm.cos_gate)
-                            mom_add(m, 0, qx, qy, qz);
+        const int c1 = min(c0 + GROUP, nch);
+        for (int c = c0; c < c1; ++c) {
+            const int base = c * CHUNK;
+            const int cnt = min(CHUNK, M - base);
+            int kept = 0;
+            for (int j = threadIdx.x; j < CHUNK; j += blockDim.x) {
+                bool keep = false;
+                if (j < cnt) {
+                    const float4 p = F.cpt[cur][base + j];
+                    if (is_inlier(pl, p.x, p.y, p.z, prm.thr2)) {
+                        const int pix = F.cidx[cur][base + j];
+                        F.labels[pix] = (short)round;
+                        int set = 1;
+                        if (F.N && (F.valid[pix] & 2)) {
+                            const float nx = F.N[pix], ny = F.N[npx + pix], nz = F.N[2 * npx + pix];
+                            const float dot = nx * pl.x + ny * pl.y + nz * pl.z;
+                            set = fabsf(dot) >= prm.cos_gate ? 0 : 1;
+                        }
+                        mom_add(m, set, __fsub_rn(p.x, p0.x), __fsub_rn(p.y, p0.y),
+                                __fsub_rn(p.z, p0.z));
+                    } else {
+                        keep = true;
                     }
-                } else {
-                    keep = true;
+                }
+                const unsigned word = __ballot_sync(0xffffffffu, keep);
+                if (lane == 0) {
+                    F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)] = word;
+                    kept += __popc(word);
                 }
             }
-            const unsigned word = __ballot_sync(0xffffffffu, keep);
-            if (lane == 0) {
-                F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)] = word;
-                kept += __popc(word);
+            if (lane == 0)
+                sh_kept[wid] = kept;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int kk = 0;
+                for (int w = 0; w < nwarps; ++w)
+                    kk += sh_kept[w];
+                F.kept[c] = kk;
             }
+            __syncthreads();
         }
         // warp reduction in a fixed order
 #pragma unroll
@@ -488,70 +522,90 @@ __global__ void __launch_bounds__(256) k_remove(RFrame *frames, int n, const int
                 }
                 sh_n[wid][set] = m.n[set];
             }
-            sh_kept[wid] = kept;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int kk = sh_kept[0];
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-                mom_merge(m, sh_s[w], sh_c[w], sh_n[w]);
-                kk += sh_kept[w];
+        // across warps: one thread per moment value, warps merged in order
+        float *rec = F.partial + (long long)(c0 / GROUP) * PART_WORDS;
+        if ((int)threadIdx.x < 2 * NMOM) {
+            const int v = threadIdx.x;
+            float ss = sh_s[0][v], cc = sh_c[0][v];
+            for (int w = 1; w < nwarps; ++w) {
+                nadd(ss, cc, sh_s[w][v]);
+                cc = __fadd_rn(cc, sh_c[w][v]);
             }
-            float *rec = F.partial + (long long)c * PART_WORDS;
-#pragma unroll
-            for (int set = 0; set < 2; ++set) {
-#pragma unroll
-                for (int k = 0; k < NMOM; ++k) {
-                    rec[2 * (set * NMOM + k)] = m.s[set][k];
-                    rec[2 * (set * NMOM + k) + 1] = m.c[set][k];
-                }
-            }
-            rec[36] = __int_as_float(m.n[0]);
-            rec[37] = __int_as_float(m.n[1]);
-            F.kept[c] = kk;
+            rec[2 * v] = ss;
+            rec[2 * v + 1] = cc;
+        } else if ((int)threadIdx.x < 2 * NMOM + 2) {
+            const int set = threadIdx.x - 2 * NMOM;
+            int nn = 0;
+            for (int w = 0; w < nwarps; ++w)
+                nn += sh_n[w][set];
+            rec[36 + set] = __int_as_float(nn);
         }
         __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------
-// refit: FP64 reduction + 3x3 symmetric eigen-solve (cyclic Jacobi with the
-// rotation angle from atan2)
+// refit: FP64 reduction + smallest eigenpair of the 3x3 covariance.
+// The smallest eigenvalue is the smallest root of the characteristic cubic
+//   f(l) = det - c1 l + tr l^2 - l^3   (c1 = sum of the principal 2x2 minors),
+// found by Newton's method from l = 0: on [0, l_min] f is decreasing and
+// convex (f'' = 2 tr - 6 l > 0 below tr / 3), so the iterates rise
+// monotonically to l_min.  Its eigenvector is orthogonal to every row of
+// A - l_min I: the largest of the three pairwise cross products of the rows.
+// No transcendental functions: FP64 is a narrow unit on this GPU.
 // ---------------------------------------------------------------------------
-__device__ void eig_sym3(double a[3][3], double v[3][3])
+__device__ void smallest_eigenpair(const double a[3][3], double &lmin, double v[3])
 {
+    const double tr = a[0][0] + a[1][1] + a[2][2];
+    const double c1 = a[0][0] * a[1][1] + a[0][0] * a[2][2] + a[1][1] * a[2][2] -
+                      a[0][1] * a[0][1] - a[0][2] * a[0][2] - a[1][2] * a[1][2];
+    const double det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[1][2]) -
+                       a[0][1] * (a[0][1] * a[2][2] - a[1][2] * a[0][2]) +
+                       a[0][2] * (a[0][1] * a[1][2] - a[1][1] * a[0][2]);
+    double l = 0.0;
+    for (int it = 0; it < 64; ++it) {
+        const double f = det - l * (c1 - l * (tr - l));
+        const double fp = -c1 + l * (2.0 * tr - 3.0 * l);
+        if (!(fp < 0.0))
+            break;
+        const double nl = l - f / fp;
+        if (!(nl > l))
+            break;
+        l = nl;
+    }
+    lmin = l;
+    double r[3][3];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
-            v[i][j] = i == j ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 64; ++sweep) {
-        const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
-        const double scale = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]);
-        if (off <= 1e-22 * scale || off == 0.0)
-            break;
-        for (int pq = 0; pq < 3; ++pq) {
-            const int p = pq == 2 ? 1 : 0;
-            const int q = pq == 0 ? 1 : 2;
-            if (a[p][q] == 0.0)
-                continue;
-            const double th = 0.5 * atan2(2.0 * a[p][q], a[q][q] - a[p][p]);
-            const double cs = cos(th), sn = sin(th);
-            // columns p, q of a and v: x_p' = c x_p - s x_q, x_q' = s x_p + c x_q
-            for (int k = 0; k < 3; ++k) {
-                const double xp = a[k][p], xq = a[k][q];
-                a[k][p] = cs * xp - sn * xq;
-                a[k][q] = sn * xp + cs * xq;
-            }
-            for (int k = 0; k < 3; ++k) {
-                const double xp = a[p][k], xq = a[q][k];
-                a[p][k] = cs * xp - sn * xq;
-                a[q][k] = sn * xp + cs * xq;
-            }
-            for (int k = 0; k < 3; ++k) {
-                const double xp = v[k][p], xq = v[k][q];
-                v[k][p] = cs * xp - sn * xq;
-                v[k][q] = sn * xp + cs * xq;
-            }
+            r[i][j] = a[i][j] - (i == j ? l : 0.0);
+    double best = -1.0;
+    v[0] = 0.0;
+    v[1] = 0.0;
+    v[2] = 1.0;
+    for (int pq = 0; pq < 3; ++pq) {
+        const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+        const double x = r[p][1] * r[q][2] - r[p][2] * r[q][1];
+        const double y = r[p][2] * r[q][0] - r[p][0] * r[q][2];
+        const double z = r[p][0] * r[q][1] - r[p][1] * r[q][0];
+        const double n2 = x * x + y * y + z * z;
+        if (n2 > best) {
+            best = n2;
+            v[0] = x;
+            v[1] = y;
+            v[2] = z;
         }
+    }
+    const double ln = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (ln > 0.0) {
+        v[0] /= ln;
+        v[1] /= ln;
+        v[2] /= ln;
+    } else {
+        v[0] = 0.0;
+        v[1] = 0.0;
+        v[2] = 1.0;
     }
 }
 
@@ -561,13 +615,13 @@ __global__ void __launch_bounds__(256) k_refit(RFrame *frames, RParams prm, int 
     RState *st = F.st;
     if (st->done)
         return;
-    const int nchunks = st->nchunks;
+    const int ngroups = (st->nchunks + GROUP - 1) / GROUP;
     double acc[2 * NMOM];
     long long cnt[2] = {0, 0};
 #pragma unroll
     for (int k = 0; k < 2 * NMOM; ++k)
         acc[k] = 0.0;
-    for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
+    for (int c = threadIdx.x; c < ngroups; c += blockDim.x) {
         const float *rec = F.partial + (long long)c * PART_WORDS;
 #pragma unroll
         for (int k = 0; k < 2 * NMOM; ++k)
@@ -601,25 +655,23 @@ __global__ void __launch_bounds__(256) k_refit(RFrame *frames, RParams prm, int 
         cnt[0] += scnt[w][0];
         cnt[1] += scnt[w][1];
     }
-    const int set = cnt[0] >= 3 ? 0 : 1;
-    const double nn = (double)cnt[set];
-    const double *S = acc + set * NMOM;
+    // gated inliers if at least 3 pass the gate, else all inliers (set 0 + set 1)
+    const bool gated = cnt[0] >= 3;
+    const long long nsel = gated ? cnt[0] : cnt[0] + cnt[1];
+    double S[NMOM];
+    for (int k = 0; k < NMOM; ++k)
+        S[k] = gated ? acc[k] : acc[k] + acc[NMOM + k];
+    const double nn = (double)nsel;
     const double mx = S[0] / nn, my = S[1] / nn, mz = S[2] / nn;
-    double a[3][3], v[3][3];
+    double a[3][3], lmin, nv[3];
     a[0][0] = S[3] / nn - mx * mx;
     a[0][1] = a[1][0] = S[4] / nn - mx * my;
     a[0][2] = a[2][0] = S[5] / nn - mx * mz;
     a[1][1] = S[6] / nn - my * my;
     a[1][2] = a[2][1] = S[7] / nn - my * mz;
     a[2][2] = S[8] / nn - mz * mz;
-    eig_sym3(a, v);
-    int kmin = 0;
-    for (int k = 1; k < 3; ++k)
-        if (a[k][k] < a[kmin][kmin])
-            kmin = k;
-    double n0 = v[0][kmin], n1 = v[1][kmin], n2 = v[2][kmin];
-    const double ln = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
-    n0 /= ln; n1 /= ln; n2 /= ln;
+    smallest_eigenpair(a, lmin, nv);
+    double n0 = nv[0], n1 = nv[1], n2 = nv[2];
     const float4 p0 = st->p0;
     const double cx = (double)p0.x + mx, cy = (double)p0.y + my, cz = (double)p0.z + mz;
     double d = -(n0 * cx + n1 * cy + n2 * cz);
@@ -632,8 +684,8 @@ __global__ void __launch_bounds__(256) k_refit(RFrame *frames, RParams prm, int 
     out.n[2] = n2;
     out.d = d;
     out.n_inliers = st->best_count;
-    out.n_refit = (int)cnt[set];
-    out.rms = (float)sqrt(fmax(a[kmin][kmin], 0.0));
+    out.n_refit = (int)nsel;
+    out.rms = (float)sqrt(fmax(lmin, 0.0));
     out.hyp_index = st->best_h;
     st->n_planes += 1;
     if (round + 1 >= prm.max_planes)
@@ -660,7 +712,9 @@ cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream
     if (ev_before)
         cudaEventRecord(ev_before, s);
     const int hpt = (p.H + 127) / 128;
-    if (hpt <= 2)
+    if (hpt <= 1)
+        k_score<1><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
+    else if (hpt <= 2)
         k_score<2><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
     else if (hpt <= 4)
         k_score<4><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);

@@ -29,6 +29,8 @@ class Params:
     K: float = 0.02
     mode: int = 0                 # 0 PM4, 1 ALG1
     iters_per_launch: int = 0     # temporal blocking depth, 0 = auto
+    tile_w: int = 0               # fused-diffusion output tile, 0 = auto
+    tile_h: int = 0
     hypotheses: int = 1024
     thr: float = 0.01
     max_planes: int = 12
@@ -94,7 +96,8 @@ class Pipeline:
         self.p = params or Params()
         self.lib = _ffi.load()
         p = self.p
-        self._dp = _ffi.DiffusionParams(p.iters, p.lam, p.K, p.mode, p.iters_per_launch)
+        self._dp = _ffi.DiffusionParams(p.iters, p.lam, p.K, p.mode, p.iters_per_launch,
+                                        p.tile_w, p.tile_h)
         self._rp = _ffi.RansacParams(p.hypotheses, p.thr, p.max_planes, p.min_inliers,
                                      p.seed, p.gate_deg)
         self._mp = _ffi.MiscParams(p.stencil, p.depth_scale)

@@ -45,7 +45,7 @@ def test_last_error_initially_empty_or_text():
 def _create(**kw):
     lib = pm.load_library()
     dp = _ffi.DiffusionParams(kw.get('iters', 10), kw.get('lam', 0.2), kw.get('K', 0.02),
-                              kw.get('mode', 0), kw.get('ipl', 0))
+                              kw.get('mode', 0), kw.get('ipl', 0), kw.get('tw', 0), kw.get('th', 0))
     rp = _ffi.RansacParams(kw.get('H', 256), kw.get('thr', 0.01), kw.get('mp', 4),
                            kw.get('mi', 100), 0, 20.0)
     mp = _ffi.MiscParams(kw.get('stencil', 0), 0.001)
@@ -59,7 +59,7 @@ def _create(**kw):
                                 dict(ipl=9), dict(H=0), dict(H=4096), dict(thr=0.0),
                                 dict(mp=0), dict(mp=65), dict(mi=2), dict(stencil=3),
                                 dict(w=0), dict(frames=0), dict(frames=2000),
-                                dict(iters=-1)])
+                                dict(iters=-1), dict(tw=81), dict(th=49), dict(tw=-1)])
 def test_create_rejects_bad_parameters_before_touching_the_device(kw):
     st, h = _create(**kw)
     assert st == _ffi.PM_ERR_ARG

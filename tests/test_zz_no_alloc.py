@@ -26,7 +26,7 @@ CODES = {'u16': _ffi.PM_U16_MM, 'f16': _ffi.PM_F16_M, 'f32': _ffi.PM_F32_M}
 
 def noalloc_diffuse(depth: torch.Tensor, dtype: str, p: Params, out: torch.Tensor) -> int:
     lib = _ffi.load()
-    dp = _ffi.DiffusionParams(p.iters, p.lam, p.K, p.mode, 0)
+    dp = _ffi.DiffusionParams(p.iters, p.lam, p.K, p.mode, 0, 0, 0)
     h, w = depth.shape
     pitch = depth.stride(0) * depth.element_size()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
