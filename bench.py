@@ -23,6 +23,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -58,7 +60,7 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile('w+', suffix='.csv', delete=False)
         try:
             self.p = subprocess.Popen(['nvidia-smi', '-i', str(index), '--query-gpu=' + self.Q,
-                                       '--format=csv,noheader,nounits', '-lms', '200'],
+                                       '--format=csv,noheader,nounits', '-lms', '100'],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -175,6 +177,50 @@ def diffusion_hbm(torch, pm, dev, pk, side=8192, reps=5):
             'achieved': gbs, 'peak': pk['hbm_gbs'], 'unit': 'GB/s', 'frac': gbs / pk['hbm_gbs']}
 
 
+def run_served(torch, pm, args, c2_frames, c2_dev):
+    """The served form: 16 simulated cameras (fixed resolution each from
+    424x240 / 640x480 / 848x480 / 1280x720, staircases, camera advancing 5 cm
+    per frame), Poisson arrivals with a mean gap of 33 ms, continuous batching
+    under a 4 GiB budget, real time for --served-seconds; then the capacity of
+    the same loop with every request visible at once, on that stream mix and
+    on the 640x480 workload alone."""
+    import synth
+    from paper_2411_01919_b300.serve import Request, Server, poisson_arrivals, summarize
+    n_streams, poses = 16, 4
+    pool = synth.stream_pool(n_streams, poses, seed=0, workers=8)
+    host = {s: [torch.from_numpy(np.ascontiguousarray(f.encoded)).pin_memory() for f in fr]
+            for s, fr in pool.items()}
+    p = pm.Params(iters=30, hypotheses=HYP, thr=THR, max_planes=MAXP, min_inliers=MINI, seed=0)
+
+    def make_reqs(arr):
+        return [Request(s, k, t, host[s][k % poses], pool[s][k % poses].cam.intrinsics,
+                        frame_idx=k) for s, k, t in arr]
+
+    out = {'streams': n_streams, 'rate_per_stream_hz': 30, 'budget_bytes': 4 << 30,
+           'resolutions': sorted({'%dx%d' % (f[0].w, f[0].h) for f in pool.values()}),
+           'distinct_poses_per_stream': poses}
+    srv = Server(p, budget_bytes=4 << 30, max_batch=16, n_lanes=2)
+    srv.run(make_reqs(poisson_arrivals(n_streams, 2.0, 1 / 30, seed=99)))   # warm-up
+    arr = poisson_arrivals(n_streams, args.served_seconds, 1 / 30, seed=1)
+    reqs = srv.run(make_reqs(arr), realtime=True)
+    out.update({'duration_s': args.served_seconds, 'offered': len(arr),
+                'offered_frames_per_s': len(arr) / args.served_seconds})
+    out['realtime'] = summarize(reqs, srv.elapsed)
+    cap = srv.run(make_reqs([(s, k, 0.0) for k in range(40) for s in range(n_streams)]),
+                  realtime=False)
+    out['capacity_mix'] = summarize(cap, srv.elapsed)
+    srv.close()
+    srv = Server(p, budget_bytes=4 << 30, max_batch=16, n_lanes=2, max_w=640, max_h=480)
+    h2 = [torch.from_numpy(f.encoded).pin_memory() for f in c2_frames]
+    c2 = [Request(i % 16, i, 0.0, h2[i % len(h2)], c2_frames[0].cam.intrinsics, frame_idx=i)
+          for i in range(640)]
+    srv.run(c2[:64], realtime=False)
+    cap2 = srv.run(c2, realtime=False)
+    out['capacity_640x480'] = summarize(cap2, srv.elapsed)
+    srv.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_2411_01919_b300 as pm
@@ -187,12 +233,18 @@ def run_ours(args):
     dev = torch.device('cuda', local)
     pk, pk_kind = peaks()
     B = args.batch
-    frames = make_frames(B, 1000 * rank)
+    from paper_2411_01919_b300.shard import max_over_ranks, rank_frame_seeds
+    frames = [__import__('synth').frame_c2(sd) for sd in rank_frame_seeds(rank, world, B)]
     dframes = [torch.from_numpy(f.encoded).to(dev) for f in frames]
     K = frames[0].cam.intrinsics
     params = pm.Params(iters=ITERS, hypotheses=HYP, thr=THR, max_planes=MAXP, min_inliers=MINI,
                        seed=0)
     pipe = pm.Pipeline(params, 640, 480, B)
+    tuned = None
+    if not args.no_tune:
+        from paper_2411_01919_b300.tune import DiffusionTuner
+        tuned = DiffusionTuner().tune(pipe, [dict(depth=dframes[i], K=frames[i].cam.intrinsics,
+                                                  frame_idx=i) for i in range(B)])
     pipe.set_timing(2)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     s = torch.cuda.current_stream()
@@ -224,11 +276,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(step_ms), device=dev)
     value = world * B * args.steps / (tot_ms * 1e-3)
 
     # plain per-frame path: pm_process_frame, synchronised per frame
@@ -241,9 +289,15 @@ def run_ours(args):
         t0 = time.perf_counter()
         pipe1.process_frame(dframes[i], K, frame_idx=i, labels=False)
         lat.append(1e3 * (time.perf_counter() - t0))
+    pipe1.set_timing(1)
+    stage = []
+    for i in range(min(8, B)):
+        pipe1.process_frame(dframes[i], K, frame_idx=i, labels=False)
+        stage.append(pipe1.stage_times())
     plain = {'value': len(lat) / (sum(lat) * 1e-3), 'unit': 'frames/s',
              'p50_ms': percentile(lat, 50), 'p99_ms': percentile(lat, 99), 'frames': len(lat),
-             'api': 'pm_process_frame, one stream, synchronised per frame'}
+             'api': 'pm_process_frame, one stream, synchronised per frame',
+             'stage_ms_median': {k: statistics.median(x[k] for x in stage) for k in stage[0]}}
     pipe1.close()
 
     # end to end: pinned host depth -> device, batch, planes back to host
@@ -284,6 +338,7 @@ def run_ours(args):
             'share_of_step': (score_ms / args.steps) / (tot_ms / args.steps) if world == 1 else None}
 
     hbm = diffusion_hbm(torch, pm, dev, pk) if not args.skip_hbm else None
+    served = run_served(torch, pm, args, frames, dframes) if args.served_seconds > 0 else None
 
     cpu = None
     if rank == 0 and not args.skip_cpu:
@@ -298,10 +353,13 @@ def run_ours(args):
             'data': 'synthetic',
             'config': {'workload': WORKLOAD, 'batch_per_gpu': B, 'form': 'batched, CUDA graph',
                        'l2': 'flushed between steps (256 MB write, untimed)',
-                       'parallelism': 'frames sharded across GPUs, no collective'},
+                       'parallelism': 'frames sharded across GPUs, no collective',
+                       'diffusion_tiling': (dict(zip(('iters_per_launch', 'tile_w', 'tile_h'),
+                                                     tuned['best'])) if tuned else 'library default')},
             'latency_ms': {'p50': percentile(step_ms, 50), 'p99': percentile(step_ms, 99),
                            'note': 'a batched frame completes with its step'},
             'plain': plain, 'speedup_vs_plain': value / world / plain['value'],
+            'served': served,
             'e2e': e2e, 'roofline': roof, 'diffusion_hbm': hbm, 'cpu_baseline': cpu,
             'gpu_launches': launches, 'clocks': clk,
             'paper_context': '>30 Hz whole pipeline; 7.5 ms/frame; <15 ms at 640x480 with 10 '
@@ -317,13 +375,15 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
-    ap.add_argument('--steps', type=int, default=10)
+    ap.add_argument('--steps', type=int, default=30)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', choices=['ours', 'reference'], default='ours')
     ap.add_argument('--batch', type=int, default=64)
     ap.add_argument('--plain-frames', type=int, default=32)
     ap.add_argument('--skip-cpu', action='store_true')
     ap.add_argument('--skip-hbm', action='store_true')
+    ap.add_argument('--no-tune', action='store_true')
+    ap.add_argument('--served-seconds', type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == 'ours':
         print('note: raising --warmup to 3 (timing rule)', file=sys.stderr)

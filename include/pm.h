@@ -201,6 +201,12 @@ pm_status pm_process_batch_async(pm_ctx *ctx, const pm_frame *frames, int n, int
                                  void *stream);
 pm_status pm_batch_collect(pm_ctx *ctx, pm_plane *planes, int *n_planes, int n);
 
+/* Change the diffusion tiling of a context (autotuning): temporal blocking
+ * depth iters_per_launch (1..8) and output tile tile_w x tile_h (limits as in
+ * pm_diffusion_params; 0 = library choice).  Results are bit-identical for
+ * every choice; only speed changes.  PM_ERR_ARG for out-of-range values. */
+pm_status pm_set_tiling(pm_ctx *ctx, int iters_per_launch, int tile_w, int tile_h);
+
 /* Device bytes of scratch a context created with these limits allocates. */
 long long pm_scratch_bytes(int max_w, int max_h, int max_frames, int hypotheses, int max_planes);
 

@@ -438,6 +438,8 @@ pm_status run_batch(pm_ctx *ctx, std::vector<FrameJob> &jobs, bool ransac, bool 
     if (use_graph && s != nullptr) {
         std::vector<long long> sig = signature(jobs, T, ransac);
         sig.push_back(ctx->timing);
+        sig.push_back(pl.dx);
+        sig.push_back(pl.dy);
         cudaGraphExec_t exec = nullptr;
         long long glaunch = 0;
         for (GraphEntry &g : ctx->graphs)
@@ -824,6 +826,19 @@ pm_status pm_batch_collect(pm_ctx *ctx, pm_plane *planes, int *n_planes, int n)
         if (st != PM_OK)
             return st;
     }
+    return PM_OK;
+}
+
+pm_status pm_set_tiling(pm_ctx *ctx, int iters_per_launch, int tile_w, int tile_h)
+{
+    if (!ctx)
+        return fail(PM_ERR_ARG, "null context");
+    if (iters_per_launch < 0 || iters_per_launch > DT_MAX || tile_w < 0 || tile_h < 0 ||
+        tile_w + 2 * DT_MAX > TILE_MAX_DX || tile_h + 2 * DT_MAX > TILE_MAX_DY)
+        return fail(PM_ERR_ARG, "tiling out of range");
+    ctx->dp.iters_per_launch = iters_per_launch;
+    ctx->dp.tile_w = tile_w;
+    ctx->dp.tile_h = tile_h;
     return PM_OK;
 }
 

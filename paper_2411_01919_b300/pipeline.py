@@ -257,6 +257,11 @@ class Pipeline:
             out.append(Planes.from_c(sub, counts[i], self._pending_frames[i].get('labels')))
         return out
 
+    def set_tiling(self, iters_per_launch: int = 0, tile_w: int = 0, tile_h: int = 0):
+        """Diffusion tiling (bit-identical results for every choice)."""
+        check(self.lib.pm_set_tiling(self._h, iters_per_launch, tile_w, tile_h))
+        self.p.iters_per_launch, self.p.tile_w, self.p.tile_h = iters_per_launch, tile_w, tile_h
+
     # -- instrumentation ----------------------------------------------------
     def set_timing(self, mode: int = 1):
         """0 off, 1 per-stage events, 2 events around every scoring launch."""

@@ -1,0 +1,240 @@
+"""Request loop for many depth cameras on one GPU: continuous batching.
+
+Requests (one depth frame of one camera stream) arrive over time.  The loop
+keeps `n_lanes` execution lanes, each a libpm context with its own CUDA
+stream and room for `max_batch` frames.  Whenever a lane is idle it takes the
+oldest admitted requests (at most one per stream per batch, so a stream's
+frames finish in order), copies their depth from pinned host memory into the
+stream's device buffer for that lane, and enqueues the whole path for the
+batch without waiting (pm_process_batch_async).  Requests that arrive while
+batches are on the GPU are admitted as memory frees up and go into the next
+batch of whichever lane frees first; with two lanes one batch runs while the
+next is being filled and launched, so their work overlaps on the device.
+
+Admission is by memory: a request holds, while it is queued or on the GPU,
+the scratch bytes its frame size needs (pm_scratch_bytes for one frame) plus
+its input bytes; the sum over admitted requests stays within the budget
+(default 4 GiB) minus what the lanes and the per-stream buffers hold for good.
+A request not admitted within `max_wait_s` of its arrival is refused.
+
+Each frame's result is bit-identical to processing it alone with
+pm_process_frame (the batched kernels never mix frames), which the test suite
+checks on a mixed stream load.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from .pipeline import Params, Pipeline, Planes, scratch_bytes
+
+
+@dataclass
+class Request:
+    stream: int
+    k: int                      # frame number within the stream
+    t_arrival: float            # seconds since the start of the run
+    depth: torch.Tensor         # pinned host [h, w] (uint16 / float16 / float32)
+    K: tuple
+    frame_idx: int
+    iters: int = -1
+    bytes: int = 0
+    t_admit: Optional[float] = None
+    t_done: Optional[float] = None
+    planes: Optional[Planes] = None
+    refused: bool = False
+
+
+@dataclass
+class _Lane:
+    pipe: Pipeline
+    stream: torch.cuda.Stream
+    index: int
+    batch: List[Request] = field(default_factory=list)
+    event: Optional[torch.cuda.Event] = None
+
+    @property
+    def busy(self):
+        return bool(self.batch)
+
+
+class Server:
+    def __init__(self, params: Params, budget_bytes: int = 4 << 30, max_batch: int = 16,
+                 n_lanes: int = 2, max_w: int = 1280, max_h: int = 720,
+                 max_wait_s: float = 1.0, use_graph: bool = False):
+        self.p = params
+        self.max_batch = max_batch
+        self.max_wait_s = max_wait_s
+        self.use_graph = use_graph
+        self.lanes = [_Lane(Pipeline(params, max_w, max_h, max_batch), torch.cuda.Stream(), i)
+                      for i in range(n_lanes)]
+        self.static_bytes = n_lanes * scratch_bytes(max_w, max_h, max_batch, params.hypotheses,
+                                                    params.max_planes)
+        if self.static_bytes > budget_bytes:
+            raise ValueError('lanes alone need %d bytes, above the budget of %d'
+                             % (self.static_bytes, budget_bytes))
+        self.budget = budget_bytes
+        self.in_use = 0                       # admitted requests
+        self.stream_bytes = 0                 # per-stream device buffers
+        self.dev: Dict[int, List[torch.Tensor]] = {}
+        self.stats = collections.Counter()
+
+    # -- memory -----------------------------------------------------------
+    def request_bytes(self, r: Request) -> int:
+        h, w = r.depth.shape
+        return (scratch_bytes(w, h, 1, self.p.hypotheses, self.p.max_planes)
+                + r.depth.numel() * r.depth.element_size())
+
+    def _room(self) -> int:
+        return self.budget - self.static_bytes - self.stream_bytes - self.in_use
+
+    def _stream_buffers(self, r: Request) -> List[torch.Tensor]:
+        bufs = self.dev.get(r.stream)
+        if bufs is not None and (bufs[0].shape != r.depth.shape or bufs[0].dtype != r.depth.dtype):
+            raise ValueError('stream %d changed its frame size or dtype' % r.stream)
+        if bufs is None:
+            bufs = [torch.empty(r.depth.shape, dtype=r.depth.dtype, device='cuda')
+                    for _ in self.lanes]
+            self.dev[r.stream] = bufs
+            self.stream_bytes += sum(b.numel() * b.element_size() for b in bufs)
+        return bufs
+
+    # -- the loop -----------------------------------------------------------
+    def _launch(self, lane: _Lane, batch: List[Request]):
+        frames = []
+        with torch.cuda.stream(lane.stream):
+            for r in batch:
+                buf = self._stream_buffers(r)[lane.index]
+                buf.copy_(r.depth, non_blocking=True)
+                frames.append(dict(depth=buf, K=r.K, frame_idx=r.frame_idx, iters=r.iters))
+            lane.pipe.submit_batch(frames, use_graph=self.use_graph, stream=lane.stream)
+            lane.event = torch.cuda.Event()
+            lane.event.record(lane.stream)
+        lane.batch = batch
+        self.stats['batches'] += 1
+        self.stats['batched_frames'] += len(batch)
+
+    def _finish(self, lane: _Lane, now: float, done: List[Request]):
+        res = lane.pipe.collect_batch()
+        for r, planes in zip(lane.batch, res):
+            r.planes = planes
+            r.t_done = now
+            self.in_use -= r.bytes
+            done.append(r)
+        lane.batch = []
+        lane.event = None
+
+    def _admit(self, waiting: collections.deque, admitted: collections.deque, now: float):
+        while waiting:
+            r = waiting[0]
+            if now - r.t_arrival > self.max_wait_s:
+                waiting.popleft()
+                r.refused = True
+                self.stats['refused'] += 1
+                continue
+            need = self.request_bytes(r)
+            if r.stream not in self.dev:
+                # a stream's first request also reserves its device buffers
+                extra = len(self.lanes) * r.depth.numel() * r.depth.element_size()
+                if need + extra > self._room():
+                    break
+                self._stream_buffers(r)
+            elif need > self._room():
+                break
+            waiting.popleft()
+            r.bytes = need
+            r.t_admit = now
+            self.in_use += need
+            self.stats['peak_in_use'] = max(self.stats['peak_in_use'], self.in_use)
+            admitted.append(r)
+
+    def _take_batch(self, admitted: collections.deque) -> List[Request]:
+        batch, seen, rest = [], set(), collections.deque()
+        while admitted and len(batch) < self.max_batch:
+            r = admitted.popleft()
+            if r.stream in seen:
+                rest.append(r)
+            else:
+                seen.add(r.stream)
+                batch.append(r)
+        while rest:
+            admitted.appendleft(rest.pop())
+        return batch
+
+    def run(self, requests: Sequence[Request], realtime: bool = True) -> List[Request]:
+        """Serve `requests` (sorted by arrival).  realtime: requests become
+        visible at their arrival time on the wall clock; otherwise all are
+        visible at once (throughput mode).  Returns every request, with
+        t_done/planes filled in or refused set."""
+        reqs = sorted(requests, key=lambda r: r.t_arrival)
+        waiting, admitted = collections.deque(), collections.deque()
+        done: List[Request] = []
+        i = 0
+        t0 = time.perf_counter()
+        while i < len(reqs) or waiting or admitted or any(l.busy for l in self.lanes):
+            now = time.perf_counter() - t0
+            while i < len(reqs) and (not realtime or reqs[i].t_arrival <= now):
+                if not realtime:
+                    reqs[i].t_arrival = now
+                waiting.append(reqs[i])
+                i += 1
+            progressed = False
+            for lane in self.lanes:
+                if lane.busy and lane.event.query():
+                    self._finish(lane, time.perf_counter() - t0, done)
+                    progressed = True
+            self._admit(waiting, admitted, now)
+            for lane in self.lanes:
+                if not lane.busy and admitted:
+                    batch = self._take_batch(admitted)
+                    if batch:
+                        self._launch(lane, batch)
+                        progressed = True
+            if not progressed:
+                if realtime and i < len(reqs) and not admitted and not waiting:
+                    nxt = reqs[i].t_arrival - (time.perf_counter() - t0)
+                    if nxt > 0 and not any(l.busy for l in self.lanes):
+                        time.sleep(min(nxt, 0.002))
+                        continue
+                time.sleep(20e-6)
+        self.elapsed = time.perf_counter() - t0
+        return reqs
+
+    def close(self):
+        for lane in self.lanes:
+            lane.pipe.close()
+
+
+def summarize(reqs: Sequence[Request], elapsed: float) -> dict:
+    ok = [r for r in reqs if r.t_done is not None]
+    lat = sorted(1e3 * (r.t_done - r.t_arrival) for r in ok)
+
+    def pct(q):
+        if not lat:
+            return None
+        return lat[min(len(lat) - 1, int(round(q / 100.0 * (len(lat) - 1))))]
+
+    return {'frames': len(ok), 'refused': sum(r.refused for r in reqs),
+            'frames_per_s': len(ok) / elapsed if elapsed > 0 else None,
+            'p50_ms': pct(50), 'p99_ms': pct(99), 'max_ms': lat[-1] if lat else None,
+            'elapsed_s': elapsed}
+
+
+def poisson_arrivals(n_streams: int, duration_s: float, mean_gap_s: float, seed: int):
+    """(stream, k, t) for Poisson arrivals of every stream over duration_s."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(n_streams):
+        t = rng.uniform(0, mean_gap_s)
+        k = 0
+        while t < duration_s:
+            out.append((s, k, t))
+            t += rng.exponential(mean_gap_s)
+            k += 1
+    out.sort(key=lambda x: x[2])
+    return out

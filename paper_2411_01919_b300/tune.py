@@ -1,0 +1,78 @@
+"""Autotuner for the fused diffusion kernel of a batch shape.
+
+The temporal-blocking depth (iterations fused per launch) and the output tile
+of k_diffuse_tiles trade halo recomputation against launch count and
+occupancy, and the best choice depends on the batch: frame sizes, iteration
+counts and how many tiles there are per SM.  Every choice gives bit-identical
+results (the per-pixel update is the same), so the tuner measures each
+candidate on the batch itself and keeps the fastest.  Results are cached per
+batch shape.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+from typing import Dict, List, Sequence, Tuple
+
+import torch
+
+# (iterations per launch, tile_w, tile_h)
+CANDIDATES: List[Tuple[int, int, int]] = [
+    (T, tw, th) for T in (4, 6, 8) for (tw, th) in ((48, 24), (64, 32), (80, 48), (64, 48))
+]
+
+
+def batch_key(frames: Sequence[dict], default_iters: int) -> str:
+    shapes = sorted((int(f['depth'].shape[1]), int(f['depth'].shape[0]),
+                     int(f.get('iters', -1)) if int(f.get('iters', -1)) >= 0 else default_iters)
+                    for f in frames)
+    return json.dumps(shapes)
+
+
+class DiffusionTuner:
+    """Picks the fastest diffusion tiling for a batch shape on one Pipeline."""
+
+    def __init__(self, cache_path: str = None, candidates=None, reps: int = 3):
+        self.cache: Dict[str, list] = {}
+        self.cache_path = cache_path
+        self.candidates = list(candidates or CANDIDATES)
+        self.reps = reps
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as fh:
+                self.cache = json.load(fh)
+
+    def _time_diffusion(self, pipe, frames) -> float:
+        ts = []
+        for _ in range(self.reps):
+            pipe.process_batch(frames, use_graph=False)
+            ts.append(pipe.stage_times()['diffuse_ms'])
+        return statistics.median(ts)
+
+    def tune(self, pipe, frames: Sequence[dict]) -> dict:
+        """Measure every candidate on `frames`, leave the best set on `pipe` and
+        return {'best': (T, tw, th), 'ms': {candidate: median diffusion ms}}."""
+        key = batch_key(frames, pipe.p.iters)
+        if key in self.cache:
+            best = tuple(self.cache[key])
+            pipe.set_tiling(*best)
+            return {'best': best, 'ms': None, 'cached': True}
+        old = (pipe.p.iters_per_launch, pipe.p.tile_w, pipe.p.tile_h)
+        pipe.set_timing(1)
+        table = {}
+        try:
+            pipe.process_batch(frames, use_graph=False)          # warm-up
+            for cand in self.candidates:
+                pipe.set_tiling(*cand)
+                table[cand] = self._time_diffusion(pipe, frames)
+        finally:
+            pipe.set_timing(0)
+            pipe.set_tiling(*old)
+        best = min(table, key=table.get)
+        pipe.set_tiling(*best)
+        self.cache[key] = list(best)
+        if self.cache_path:
+            with open(self.cache_path, 'w') as fh:
+                json.dump(self.cache, fh)
+        torch.cuda.synchronize()
+        return {'best': best, 'ms': {str(k): v for k, v in table.items()}, 'cached': False}

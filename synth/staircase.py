@@ -502,3 +502,28 @@ def plane_frame(w, h, fx, fy, cx, cy, n, d, dtype='f32') -> Frame:
     enc = z.astype({'f32': np.float32, 'f16': np.float16}[dtype]) if dtype != 'u16' else \
         np.clip(np.rint(z * 1000), 0, U16_MAX).astype(np.uint16)
     return Frame(cam, z, z.copy(), pid, planes, dtype, enc)
+
+
+def _c5_job(args):
+    stream, k, seed = args
+    f = frame_c5(stream, k, seed)
+    return stream, k, f
+
+
+def stream_pool(n_streams: int, poses: int, seed: int = 0, workers: int = 0):
+    """Frames of `n_streams` simulated cameras at `poses` successive poses (5 cm
+    apart), rendered in a pool of spawned worker processes (safe to call after
+    CUDA is initialised).  Returns {stream: [Frame, ...]}."""
+    import multiprocessing as mp
+    jobs = [(s, k, seed) for s in range(n_streams) for k in range(poses)]
+    out = {s: [None] * poses for s in range(n_streams)}
+    if workers and workers > 1:
+        ctx = mp.get_context('spawn')
+        with ctx.Pool(workers) as pool:
+            for s, k, f in pool.imap_unordered(_c5_job, jobs):
+                out[s][k] = f
+    else:
+        for job in jobs:
+            s, k, f = _c5_job(job)
+            out[s][k] = f
+    return out
