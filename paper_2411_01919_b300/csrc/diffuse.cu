@@ -39,13 +39,15 @@ __device__ __forceinline__ float pair_diff(float2 q, float2 p)
     return __fadd_rn(__fsub_rn(q.x, p.x), __fsub_rn(q.y, p.y));
 }
 
-// (hi, lo) + a, renormalised: two-sum of hi and a, the error folded into lo,
-// then a fast two-sum so that |lo| <= ulp(hi)/2.
+// (hi, lo) + a, renormalised.  The update is small next to the depth
+// (|a| <= lambda * 4 * max|g(x) x| = 0.86 K, a few mm, against depths of
+// decimetres and more), so Dekker's fast two-sum gives the exact rounding
+// error of hi + a; it is folded into lo and the pair renormalised so that
+// |lo| <= ulp(hi)/2.
 __device__ __forceinline__ float2 pair_add(float2 p, float a)
 {
     const float s = __fadd_rn(p.x, a);
-    const float bb = __fsub_rn(s, p.x);
-    const float e = __fadd_rn(__fsub_rn(p.x, __fsub_rn(s, bb)), __fsub_rn(a, bb));
+    const float e = __fsub_rn(a, __fsub_rn(s, p.x));
     const float l = __fadd_rn(p.y, e);
     const float h2 = __fadd_rn(s, l);
     return make_float2(h2, __fsub_rn(l, __fsub_rn(h2, s)));
@@ -190,26 +192,41 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
         const int y0 = r0 + wy * band;
         const int y1 = min(y0 + band, SY - r0);
         if (y0 < y1) {
-            for (int x = r0 + lane; x < SX - r0; x += 32) {
-                if (MODE == 0) {
-                    float2 cen = A[y0 * SX + x];
-                    float fN = link_flux(cen, A[(y0 - 1) * SX + x], c);
-                    for (int y = y0; y < y1; ++y) {
-                        const int k = y * SX + x;
-                        const float2 dn = A[k + SX];
-                        const float fS = link_flux(cen, dn, c);
-                        const float fW = link_flux(cen, A[k - 1], c);
-                        const float fE = link_flux(cen, A[k + 1], c);
-                        B[k] = pm4_combine(cen, fN, fS, fW, fE, lam);
-                        fN = cen.x == 0.0f ? 0.0f : -fS;
-                        cen = dn;
+            if (MODE == 0) {
+                // the (up to) three column groups of this lane, walked down together
+                constexpr int G = TILE_MAX_DX / 32;
+                float2 cen[G];
+                float fN[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const int x = r0 + lane + 32 * g;
+                    if (x < SX - r0) {
+                        cen[g] = A[y0 * SX + x];
+                        fN[g] = link_flux(cen[g], A[(y0 - 1) * SX + x], c);
                     }
-                } else {
+                }
+                for (int y = y0; y < y1; ++y) {
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const int x = r0 + lane + 32 * g;
+                        if (x < SX - r0) {
+                            const int k = y * SX + x;
+                            const float2 dn = A[k + SX];
+                            const float fS = link_flux(cen[g], dn, c);
+                            const float fW = link_flux(cen[g], A[k - 1], c);
+                            const float fE = link_flux(cen[g], A[k + 1], c);
+                            B[k] = pm4_combine(cen[g], fN[g], fS, fW, fE, lam);
+                            fN[g] = cen[g].x == 0.0f ? 0.0f : -fS;
+                            cen[g] = dn;
+                        }
+                    }
+                }
+            } else {
+                for (int x = r0 + lane; x < SX - r0; x += 32)
                     for (int y = y0; y < y1; ++y) {
                         const int k = y * SX + x;
                         B[k] = update_alg1(A[k], A[k - SX], A[k + SX], A[k - 1], A[k + 1], lam, c);
                     }
-                }
             }
         }
         __syncthreads();
@@ -227,21 +244,78 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
     }
 }
 
+// One iteration over one frame, one pass over HBM.  Block = 32 x 8 threads;
+// lane l of warp w covers the two columns x0 = 64*blockIdx.x + 2l, x0 + 1 and
+// walks STREAM_ROWS rows down: the north link flux of a row is the negated
+// south link flux of the row before (exactly, see link_flux), the link
+// between the two columns is evaluated once, and the west flux of x0 is the
+// negated east flux of the lane to the left (a shuffle); only lane 0 and
+// lane 31 read a column of the neighbouring warp.  Every link appears in the
+// sum of update_pm4 with the same value and in the same order, so the result
+// is bit-identical to the tiled kernel.
+constexpr int STREAM_ROWS = 8;
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_diffuse_stream(DiffFrame f, float lam, float c)
 {
-    const int x = blockIdx.x * 32 + threadIdx.x;
-    const int y = blockIdx.y * 8 + threadIdx.y;
-    if (x >= f.w || y >= f.h)
+    const int lane = threadIdx.x;
+    const int x0 = blockIdx.x * 64 + 2 * lane;
+    const int y0 = (blockIdx.y * 8 + threadIdx.y) * STREAM_ROWS;
+    if (y0 >= f.h)
         return;
+    const int y1 = min(y0 + STREAM_ROWS, f.h);
     const float2 Z = make_float2(0.0f, 0.0f);
-    const float2 Ip = load_px(f.src, f.src_dtype, f.src_pitch, x, y, f.scale);
-    const float2 In = y > 0 ? load_px(f.src, f.src_dtype, f.src_pitch, x, y - 1, f.scale) : Z;
-    const float2 Is = y + 1 < f.h ? load_px(f.src, f.src_dtype, f.src_pitch, x, y + 1, f.scale) : Z;
-    const float2 Iw = x > 0 ? load_px(f.src, f.src_dtype, f.src_pitch, x - 1, y, f.scale) : Z;
-    const float2 Ie = x + 1 < f.w ? load_px(f.src, f.src_dtype, f.src_pitch, x + 1, y, f.scale) : Z;
-    const float2 out = f.n_iters > 0 ? update<MODE>(Ip, In, Is, Iw, Ie, lam, c) : Ip;
-    store_px(f, (long long)y * f.w + x, out);
+    auto ld = [&](int x, int y) -> float2 {
+        return (x >= 0 && x < f.w && y >= 0 && y < f.h)
+                   ? load_px(f.src, f.src_dtype, f.src_pitch, x, y, f.scale) : Z;
+    };
+    float2 a0 = ld(x0, y0), a1 = ld(x0 + 1, y0);
+    float2 u0 = ld(x0, y0 - 1), u1 = ld(x0 + 1, y0 - 1);
+    float fN0 = 0.0f, fN1 = 0.0f;
+    if (MODE == 0) {
+        fN0 = link_flux(a0, u0, c);
+        fN1 = link_flux(a1, u1, c);
+    }
+    for (int y = y0; y < y1; ++y) {
+        const float2 d0 = ld(x0, y + 1), d1 = ld(x0 + 1, y + 1);
+        float2 L = make_float2(__shfl_up_sync(0xffffffffu, a1.x, 1),
+                               __shfl_up_sync(0xffffffffu, a1.y, 1));
+        float2 R = make_float2(__shfl_down_sync(0xffffffffu, a0.x, 1),
+                               __shfl_down_sync(0xffffffffu, a0.y, 1));
+        if (lane == 0)
+            L = ld(x0 - 1, y);
+        if (lane == 31)
+            R = ld(x0 + 2, y);
+        float2 n0, n1;
+        if (MODE == 0) {
+            const float f01 = link_flux(a0, a1, c);              // into x0 from x0+1
+            const float fE1 = link_flux(a1, R, c);               // into x0+1 from x0+2
+            const float fEl = __shfl_up_sync(0xffffffffu, fE1, 1);
+            float fW0 = L.x == 0.0f ? 0.0f : -fEl;               // into x0 from x0-1
+            if (lane == 0)
+                fW0 = link_flux(a0, L, c);
+            const float fW1 = a0.x == 0.0f ? 0.0f : -f01;
+            const float fS0 = link_flux(a0, d0, c), fS1 = link_flux(a1, d1, c);
+            n0 = pm4_combine(a0, fN0, fS0, fW0, f01, lam);
+            n1 = pm4_combine(a1, fN1, fS1, fW1, fE1, lam);
+            fN0 = a0.x == 0.0f ? 0.0f : -fS0;
+            fN1 = a1.x == 0.0f ? 0.0f : -fS1;
+        } else {
+            n0 = update_alg1(a0, u0, d0, L, a1, lam, c);
+            n1 = update_alg1(a1, u1, d1, a0, R, lam, c);
+        }
+        if (f.n_iters == 0) {
+            n0 = a0;
+            n1 = a1;
+        }
+        const long long row = (long long)y * f.w;
+        if (x0 < f.w)
+            store_px(f, row + x0, n0);
+        if (x0 + 1 < f.w)
+            store_px(f, row + x0 + 1, n1);
+        u0 = a0; u1 = a1;
+        a0 = d0; a1 = d1;
+    }
 }
 
 static inline float conductance_scale(float K)
@@ -284,7 +358,7 @@ cudaError_t launch_diffuse_tiles(const DiffFrame *d_frames, int n_frames, int to
 cudaError_t launch_diffuse_stream(const DiffFrame &f, float lambda, float K, int mode,
                                   cudaStream_t s)
 {
-    dim3 grid((f.w + 31) / 32, (f.h + 7) / 8);
+    dim3 grid((f.w + 63) / 64, (f.h + 8 * STREAM_ROWS - 1) / (8 * STREAM_ROWS));
     const float c = conductance_scale(K);
     if (mode == 0)
         k_diffuse_stream<0><<<grid, dim3(32, 8), 0, s>>>(f, lambda, c);

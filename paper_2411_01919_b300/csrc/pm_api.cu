@@ -109,6 +109,8 @@ struct pm_ctx {
     cudaEvent_t kev[2 * MAX_PLANES] = {};
     float stage_ms[3] = {0, 0, 0};
     int pending_n = 0;
+    cudaStream_t gstream = nullptr;       // graph stream when the caller passes the legacy stream
+    cudaEvent_t gev[2] = {nullptr, nullptr};
     long long launches = 0;               // kernels launched by the last call
     int last_n = 0;                       // frames of the last call
 
@@ -382,7 +384,7 @@ pm_status enqueue_batch(pm_ctx *ctx, const Plan &pl, int n, int T, bool ransac, 
 {
     PM_CK(cudaMemcpyAsync(ctx->d_tables, ctx->h_tables, pl.bytes, cudaMemcpyHostToDevice, s));
     if (timed)
-        PM_CK(cudaEventRecord(ctx->ev[0], s));
+        PM_CK(record_event(ctx->ev[0], s));
     for (size_t k = 0; k < pl.diff_off.size(); ++k) {
         if (pl.diff_n[k] == 0)
             continue;
@@ -393,20 +395,20 @@ pm_status enqueue_batch(pm_ctx *ctx, const Plan &pl, int n, int T, bool ransac, 
         ctx->launches += 1;
     }
     if (timed)
-        PM_CK(cudaEventRecord(ctx->ev[1], s));
+        PM_CK(record_event(ctx->ev[1], s));
     if (!ransac)
         return PM_OK;
     PM_CK(launch_normals_batch(ctx->d_tables + pl.norm_off, n, pl.max_w, pl.max_h,
                                ctx->mp.normal_stencil, s));
     ctx->launches += 1;
     if (timed)
-        PM_CK(cudaEventRecord(ctx->ev[2], s));
+        PM_CK(record_event(ctx->ev[2], s));
     pm_status st = enqueue_ransac(ctx, reinterpret_cast<RFrame *>(ctx->d_tables + pl.rframe_off),
                                   n, pl.total_chunks, s);
     if (st != PM_OK)
         return st;
     if (timed)
-        PM_CK(cudaEventRecord(ctx->ev[3], s));
+        PM_CK(record_event(ctx->ev[3], s));
     PM_CK(cudaMemcpyAsync(ctx->h_state, ctx->at<RState>(ctx->lay.state), n * sizeof(RState),
                           cudaMemcpyDeviceToHost, s));
     PM_CK(cudaMemcpyAsync(ctx->h_planes, ctx->at<pm_plane>(ctx->lay.planes),
@@ -435,7 +437,28 @@ pm_status run_batch(pm_ctx *ctx, std::vector<FrameJob> &jobs, bool ransac, bool 
     if (st != PM_OK)
         return st;
     build_tables(ctx, jobs, T, ransac, true);
-    if (use_graph && s != nullptr) {
+    if (use_graph) {
+        // a stream that is being captured by the caller gets plain launches
+        // (they become part of the caller's graph)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        PM_CK(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone)
+            use_graph = false;
+    }
+    if (use_graph) {
+        // the legacy default stream cannot be captured: run the graph on the
+        // context's own stream, ordered after and before the caller's work
+        const bool bridge = s == nullptr;
+        if (bridge) {
+            if (!ctx->gstream) {
+                PM_CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+                PM_CK(cudaEventCreateWithFlags(&ctx->gev[0], cudaEventDisableTiming));
+                PM_CK(cudaEventCreateWithFlags(&ctx->gev[1], cudaEventDisableTiming));
+            }
+            PM_CK(cudaEventRecord(ctx->gev[0], s));
+            PM_CK(cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0));
+            s = ctx->gstream;
+        }
         std::vector<long long> sig = signature(jobs, T, ransac);
         sig.push_back(ctx->timing);
         sig.push_back(pl.dx);
@@ -470,6 +493,10 @@ pm_status run_batch(pm_ctx *ctx, std::vector<FrameJob> &jobs, bool ransac, bool 
         }
         PM_CK(cudaGraphLaunch(exec, s));
         ctx->launches = glaunch;
+        if (bridge) {
+            PM_CK(cudaEventRecord(ctx->gev[1], s));
+            PM_CK(cudaStreamWaitEvent(nullptr, ctx->gev[1], 0));
+        }
         return PM_OK;
     }
     return enqueue_batch(ctx, pl, n, T, ransac, ctx->timing == 1, s);
@@ -582,6 +609,11 @@ void pm_destroy(pm_ctx *ctx)
     cudaDeviceSynchronize();
     for (GraphEntry &g : ctx->graphs)
         cudaGraphExecDestroy(g.exec);
+    if (ctx->gstream)
+        cudaStreamDestroy(ctx->gstream);
+    for (int i = 0; i < 2; ++i)
+        if (ctx->gev[i])
+            cudaEventDestroy(ctx->gev[i]);
     for (int i = 0; i < 4; ++i)
         if (ctx->ev[i])
             cudaEventDestroy(ctx->ev[i]);
@@ -712,7 +744,7 @@ pm_status pm_process_frame(pm_ctx *ctx, const void *depth, int dtype, int w, int
     std::vector<FrameJob> jobs(1);
     jobs[0] = FrameJob{depth, dtype, w, h, pitch, (float)K->fx, (float)K->fy, (float)K->cx,
                        (float)K->cy, frame_idx, ctx->dp.iters, labels, nullptr};
-    st = run_batch(ctx, jobs, true, false, s);
+    st = run_batch(ctx, jobs, true, true, s);
     if (st != PM_OK)
         return st;
     PM_CK(cudaStreamSynchronize(s));
@@ -741,7 +773,7 @@ pm_status pm_process_frame_host(pm_ctx *ctx, const void *depth_host, int dtype, 
     std::vector<FrameJob> jobs(1);
     jobs[0] = FrameJob{d_in, dtype, w, h, (long long)w * es, (float)K->fx, (float)K->fy,
                        (float)K->cx, (float)K->cy, frame_idx, ctx->dp.iters, d_lab, nullptr};
-    st = run_batch(ctx, jobs, true, false, s);
+    st = run_batch(ctx, jobs, true, true, s);
     if (st != PM_OK)
         return st;
     if (labels_host)

@@ -18,6 +18,7 @@ constexpr int MAX_HYP = 2048;            // hypotheses per round (score kernel r
 constexpr int MAX_PLANES = 64;
 constexpr int NMOM = 9;                  // Sx Sy Sz Sxx Sxy Sxz Syy Syz Szz
 constexpr int GROUP = 4;                 // chunks per moment record
+constexpr int REMOVE_THREADS = 256;      // threads of the removal kernel (CHUNK / 4 candidates each)
 // per-group moment record: gated inliers then the other inliers, each NMOM
 // (sum, comp) float pairs, then two int counts (as float bit patterns), padded
 // to 40 words
@@ -158,6 +159,19 @@ cudaError_t launch_diffuse_stream(const DiffFrame &f, float lambda, float K, int
                                   cudaStream_t s);
 cudaError_t diffuse_init();   // opt the tile kernels into > 48 KB of shared memory
 pm_status set_last_error(pm_status s, const char *msg);
+
+// Record `e` on `s` as a real event: during stream capture a plain
+// cudaEventRecord only expresses a dependency, so captured timing events are
+// recorded as external event nodes of the graph.
+inline cudaError_t record_event(cudaEvent_t e, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t err = cudaStreamIsCapturing(s, &cs);
+    if (err != cudaSuccess)
+        return err;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                              : cudaEventRecord(e, s);
+}
 cudaError_t launch_normals(const float *depth, int w, int h, float fx, float fy, float cx,
                            float cy, int stencil, float *P, float *N, unsigned char *valid,
                            cudaStream_t s);

@@ -393,14 +393,15 @@ struct Mom {
     int n[2];
 };
 
-__device__ __forceinline__ void mom_add(Mom &m, int set, float x, float y, float z)
+template <int SET>
+__device__ __forceinline__ void mom_add(Mom &m, float x, float y, float z)
 {
     const float v[NMOM] = {x, y, z, __fmul_rn(x, x), __fmul_rn(x, y), __fmul_rn(x, z),
                            __fmul_rn(y, y), __fmul_rn(y, z), __fmul_rn(z, z)};
 #pragma unroll
     for (int k = 0; k < NMOM; ++k)
-        nadd(m.s[set][k], m.c[set][k], v[k]);
-    m.n[set] += 1;
+        nadd(m.s[SET][k], m.c[SET][k], v[k]);
+    m.n[SET] += 1;
 }
 
 __device__ __forceinline__ void mom_merge(Mom &a, const float *os, const float *oc, const int *on)
@@ -423,14 +424,15 @@ __device__ __forceinline__ void mom_merge(Mom &a, const float *os, const float *
 // group: one record of compensated moments of the inliers, centred at the
 // winner's first sample point, in two disjoint sets -- set 0: inliers whose
 // normal passes the refit gate, set 1: the other inliers.
-__global__ void __launch_bounds__(256) k_remove(RFrame *frames, int n, const int *chunk_base,
-                                                RParams prm, int round)
+__global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n,
+                                                           const int *chunk_base, RParams prm,
+                                                           int round)
 {
     __shared__ float sh_s[8][2 * NMOM], sh_c[8][2 * NMOM];
-    __shared__ int sh_n[8][2], sh_kept[8];
+    __shared__ int sh_n[8][2], sh_kept_w[CHUNK / REMOVE_THREADS][8];
     const int total = chunk_base[n];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
+    const int nwarps = REMOVE_THREADS >> 5;
     for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
         const int f = frame_of(chunk_base, n, wi);
         const int c0 = wi - chunk_base[f];
@@ -458,39 +460,59 @@ __global__ void __launch_bounds__(256) k_remove(RFrame *frames, int n, const int
         for (int c = c0; c < c1; ++c) {
             const int base = c * CHUNK;
             const int cnt = min(CHUNK, M - base);
-            int kept = 0;
-            for (int j = threadIdx.x; j < CHUNK; j += blockDim.x) {
-                bool keep = false;
-                if (j < cnt) {
-                    const float4 p = F.cpt[cur][base + j];
-                    if (is_inlier(pl, p.x, p.y, p.z, prm.thr2)) {
-                        const int pix = F.cidx[cur][base + j];
-                        F.labels[pix] = (short)round;
-                        int set = 1;
-                        if (F.N && (F.valid[pix] & 2)) {
-                            const float nx = F.N[pix], ny = F.N[npx + pix], nz = F.N[2 * npx + pix];
-                            const float dot = nx * pl.x + ny * pl.y + nz * pl.z;
-                            set = fabsf(dot) >= prm.cos_gate ? 0 : 1;
-                        }
-                        mom_add(m, set, __fsub_rn(p.x, p0.x), __fsub_rn(p.y, p0.y),
-                                __fsub_rn(p.z, p0.z));
-                    } else {
-                        keep = true;
-                    }
-                }
-                const unsigned word = __ballot_sync(0xffffffffu, keep);
+            // the PER_THREAD candidates of this thread, loaded together
+            constexpr int PER_THREAD = CHUNK / REMOVE_THREADS;
+            float4 p[PER_THREAD];
+            bool inl[PER_THREAD];
+#pragma unroll
+            for (int u = 0; u < PER_THREAD; ++u) {
+                const int j = threadIdx.x + u * REMOVE_THREADS;
+                p[u] = j < cnt ? F.cpt[cur][base + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < PER_THREAD; ++u) {
+                const int j = threadIdx.x + u * REMOVE_THREADS;
+                inl[u] = j < cnt && is_inlier(pl, p[u].x, p[u].y, p[u].z, prm.thr2);
+                const unsigned word = __ballot_sync(0xffffffffu, j < cnt && !inl[u]);
                 if (lane == 0) {
                     F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)] = word;
-                    kept += __popc(word);
+                    sh_kept_w[u][wid] = __popc(word);
                 }
             }
-            if (lane == 0)
-                sh_kept[wid] = kept;
+            int pix[PER_THREAD];
+            unsigned char vb[PER_THREAD];
+#pragma unroll
+            for (int u = 0; u < PER_THREAD; ++u) {
+                const int j = threadIdx.x + u * REMOVE_THREADS;
+                pix[u] = inl[u] ? F.cidx[cur][base + j] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < PER_THREAD; ++u)
+                vb[u] = (inl[u] && F.N) ? F.valid[pix[u]] : 0;
+#pragma unroll
+            for (int u = 0; u < PER_THREAD; ++u) {
+                if (!inl[u])
+                    continue;
+                F.labels[pix[u]] = (short)round;
+                bool gated = false;
+                if (vb[u] & 2) {
+                    const float nx = F.N[pix[u]], ny = F.N[npx + pix[u]], nz = F.N[2 * npx + pix[u]];
+                    const float dot = nx * pl.x + ny * pl.y + nz * pl.z;
+                    gated = fabsf(dot) >= prm.cos_gate;
+                }
+                const float qx = __fsub_rn(p[u].x, p0.x), qy = __fsub_rn(p[u].y, p0.y),
+                            qz = __fsub_rn(p[u].z, p0.z);
+                if (gated)
+                    mom_add<0>(m, qx, qy, qz);
+                else
+                    mom_add<1>(m, qx, qy, qz);
+            }
             __syncthreads();
             if (threadIdx.x == 0) {
                 int kk = 0;
-                for (int w = 0; w < nwarps; ++w)
-                    kk += sh_kept[w];
+                for (int u = 0; u < PER_THREAD; ++u)
+                    for (int w = 0; w < nwarps; ++w)
+                        kk += sh_kept_w[u][w];
                 F.kept[c] = kk;
             }
             __syncthreads();
@@ -710,7 +732,7 @@ cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream
     k_plan<<<1, 1024, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p.min_inliers, round);
     k_hyp<<<dim3((p.H + 127) / 128, L.n), 128, 0, s>>>(L.d_frames, p, round);
     if (ev_before)
-        cudaEventRecord(ev_before, s);
+        record_event(ev_before, s);
     const int hpt = (p.H + 127) / 128;
     if (hpt <= 1)
         k_score<1><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
@@ -723,9 +745,9 @@ cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream
     else
         k_score<16><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
     if (ev_after)
-        cudaEventRecord(ev_after, s);
+        record_event(ev_after, s);
     k_select<<<L.n, 1024, 0, s>>>(L.d_frames, p);
-    k_remove<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
+    k_remove<<<L.chunk_blocks, REMOVE_THREADS, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
     k_refit<<<L.n, 256, 0, s>>>(L.d_frames, p, round);
     if (!last)
         k_compact<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, round);

@@ -333,3 +333,19 @@ def test_argument_errors_raise():
             pipe.diffuse(torch.zeros((4, 4), dtype=torch.float64, device=DEV))
         with pytest.raises(PmError):
             pipe.process_batch([dict(depth=torch.zeros((4, 4), device=DEV), K=(0, 1, 0, 0))])
+
+
+def test_graph_replay_records_kernel_timing_events():
+    fr = frame('c1')
+    p = params('c1')
+    d = to_dev(fr.encoded)
+    with Pipeline(p, fr.w, fr.h, 2) as pipe:
+        pipe.set_timing(2)
+        batch = [dict(depth=d, K=fr.cam.intrinsics, frame_idx=i) for i in range(2)]
+        for s in (None, torch.cuda.Stream()):
+            with torch.cuda.stream(s or torch.cuda.current_stream()):
+                pipe.process_batch(batch, use_graph=True)       # capture
+                pipe.process_batch(batch, use_graph=True)       # replay
+            st = pipe.kernel_stats()
+            assert st['score_ms'] > 0 and st['score_pairs'] > 0
+            assert st['launches'] >= 3 + 7 * p.max_planes - 1
