@@ -319,7 +319,7 @@ def run_ours(args):
         if k > 0:
             e2e_ms.append(a.elapsed_time(b))
     h2d = sum(h.numel() * h.element_size() for h in host)
-    d2h = B * (64 * 48 + 320)
+    d2h = B * (64 * 48 + 336)   # planes + per-frame state read back by the call
     e2e = {'value': B / (statistics.mean(e2e_ms) * 1e-3), 'unit': 'frames/s',
            'h2d_bytes_per_step': h2d, 'd2h_bytes_per_step': d2h,
            'api': 'pm_process_batch after pinned-host copies'}

@@ -35,7 +35,7 @@ int elem_size(int dtype) { return dtype == PM_F32_M ? 4 : 2; }
 // Layout of the device scratch arena: every region is 256-byte aligned.
 struct Layout {
     size_t buf[2], depth, P, N, valid, labels, cidx[2], cpt[2], input;
-    size_t hyp, hyp_p0, counts, kept, keepbits, partial, state, planes, chunk_base;
+    size_t hyp, hyp_p0, counts, kept, keepbits, partial, state, planes, chunk_base, counter;
     size_t total;
 };
 
@@ -70,6 +70,7 @@ Layout make_layout(long long npx, int frames, int H, int max_chunks)
     L.state = take(F * sizeof(RState));
     L.planes = take(F * MAX_PLANES * sizeof(pm_plane));
     L.chunk_base = take((F + 1) * 4);
+    L.counter = take(4);
     L.total = off;
     return L;
 }
@@ -359,7 +360,10 @@ pm_status enqueue_ransac(pm_ctx *ctx, RFrame *d_rframes, int n, long long total_
     L.max_total_chunks = (int)total_chunks;
     L.prm = ransac_params(ctx);
     long long sb = (long long)ctx->sms * 8, cb = (long long)ctx->sms * 4;
-    L.score_blocks = (int)(total_chunks < sb ? total_chunks : sb);
+    L.d_counter = ctx->at<unsigned>(ctx->lay.counter);
+    L.fine_score = total_chunks < (long long)ctx->sms * 32;
+    const long long score_items = total_chunks * (L.fine_score ? 4 : 1);
+    L.score_blocks = (int)(score_items < sb ? score_items : sb);
     L.chunk_blocks = (int)(total_chunks < cb ? total_chunks : cb);
     if (L.score_blocks < 1)
         L.score_blocks = 1;
@@ -372,7 +376,7 @@ pm_status enqueue_ransac(pm_ctx *ctx, RFrame *d_rframes, int n, long long total_
         cudaEvent_t a = ctx->timing == 2 ? ctx->kev[2 * r] : nullptr;
         cudaEvent_t b = ctx->timing == 2 ? ctx->kev[2 * r + 1] : nullptr;
         PM_CK(ransac_round(L, r, last, s, a, b));
-        ctx->launches += RANSAC_ROUND_LAUNCHES - (last ? 1 : 0);
+        ctx->launches += ransac_round_launches(L.fine_score) - (last ? 1 : 0);
     }
     return PM_OK;
 }
@@ -584,7 +588,9 @@ pm_status pm_create(const pm_diffusion_params *dp, const pm_ransac_params *rp,
         return bail(fail(PM_ERR_OOM, "scratch arena of " + std::to_string(ctx->lay.total) +
                                          " bytes: " + cudaGetErrorString(e)));
     }
-    e = cudaMallocHost(&ctx->h_state, max_frames * sizeof(RState));
+    e = cudaMemset(ctx->arena + ctx->lay.counter, 0, 4);
+    if (e == cudaSuccess)
+        e = cudaMallocHost(&ctx->h_state, max_frames * sizeof(RState));
     if (e == cudaSuccess)
         e = cudaMallocHost(&ctx->h_planes, (size_t)max_frames * MAX_PLANES * sizeof(pm_plane));
     for (int i = 0; i < 4 && e == cudaSuccess; ++i)

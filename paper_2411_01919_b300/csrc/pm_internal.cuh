@@ -59,7 +59,8 @@ struct RState {
     int done;         // 1 once the frame stopped
     int n_planes;
     int nchunks;      // chunks of the current list (0 when done)
-    int chunk_base;   // first global work item of this frame in the current round
+    int score_done;   // scoring work items finished this round
+    int remove_done;  // removal groups finished this round
     int best_h;
     int best_count;
     float4 best_plane;
@@ -195,12 +196,16 @@ struct RansacLaunch {
     RParams prm;
     int score_blocks;     // persistent grid sizes
     int chunk_blocks;
+    unsigned *d_counter;  // grid-completion counter of the compaction kernel
+    bool fine_score;      // finer scoring work items (small batches)
 };
 cudaError_t ransac_init(const RansacLaunch &L, cudaStream_t s);
 // ev_score: optional event pair recorded around the scoring launch.
 cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream_t s,
                          cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
 constexpr int RANSAC_INIT_LAUNCHES = 3;
-constexpr int RANSAC_ROUND_LAUNCHES = 7;   // the last round skips compaction
+// launches per round: 4 with selection/refit fused (small batches), 6 without;
+// the last round skips compaction
+inline int ransac_round_launches(bool fine) { return fine ? 4 : 6; }
 
 }  // namespace pm

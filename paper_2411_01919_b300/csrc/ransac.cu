@@ -1,22 +1,26 @@
 // ransac.cu -- sequential multi-plane RANSAC (Sec. III-D, Eq. 3, Alg. 2) for
 // sm_103a, batched over frames.
 //
-// Per plane round r, for every frame f still running:
-//   k_plan    : candidate count -> chunk count; cross-frame prefix of chunks
+// One plane round of every frame still running takes four launches:
 //   k_hyp     : Philox4x64-10 -> three candidate indices -> FP32 plane (Alg. 2
 //               "select random subset of 3 points", "fit plane model")
 //   k_score   : every hypothesis against every candidate on FP32 CUDA cores
-//               (Alg. 2 inner parallel loop); per-thread integer counters,
-//               one atomic add per (CTA, hypothesis)
-//   k_select  : block argmax with the integer key (count, -index)
-//   k_remove  : label the winner's inliers, keep-bitmask of the rest,
-//               compensated-FP32 moments of the inliers (gated by normal and all)
-//   k_refit   : FP64 reduction of the per-chunk moments in a fixed order and
-//               FP64 3x3 eigen-solve -> plane
-//   k_compact : order-preserving compaction of the kept candidates
-// Work is split into chunks of CHUNK candidates; a frame's chunking never
-// depends on the other frames of the batch, and every reduction runs in a
-// fixed order, so a frame's result is bit-identical alone and in a batch.
+//               (Alg. 2 inner parallel loop); integer counters per thread, one
+//               atomic add per (work item, hypothesis).  The CTA that finishes
+//               a frame's last work item picks the frame's winner: the
+//               maximum count, ties to the lowest index (integer key).
+//   k_remove  : labels of the winner's inliers, keep bitmask of the rest,
+//               compensated-FP32 moments of the inliers; the CTA that finishes
+//               a frame's last group reduces the moments in FP64 in a fixed
+//               order and solves the 3x3 eigenproblem -> plane.
+//   k_compact : order-preserving compaction of the kept candidates; the last
+//               CTA of the grid plans the next round (candidate counts, stop
+//               rule, cross-frame prefix of chunks).
+// "Last CTA" is detected with a __threadfence() and an atomic counter; no CTA
+// ever waits for another.  Work is split into chunks of CHUNK candidates; a
+// frame's chunking never depends on the other frames of the batch, and every
+// reduction runs in a fixed order, so a frame's result is bit-identical alone
+// and in a batch.
 #include "pm_internal.cuh"
 
 namespace pm {
@@ -54,26 +58,28 @@ __device__ __forceinline__ int frame_of(const int *__restrict__ base, int n, int
 }
 
 // ---------------------------------------------------------------------------
-// round planning
+// round planning (run by one block of any size that is a multiple of 32)
 // ---------------------------------------------------------------------------
 
-// Exclusive scan of per-frame chunk counts over one block (n <= 1024).
-__device__ void scan_chunks(int *chunk_base, int n, int my)
+// Exclusive prefix over the threads of the block; *total gets the sum.
+__device__ int block_exscan(int v, int *total)
 {
     __shared__ int warp_tot[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int x = my;
+    const int nw = blockDim.x >> 5;
+    int x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         int y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o)
             x += y;
     }
+    __syncthreads();
     if (lane == 31)
         warp_tot[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        int t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+        int t = lane < nw ? warp_tot[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             int y = __shfl_up_sync(0xffffffffu, t, o);
@@ -83,50 +89,97 @@ __device__ void scan_chunks(int *chunk_base, int n, int my)
         warp_tot[lane] = t;
     }
     __syncthreads();
-    int incl = x + (wid > 0 ? warp_tot[wid - 1] : 0);
-    if ((int)threadIdx.x < n)
-        chunk_base[threadIdx.x] = incl - my;
-    if ((int)threadIdx.x == n - 1)
-        chunk_base[n] = incl;
+    const int incl = x + (wid > 0 ? warp_tot[wid - 1] : 0);
+    *total = warp_tot[nw - 1];
+    __syncthreads();
+    return incl - v;
 }
 
-// Initial plan: chunks over pixels; reset the per-frame state.
-__global__ void __launch_bounds__(1024) k_plan0(RFrame *frames, int n, int *chunk_base)
+// Per-frame chunk counts for the next round and their cross-frame prefix.
+// initial: chunks over the frame's pixels and a fresh per-frame state;
+// otherwise: the candidates kept by the last compaction, the stop rule, and
+// the candidate count of `round` recorded for the statistics.
+__device__ void plan_round(RFrame *frames, int n, int *chunk_base, int min_inliers, int round,
+                           bool initial)
 {
-    int my = 0;
-    if ((int)threadIdx.x < n) {
-        RFrame &F = frames[threadIdx.x];
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int f0 = threadIdx.x * per, f1 = min(f0 + per, n);
+    int mine = 0;
+    for (int f = f0; f < f1; ++f) {
+        RFrame &F = frames[f];
         RState *st = F.st;
-        st->M = 0;
-        st->M_next = 0;
-        st->done = 0;
-        st->n_planes = 0;
-        st->best_h = -1;
-        st->best_count = -1;
-        for (int r = 0; r < MAX_PLANES; ++r)
-            st->m_hist[r] = 0;
-        my = (F.npx + CHUNK - 1) / CHUNK;
-        st->nchunks = my;
+        int nc;
+        if (initial) {
+            st->M = 0;
+            st->M_next = 0;
+            st->done = 0;
+            st->n_planes = 0;
+            st->best_h = -1;
+            st->best_count = -1;
+            for (int r = 0; r < MAX_PLANES; ++r)
+                st->m_hist[r] = 0;
+            nc = (F.npx + CHUNK - 1) / CHUNK;
+        } else {
+            if (!st->done) {
+                st->M = __ldcg(&st->M_next);
+                if (st->M < 3 || st->M < min_inliers)
+                    st->done = 1;
+            }
+            nc = st->done ? 0 : (st->M + CHUNK - 1) / CHUNK;
+            st->m_hist[round] = st->done ? 0 : st->M;
+        }
+        st->nchunks = nc;
+        mine += nc;
     }
-    scan_chunks(chunk_base, n, my);
+    int total;
+    int off = block_exscan(mine, &total);
+    for (int f = f0; f < f1; ++f) {
+        chunk_base[f] = off;
+        off += frames[f].st->nchunks;
+    }
+    if (threadIdx.x == 0)
+        chunk_base[n] = total;
 }
 
-__global__ void __launch_bounds__(1024) k_plan(RFrame *frames, int n, int *chunk_base,
-                                               int min_inliers, int round)
+__global__ void __launch_bounds__(1024) k_plan0(RFrame *frames, int n, int *chunk_base,
+                                                unsigned *grid_counter)
 {
-    int my = 0;
-    if ((int)threadIdx.x < n) {
-        RState *st = frames[threadIdx.x].st;
-        if (!st->done) {
-            st->M = st->M_next;
-            if (st->M < 3 || st->M < min_inliers)
-                st->done = 1;
-        }
-        my = st->done ? 0 : (st->M + CHUNK - 1) / CHUNK;
-        st->nchunks = my;
-        st->m_hist[round] = st->done ? 0 : st->M;
+    if (threadIdx.x == 0)
+        *grid_counter = 0u;
+    plan_round(frames, n, chunk_base, 0, 0, true);
+}
+
+// Whether this CTA is the last of the grid to get here (then after a fence it
+// sees every other CTA's writes).  Resets the counter for the next launch.
+__device__ bool last_cta_of_grid(unsigned *counter)
+{
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(counter, 1u);
+        last = prev == gridDim.x - 1;
+        if (last)
+            *counter = 0u;
     }
-    scan_chunks(chunk_base, n, my);
+    __syncthreads();
+    if (last)
+        __threadfence();
+    return last;
+}
+
+// Whether this CTA finished the last of the `items` work items of a frame.
+__device__ bool last_item_of_frame(int *counter, int items)
+{
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        last = atomicAdd(counter, 1) == items - 1;
+    __syncthreads();
+    if (last)
+        __threadfence();
+    return last;
 }
 
 // ---------------------------------------------------------------------------
@@ -134,6 +187,7 @@ __global__ void __launch_bounds__(1024) k_plan(RFrame *frames, int n, int *chunk
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_mark0(RFrame *frames, int n, const int *chunk_base)
 {
+    __shared__ int wsum[8];
     const int total = chunk_base[n];
     for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
         const int f = frame_of(chunk_base, n, wi);
@@ -154,7 +208,6 @@ __global__ void __launch_bounds__(256) k_mark0(RFrame *frames, int n, const int 
                 kept += __popc(word);
             }
         }
-        __shared__ int wsum[8];
         if ((threadIdx.x & 31) == 0)
             wsum[threadIdx.x >> 5] = kept;
         __syncthreads();
@@ -224,28 +277,23 @@ __device__ void compact_chunk(const RFrame &F, int c, int nchunks, int src, int 
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_compact0(RFrame *frames, int n, const int *chunk_base)
+// Compaction of every chunk; the last CTA of the grid plans round `next`.
+// src_image: round 0 (the source list is the pixel array itself).
+__global__ void __launch_bounds__(256) k_compact(RFrame *frames, int n, int *chunk_base,
+                                                 int round, bool src_image, int next,
+                                                 int min_inliers, unsigned *grid_counter)
 {
     const int total = chunk_base[n];
-    for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
-        const int f = frame_of(chunk_base, n, wi);
-        const RFrame &F = frames[f];
-        compact_chunk(F, wi - chunk_base[f], F.st->nchunks, 0, 0, true);
-    }
-}
-
-__global__ void __launch_bounds__(256) k_compact(RFrame *frames, int n, const int *chunk_base,
-                                                 int round)
-{
-    const int total = chunk_base[n];
-    const int src = round & 1, dst = src ^ 1;
+    const int src = round & 1, dst = src_image ? 0 : src ^ 1;
     for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
         const int f = frame_of(chunk_base, n, wi);
         const RFrame &F = frames[f];
         if (F.st->done)
             continue;
-        compact_chunk(F, wi - chunk_base[f], F.st->nchunks, src, dst, false);
+        compact_chunk(F, wi - chunk_base[f], F.st->nchunks, src, dst, src_image);
     }
+    if (last_cta_of_grid(grid_counter))
+        plan_round(frames, n, chunk_base, min_inliers, next, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -254,9 +302,11 @@ __global__ void __launch_bounds__(256) k_compact(RFrame *frames, int n, const in
 __global__ void __launch_bounds__(128) k_hyp(RFrame *frames, RParams prm, int round)
 {
     const RFrame &F = frames[blockIdx.y];
-    const RState *st = F.st;
+    RState *st = F.st;
     if (st->done)
         return;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        st->score_done = 0;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= prm.H)
         return;
@@ -276,36 +326,84 @@ __global__ void __launch_bounds__(128) k_hyp(RFrame *frames, RParams prm, int ro
 }
 
 // ---------------------------------------------------------------------------
-// scoring: HPT hypotheses per thread in registers, the candidate chunk in
-// shared memory (one broadcast 16-byte load per point).  Per pair: the three
-// residual FMAs, one FMA for r*r - thr^2, and one integer add of that value's
-// sign bit, which is set iff it is negative (an exact zero rounds to +0, a
-// degenerate plane gives +inf): the same decision as is_inlier().
-// (Packed f32x2 FMAs were measured slower here: they issue to one FMA pipe.)
+// selection: argmax of (count, -h) by one block
 // ---------------------------------------------------------------------------
-template <int HPT>
+__device__ void select_winner(const RFrame &F, const RParams &prm)
+{
+    __shared__ unsigned long long wk[32];
+    RState *st = F.st;
+    unsigned long long key = 0;
+    for (int h = threadIdx.x; h < prm.H; h += blockDim.x) {
+        const int cnt = __ldcg(F.counts + h);
+        const unsigned long long k = ((unsigned long long)(unsigned)(cnt + 1) << 32) |
+                                     (unsigned long long)(0xffffffffu - (unsigned)h);
+        key = k > key ? k : key;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long y = __shfl_xor_sync(0xffffffffu, key, o);
+        key = y > key ? y : key;
+    }
+    if ((threadIdx.x & 31) == 0)
+        wk[threadIdx.x >> 5] = key;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            key = wk[w] > key ? wk[w] : key;
+        const int best_h = (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
+        const int best_count = (int)(key >> 32) - 1;
+        st->remove_done = 0;
+        if (best_count < prm.min_inliers || best_count < 3) {
+            st->done = 1;
+        } else {
+            st->best_h = best_h;
+            st->best_count = best_count;
+            st->best_plane = __ldcg(F.hyp + best_h);
+            st->p0 = __ldcg(F.hyp_p0 + best_h);
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// scoring.  A work item is (chunk, sub-chunk, hypothesis block): SUBS
+// sub-chunks of CHUNK / SUBS candidates, NHB blocks of 128 * HPT hypotheses.
+// HPT hypotheses per thread live in registers, the sub-chunk in shared memory
+// (one broadcast 16-byte load per point).  Per pair: the three residual FMAs,
+// one FMA for r*r - thr^2, and one integer add of that value's sign bit,
+// which is set iff it is negative (an exact zero rounds to +0, a degenerate
+// plane gives +inf): the same decision as is_inlier().  (Packed f32x2 FMAs
+// were measured slower here: they issue to one FMA pipe.)
+// ---------------------------------------------------------------------------
+template <int HPT, int NHB, int SUBS, bool FUSE>
 __global__ void __launch_bounds__(128) k_score(RFrame *frames, int n, const int *chunk_base,
                                                RParams prm, int round)
 {
-    __shared__ float4 pts[CHUNK];
-    const int total = chunk_base[n];
+    constexpr int SUB = CHUNK / SUBS;
+    constexpr int PER = NHB * SUBS;
+    __shared__ float4 pts[SUB];
+    const int total = chunk_base[n] * PER;
     const float nthr2 = -prm.thr2;
     const float4 none = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
-    for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int wi = it / PER, rem = it - wi * PER;
+        const int sub = rem / NHB, hb = rem - sub * NHB;
         const int f = frame_of(chunk_base, n, wi);
         const RFrame &F = frames[f];
+        RState *st = F.st;
         const int c = wi - chunk_base[f];
-        const int M = F.st->M;
-        const int base = c * CHUNK;
-        const int cnt = min(CHUNK, M - base);
+        const int M = st->M;
+        const int base = c * CHUNK + sub * SUB;
+        const int cnt = max(0, min(SUB, M - base));
         const float4 *src = F.cpt[round & 1] + base;
         __syncthreads();
         for (int j = threadIdx.x; j < cnt; j += blockDim.x)
             pts[j] = src[j];
         float4 pl[HPT];
+        const int h0 = hb * (128 * HPT) + threadIdx.x;
 #pragma unroll
         for (int k = 0; k < HPT; ++k) {
-            const int h = k * blockDim.x + threadIdx.x;
+            const int h = h0 + k * 128;
             pl[k] = h < prm.H ? F.hyp[h] : none;
         }
         __syncthreads();
@@ -326,55 +424,17 @@ __global__ void __launch_bounds__(128) k_score(RFrame *frames, int n, const int 
         }
 #pragma unroll
         for (int k = 0; k < HPT; ++k) {
-            const int h = k * blockDim.x + threadIdx.x;
+            const int h = h0 + k * 128;
             if (h < prm.H && acc[k] > 0u)
                 atomicAdd(F.counts + h, (int)acc[k]);
         }
+        if (FUSE && last_item_of_frame(&st->score_done, st->nchunks * PER))
+            select_winner(F, prm);
     }
 }
 
 // ---------------------------------------------------------------------------
-// selection: argmax of (count, -h)
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_select(RFrame *frames, RParams prm)
-{
-    const RFrame &F = frames[blockIdx.x];
-    RState *st = F.st;
-    if (st->done)
-        return;
-    unsigned long long key = 0;
-    for (int h = threadIdx.x; h < prm.H; h += blockDim.x) {
-        unsigned long long k = ((unsigned long long)(unsigned)(F.counts[h] + 1) << 32) |
-                               (unsigned long long)(0xffffffffu - (unsigned)h);
-        key = k > key ? k : key;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long y = __shfl_xor_sync(0xffffffffu, key, o);
-        key = y > key ? y : key;
-    }
-    __shared__ unsigned long long wk[32];
-    if ((threadIdx.x & 31) == 0)
-        wk[threadIdx.x >> 5] = key;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-            key = wk[w] > key ? wk[w] : key;
-        const int best_h = (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
-        const int best_count = (int)(key >> 32) - 1;
-        if (best_count < prm.min_inliers || best_count < 3) {
-            st->done = 1;
-        } else {
-            st->best_h = best_h;
-            st->best_count = best_count;
-            st->best_plane = F.hyp[best_h];
-            st->p0 = F.hyp_p0[best_h];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// removal + compensated moments
+// removal + compensated moments, refit by the last CTA of each frame
 // ---------------------------------------------------------------------------
 
 // Neumaier compensated accumulation in FP32.
@@ -417,16 +477,162 @@ __device__ __forceinline__ void mom_merge(Mom &a, const float *os, const float *
     }
 }
 
+// ---------------------------------------------------------------------------
+// refit: FP64 reduction + smallest eigenpair of the 3x3 covariance.
+// The smallest eigenvalue is the smallest root of the characteristic cubic
+//   f(l) = det - c1 l + tr l^2 - l^3   (c1 = sum of the principal 2x2 minors),
+// found by Newton's method from l = 0: on [0, l_min] f is decreasing and
+// convex (f'' = 2 tr - 6 l > 0 below tr / 3), so the iterates rise
+// monotonically to l_min.  Its eigenvector is orthogonal to every row of
+// A - l_min I: the largest of the three pairwise cross products of the rows.
+// No transcendental functions: FP64 is a narrow unit on this GPU.
+// ---------------------------------------------------------------------------
+__device__ void smallest_eigenpair(const double a[3][3], double &lmin, double v[3])
+{
+    const double tr = a[0][0] + a[1][1] + a[2][2];
+    const double c1 = a[0][0] * a[1][1] + a[0][0] * a[2][2] + a[1][1] * a[2][2] -
+                      a[0][1] * a[0][1] - a[0][2] * a[0][2] - a[1][2] * a[1][2];
+    const double det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[1][2]) -
+                       a[0][1] * (a[0][1] * a[2][2] - a[1][2] * a[0][2]) +
+                       a[0][2] * (a[0][1] * a[1][2] - a[1][1] * a[0][2]);
+    double l = 0.0;
+    for (int it = 0; it < 64; ++it) {
+        const double f = det - l * (c1 - l * (tr - l));
+        const double fp = -c1 + l * (2.0 * tr - 3.0 * l);
+        if (!(fp < 0.0))
+            break;
+        const double nl = l - f / fp;
+        if (!(nl > l))
+            break;
+        l = nl;
+    }
+    lmin = l;
+    double r[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            r[i][j] = a[i][j] - (i == j ? l : 0.0);
+    double best = -1.0;
+    v[0] = 0.0;
+    v[1] = 0.0;
+    v[2] = 1.0;
+    for (int pq = 0; pq < 3; ++pq) {
+        const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+        const double x = r[p][1] * r[q][2] - r[p][2] * r[q][1];
+        const double y = r[p][2] * r[q][0] - r[p][0] * r[q][2];
+        const double z = r[p][0] * r[q][1] - r[p][1] * r[q][0];
+        const double n2 = x * x + y * y + z * z;
+        if (n2 > best) {
+            best = n2;
+            v[0] = x;
+            v[1] = y;
+            v[2] = z;
+        }
+    }
+    const double ln = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (ln > 0.0) {
+        v[0] /= ln;
+        v[1] /= ln;
+        v[2] /= ln;
+    } else {
+        v[0] = 0.0;
+        v[1] = 0.0;
+        v[2] = 1.0;
+    }
+}
+
+// FP64 reduction of a frame's group records in a fixed order and the refit;
+// run by one block of REMOVE_THREADS threads.
+__device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
+{
+    RState *st = F.st;
+    const int ngroups = (st->nchunks + GROUP - 1) / GROUP;
+    double acc[2 * NMOM];
+    long long cnt[2] = {0, 0};
+#pragma unroll
+    for (int k = 0; k < 2 * NMOM; ++k)
+        acc[k] = 0.0;
+    for (int c = threadIdx.x; c < ngroups; c += blockDim.x) {
+        const float *rec = F.partial + (long long)c * PART_WORDS;
+#pragma unroll
+        for (int k = 0; k < 2 * NMOM; ++k)
+            acc[k] += (double)__ldcg(rec + 2 * k) + (double)__ldcg(rec + 2 * k + 1);
+        cnt[0] += __float_as_int(__ldcg(rec + 36));
+        cnt[1] += __float_as_int(__ldcg(rec + 37));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 2 * NMOM; ++k)
+            acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+        cnt[0] += __shfl_down_sync(0xffffffffu, cnt[0], o);
+        cnt[1] += __shfl_down_sync(0xffffffffu, cnt[1], o);
+    }
+    __shared__ double sacc[8][2 * NMOM];
+    __shared__ long long scnt[8][2];
+    if (lane == 0) {
+        for (int k = 0; k < 2 * NMOM; ++k)
+            sacc[wid][k] = acc[k];
+        scnt[wid][0] = cnt[0];
+        scnt[wid][1] = cnt[1];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0)
+        return;   // (the caller does not synchronise the block after this)
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        for (int k = 0; k < 2 * NMOM; ++k)
+            acc[k] += sacc[w][k];
+        cnt[0] += scnt[w][0];
+        cnt[1] += scnt[w][1];
+    }
+    // gated inliers if at least 3 pass the gate, else all inliers (set 0 + set 1)
+    const bool gated = cnt[0] >= 3;
+    const long long nsel = gated ? cnt[0] : cnt[0] + cnt[1];
+    double S[NMOM];
+    for (int k = 0; k < NMOM; ++k)
+        S[k] = gated ? acc[k] : acc[k] + acc[NMOM + k];
+    const double nn = (double)nsel;
+    const double mx = S[0] / nn, my = S[1] / nn, mz = S[2] / nn;
+    double a[3][3], lmin, nv[3];
+    a[0][0] = S[3] / nn - mx * mx;
+    a[0][1] = a[1][0] = S[4] / nn - mx * my;
+    a[0][2] = a[2][0] = S[5] / nn - mx * mz;
+    a[1][1] = S[6] / nn - my * my;
+    a[1][2] = a[2][1] = S[7] / nn - my * mz;
+    a[2][2] = S[8] / nn - mz * mz;
+    smallest_eigenpair(a, lmin, nv);
+    double n0 = nv[0], n1 = nv[1], n2 = nv[2];
+    const float4 p0 = st->p0;
+    const double cx = (double)p0.x + mx, cy = (double)p0.y + my, cz = (double)p0.z + mz;
+    double d = -(n0 * cx + n1 * cy + n2 * cz);
+    if (d < 0.0) {
+        n0 = -n0; n1 = -n1; n2 = -n2; d = -d;
+    }
+    pm_plane &out = F.planes[st->n_planes];
+    out.n[0] = n0;
+    out.n[1] = n1;
+    out.n[2] = n2;
+    out.d = d;
+    out.n_inliers = st->best_count;
+    out.n_refit = (int)nsel;
+    out.rms = (float)sqrt(fmax(lmin, 0.0));
+    out.hyp_index = st->best_h;
+    st->n_planes += 1;
+    if (round + 1 >= prm.max_planes)
+        st->done = 1;
+}
+
 // Removal of the winner's inliers.  A work item is a group of GROUP chunks of
 // one frame (group g = chunks [g*GROUP, g*GROUP + GROUP)), fixed by the
 // frame's own candidate count, so its moment record does not depend on the
 // rest of the batch.  Per chunk: labels, keep bitmask and kept count.  Per
 // group: one record of compensated moments of the inliers, centred at the
 // winner's first sample point, in two disjoint sets -- set 0: inliers whose
-// normal passes the refit gate, set 1: the other inliers.
+// normal passes the refit gate, set 1: the other inliers.  The CTA that
+// finishes a frame's last group refits the frame's plane.
 __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n,
                                                            const int *chunk_base, RParams prm,
-                                                           int round)
+                                                           int round, bool fuse_refit)
 {
     __shared__ float sh_s[8][2 * NMOM], sh_c[8][2 * NMOM];
     __shared__ int sh_n[8][2], sh_kept_w[CHUNK / REMOVE_THREADS][8];
@@ -439,7 +645,7 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
         if (c0 % GROUP)
             continue;
         const RFrame &F = frames[f];
-        const RState *st = F.st;
+        RState *st = F.st;
         if (st->done)
             continue;
         const int M = st->M;
@@ -564,154 +770,29 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
                 nn += sh_n[w][set];
             rec[36 + set] = __int_as_float(nn);
         }
+        if (fuse_refit && last_item_of_frame(&st->remove_done, (st->nchunks + GROUP - 1) / GROUP))
+            refit_frame(F, prm, round);
         __syncthreads();
     }
 }
 
-// ---------------------------------------------------------------------------
-// refit: FP64 reduction + smallest eigenpair of the 3x3 covariance.
-// The smallest eigenvalue is the smallest root of the characteristic cubic
-//   f(l) = det - c1 l + tr l^2 - l^3   (c1 = sum of the principal 2x2 minors),
-// found by Newton's method from l = 0: on [0, l_min] f is decreasing and
-// convex (f'' = 2 tr - 6 l > 0 below tr / 3), so the iterates rise
-// monotonically to l_min.  Its eigenvector is orthogonal to every row of
-// A - l_min I: the largest of the three pairwise cross products of the rows.
-// No transcendental functions: FP64 is a narrow unit on this GPU.
-// ---------------------------------------------------------------------------
-__device__ void smallest_eigenpair(const double a[3][3], double &lmin, double v[3])
-{
-    const double tr = a[0][0] + a[1][1] + a[2][2];
-    const double c1 = a[0][0] * a[1][1] + a[0][0] * a[2][2] + a[1][1] * a[2][2] -
-                      a[0][1] * a[0][1] - a[0][2] * a[0][2] - a[1][2] * a[1][2];
-    const double det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[1][2]) -
-                       a[0][1] * (a[0][1] * a[2][2] - a[1][2] * a[0][2]) +
-                       a[0][2] * (a[0][1] * a[1][2] - a[1][1] * a[0][2]);
-    double l = 0.0;
-    for (int it = 0; it < 64; ++it) {
-        const double f = det - l * (c1 - l * (tr - l));
-        const double fp = -c1 + l * (2.0 * tr - 3.0 * l);
-        if (!(fp < 0.0))
-            break;
-        const double nl = l - f / fp;
-        if (!(nl > l))
-            break;
-        l = nl;
-    }
-    lmin = l;
-    double r[3][3];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            r[i][j] = a[i][j] - (i == j ? l : 0.0);
-    double best = -1.0;
-    v[0] = 0.0;
-    v[1] = 0.0;
-    v[2] = 1.0;
-    for (int pq = 0; pq < 3; ++pq) {
-        const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
-        const double x = r[p][1] * r[q][2] - r[p][2] * r[q][1];
-        const double y = r[p][2] * r[q][0] - r[p][0] * r[q][2];
-        const double z = r[p][0] * r[q][1] - r[p][1] * r[q][0];
-        const double n2 = x * x + y * y + z * z;
-        if (n2 > best) {
-            best = n2;
-            v[0] = x;
-            v[1] = y;
-            v[2] = z;
-        }
-    }
-    const double ln = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    if (ln > 0.0) {
-        v[0] /= ln;
-        v[1] /= ln;
-        v[2] /= ln;
-    } else {
-        v[0] = 0.0;
-        v[1] = 0.0;
-        v[2] = 1.0;
-    }
-}
-
-__global__ void __launch_bounds__(256) k_refit(RFrame *frames, RParams prm, int round)
+// Large batches: selection and refit as their own launches, one block per
+// frame (fusing them costs every scoring / removal work item a fence that
+// waits for its atomics, which a batch with many work items per CTA feels).
+__global__ void __launch_bounds__(1024) k_select(RFrame *frames, RParams prm)
 {
     const RFrame &F = frames[blockIdx.x];
-    RState *st = F.st;
-    if (st->done)
+    if (F.st->done)
         return;
-    const int ngroups = (st->nchunks + GROUP - 1) / GROUP;
-    double acc[2 * NMOM];
-    long long cnt[2] = {0, 0};
-#pragma unroll
-    for (int k = 0; k < 2 * NMOM; ++k)
-        acc[k] = 0.0;
-    for (int c = threadIdx.x; c < ngroups; c += blockDim.x) {
-        const float *rec = F.partial + (long long)c * PART_WORDS;
-#pragma unroll
-        for (int k = 0; k < 2 * NMOM; ++k)
-            acc[k] += (double)rec[2 * k] + (double)rec[2 * k + 1];
-        cnt[0] += __float_as_int(rec[36]);
-        cnt[1] += __float_as_int(rec[37]);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int k = 0; k < 2 * NMOM; ++k)
-            acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
-        cnt[0] += __shfl_down_sync(0xffffffffu, cnt[0], o);
-        cnt[1] += __shfl_down_sync(0xffffffffu, cnt[1], o);
-    }
-    __shared__ double sacc[8][2 * NMOM];
-    __shared__ long long scnt[8][2];
-    if (lane == 0) {
-        for (int k = 0; k < 2 * NMOM; ++k)
-            sacc[wid][k] = acc[k];
-        scnt[wid][0] = cnt[0];
-        scnt[wid][1] = cnt[1];
-    }
-    __syncthreads();
-    if (threadIdx.x != 0)
+    select_winner(F, prm);
+}
+
+__global__ void __launch_bounds__(REMOVE_THREADS) k_refit(RFrame *frames, RParams prm, int round)
+{
+    const RFrame &F = frames[blockIdx.x];
+    if (F.st->done)
         return;
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-        for (int k = 0; k < 2 * NMOM; ++k)
-            acc[k] += sacc[w][k];
-        cnt[0] += scnt[w][0];
-        cnt[1] += scnt[w][1];
-    }
-    // gated inliers if at least 3 pass the gate, else all inliers (set 0 + set 1)
-    const bool gated = cnt[0] >= 3;
-    const long long nsel = gated ? cnt[0] : cnt[0] + cnt[1];
-    double S[NMOM];
-    for (int k = 0; k < NMOM; ++k)
-        S[k] = gated ? acc[k] : acc[k] + acc[NMOM + k];
-    const double nn = (double)nsel;
-    const double mx = S[0] / nn, my = S[1] / nn, mz = S[2] / nn;
-    double a[3][3], lmin, nv[3];
-    a[0][0] = S[3] / nn - mx * mx;
-    a[0][1] = a[1][0] = S[4] / nn - mx * my;
-    a[0][2] = a[2][0] = S[5] / nn - mx * mz;
-    a[1][1] = S[6] / nn - my * my;
-    a[1][2] = a[2][1] = S[7] / nn - my * mz;
-    a[2][2] = S[8] / nn - mz * mz;
-    smallest_eigenpair(a, lmin, nv);
-    double n0 = nv[0], n1 = nv[1], n2 = nv[2];
-    const float4 p0 = st->p0;
-    const double cx = (double)p0.x + mx, cy = (double)p0.y + my, cz = (double)p0.z + mz;
-    double d = -(n0 * cx + n1 * cy + n2 * cz);
-    if (d < 0.0) {
-        n0 = -n0; n1 = -n1; n2 = -n2; d = -d;
-    }
-    pm_plane &out = F.planes[st->n_planes];
-    out.n[0] = n0;
-    out.n[1] = n1;
-    out.n[2] = n2;
-    out.d = d;
-    out.n_inliers = st->best_count;
-    out.n_refit = (int)nsel;
-    out.rms = (float)sqrt(fmax(lmin, 0.0));
-    out.hyp_index = st->best_h;
-    st->n_planes += 1;
-    if (round + 1 >= prm.max_planes)
-        st->done = 1;
+    refit_frame(F, prm, round);
 }
 
 // ---------------------------------------------------------------------------
@@ -719,38 +800,53 @@ __global__ void __launch_bounds__(256) k_refit(RFrame *frames, RParams prm, int 
 // ---------------------------------------------------------------------------
 cudaError_t ransac_init(const RansacLaunch &L, cudaStream_t s)
 {
-    k_plan0<<<1, 1024, 0, s>>>(L.d_frames, L.n, L.d_chunk_base);
+    k_plan0<<<1, 1024, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, L.d_counter);
     k_mark0<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base);
-    k_compact0<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base);
+    k_compact<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, 0, true, 0,
+                                             L.prm.min_inliers, L.d_counter);
     return cudaGetLastError();
+}
+
+template <int HPT, int NHB, int SUBS, bool FUSE>
+static void launch_score(const RansacLaunch &L, int round, cudaStream_t s)
+{
+    k_score<HPT, NHB, SUBS, FUSE><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n,
+                                                                 L.d_chunk_base, L.prm, round);
 }
 
 cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream_t s,
                          cudaEvent_t ev_before, cudaEvent_t ev_after)
 {
     const RParams &p = L.prm;
-    k_plan<<<1, 1024, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p.min_inliers, round);
     k_hyp<<<dim3((p.H + 127) / 128, L.n), 128, 0, s>>>(L.d_frames, p, round);
     if (ev_before)
         record_event(ev_before, s);
-    const int hpt = (p.H + 127) / 128;
-    if (hpt <= 1)
-        k_score<1><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
-    else if (hpt <= 2)
-        k_score<2><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
-    else if (hpt <= 4)
-        k_score<4><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
-    else if (hpt <= 8)
-        k_score<8><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
-    else
-        k_score<16><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
+    // coarse work items (whole chunks, all hypotheses per CTA) when there are
+    // enough of them to fill the GPU; finer ones (half chunks, half of the
+    // hypotheses) for small batches and late rounds
+    // small batches also fold the selection into the scoring launch and the
+    // refit into the removal launch
+    const bool fine = L.fine_score;
+    if (p.H <= 256) {
+        if (fine) launch_score<2, 1, 2, true>(L, round, s); else launch_score<2, 1, 1, false>(L, round, s);
+    } else if (p.H <= 512) {
+        if (fine) launch_score<4, 1, 2, true>(L, round, s); else launch_score<4, 1, 1, false>(L, round, s);
+    } else if (p.H <= 1024) {
+        if (fine) launch_score<4, 2, 2, true>(L, round, s); else launch_score<8, 1, 1, false>(L, round, s);
+    } else {
+        if (fine) launch_score<8, 2, 2, true>(L, round, s); else launch_score<16, 1, 1, false>(L, round, s);
+    }
     if (ev_after)
         record_event(ev_after, s);
-    k_select<<<L.n, 1024, 0, s>>>(L.d_frames, p);
-    k_remove<<<L.chunk_blocks, REMOVE_THREADS, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
-    k_refit<<<L.n, 256, 0, s>>>(L.d_frames, p, round);
+    if (!fine)
+        k_select<<<L.n, 1024, 0, s>>>(L.d_frames, p);
+    k_remove<<<L.chunk_blocks, REMOVE_THREADS, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round,
+                                                       fine);
+    if (!fine)
+        k_refit<<<L.n, REMOVE_THREADS, 0, s>>>(L.d_frames, p, round);
     if (!last)
-        k_compact<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, round);
+        k_compact<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, round, false,
+                                                 round + 1, p.min_inliers, L.d_counter);
     return cudaGetLastError();
 }
 
