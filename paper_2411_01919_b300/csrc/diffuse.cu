@@ -18,10 +18,14 @@
 //    frame of a batch form one grid (a frame table maps tile -> frame).
 //  * k_diffuse_stream: one iteration per launch over one frame, one pass over
 //    HBM.
-// Holes and pixels outside the image are 0 in every buffer; the flux across a
-// link is 0 when either end is 0, which is the ghost rule J_q = I_p of the
-// oracle.  The first launch decodes the sensor encoding on the fly; the last
-// writes FP32 depth (the hi part, which is hi + lo rounded to nearest).
+// Holes and pixels outside the image hold the sentinel HOLE = 1e30 in the
+// iterate: across a link to it the difference x is about 1e30, x*x overflows
+// to +inf, 2^(x*x*c) is exactly +0 and so is the flux g(x) x -- the ghost rule
+// J_q = I_p of the oracle (no flux across a hole or the border) without a
+// branch; a hole receives only zero fluxes and keeps its value.  The first
+// launch decodes the sensor encoding on the fly (holes -> HOLE); the last
+// writes FP32 depth (the hi part, which is hi + lo rounded to nearest; HOLE
+// -> 0).
 #include "pm_internal.cuh"
 
 namespace pm {
@@ -53,23 +57,23 @@ __device__ __forceinline__ float2 pair_add(float2 p, float a)
     return make_float2(h2, __fsub_rn(l, __fsub_rn(h2, s)));
 }
 
+constexpr float HOLE = 1e30f;
+
 // Flux into p from neighbour q across one link: g(x) x with x = I_q - I_p and
 // g(x) = exp(-(x/K)^2) = 2^(x^2 * c), c = -log2(e)/K^2.  Exactly antisymmetric
-// in (p, q).  0 when q is a hole or outside the image.
+// in (p, q) (the negation of x is exact, and so are x*x and g), and exactly
+// zero when either end is HOLE.
 __device__ __forceinline__ float link_flux(float2 Ip, float2 Iq, float c)
 {
     const float x = pair_diff(Iq, Ip);
     const float g = ex2_approx(__fmul_rn(__fmul_rn(x, x), c));
-    const float f = __fmul_rn(g, x);
-    return (Iq.x == 0.0f) ? 0.0f : f;
+    return __fmul_rn(g, x);
 }
 
 // mode 0 (PM4): I' = I + lambda * (((f_N + f_S) + f_W) + f_E)
 __device__ __forceinline__ float2 update_pm4(float2 Ip, float2 In, float2 Is, float2 Iw,
                                              float2 Ie, float lam, float c)
 {
-    if (Ip.x == 0.0f)
-        return make_float2(0.0f, 0.0f);
     const float s = __fadd_rn(__fadd_rn(__fadd_rn(link_flux(Ip, In, c), link_flux(Ip, Is, c)),
                                         link_flux(Ip, Iw, c)), link_flux(Ip, Ie, c));
     return pair_add(Ip, __fmul_rn(lam, s));
@@ -80,10 +84,10 @@ __device__ __forceinline__ float2 update_pm4(float2 Ip, float2 In, float2 Is, fl
 __device__ __forceinline__ float2 update_alg1(float2 Ip, float2 In, float2 Is, float2 Iw,
                                               float2 Ie, float lam, float c)
 {
-    if (Ip.x == 0.0f)
-        return make_float2(0.0f, 0.0f);
-    const float2 Jn = In.x == 0.0f ? Ip : In, Js = Is.x == 0.0f ? Ip : Is;
-    const float2 Jw = Iw.x == 0.0f ? Ip : Iw, Je = Ie.x == 0.0f ? Ip : Ie;
+    if (Ip.x == HOLE)
+        return Ip;
+    const float2 Jn = In.x == HOLE ? Ip : In, Js = Is.x == HOLE ? Ip : Is;
+    const float2 Jw = Iw.x == HOLE ? Ip : Iw, Je = Ie.x == HOLE ? Ip : Ie;
     const float gx = __fmul_rn(pair_diff(Je, Jw), 0.5f);
     const float gy = __fmul_rn(pair_diff(Js, Jn), 0.5f);
     const float g2 = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
@@ -101,7 +105,7 @@ __device__ __forceinline__ float2 update(float2 Ip, float2 In, float2 Is, float2
                      : update_alg1(Ip, In, Is, Iw, Ie, lam, c);
 }
 
-// Source pixel -> compensated metres; holes (0, negative, non-finite) -> 0.
+// Source pixel -> compensated metres; holes (0, negative, non-finite) -> HOLE.
 // u16: q * scale split exactly (q has at most 16 significant bits, so the
 // product fits in 40 bits and the fused multiply-add returns its exact tail).
 __device__ __forceinline__ float2 load_px(const void *src, int dtype, long long pitch, int x,
@@ -114,7 +118,7 @@ __device__ __forceinline__ float2 load_px(const void *src, int dtype, long long 
     } else if (dtype == PM_U16_MM) {
         const unsigned short q = __ldg((const unsigned short *)row + x);
         if (!q)
-            return make_float2(0.0f, 0.0f);
+            return make_float2(HOLE, 0.0f);
         const float qf = (float)q;
         const float hi = __fmul_rn(qf, scale);
         return make_float2(hi, __fmaf_rn(qf, scale, -hi));
@@ -123,23 +127,24 @@ __device__ __forceinline__ float2 load_px(const void *src, int dtype, long long 
     } else {
         v = __ldg((const float *)row + x);
     }
-    return make_float2((v > 0.0f && v < __int_as_float(0x7f800000)) ? v : 0.0f, 0.0f);
+    return make_float2((v > 0.0f && v < __int_as_float(0x7f800000)) ? v : HOLE, 0.0f);
 }
+
+__device__ __forceinline__ float depth_out(float2 v) { return v.x == HOLE ? 0.0f : v.x; }
 
 __device__ __forceinline__ void store_px(const DiffFrame &f, long long i, float2 v)
 {
     if (f.dst_pair)
         reinterpret_cast<float2 *>(f.dst)[i] = v;
     else
-        reinterpret_cast<float *>(f.dst)[i] = v.x;
+        reinterpret_cast<float *>(f.dst)[i] = depth_out(v);
 }
 
-// PM4 update from the four link fluxes, in the order of update_pm4.
+// PM4 update from the four link fluxes, in the order of update_pm4 (a HOLE
+// pixel receives only zero fluxes and keeps its value).
 __device__ __forceinline__ float2 pm4_combine(float2 Ip, float fN, float fS, float fW, float fE,
                                               float lam)
 {
-    if (Ip.x == 0.0f)
-        return make_float2(0.0f, 0.0f);
     return pair_add(Ip, __fmul_rn(lam, __fadd_rn(__fadd_rn(__fadd_rn(fN, fS), fW), fE)));
 }
 
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
         const int gy = ty0 - T + y;
         for (int x = lane; x < SX; x += 32) {
             const int gx = tx0 - T + x;
-            float2 v = make_float2(0.0f, 0.0f);
+            float2 v = make_float2(HOLE, 0.0f);
             if (gx >= 0 && gx < f.w && gy >= 0 && gy < f.h)
                 v = load_px(f.src, f.src_dtype, f.src_pitch, gx, gy, f.scale);
             A[y * SX + x] = v;
@@ -216,7 +221,7 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
                             const float fW = link_flux(cen[g], A[k - 1], c);
                             const float fE = link_flux(cen[g], A[k + 1], c);
                             B[k] = pm4_combine(cen[g], fN[g], fS, fW, fE, lam);
-                            fN[g] = cen[g].x == 0.0f ? 0.0f : -fS;
+                            fN[g] = -fS;
                             cen[g] = dn;
                         }
                     }
@@ -244,18 +249,53 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
     }
 }
 
+// Source pixel of a launch whose encoding SRC is known at compile time.
+template <int SRC>
+__device__ __forceinline__ float2 load_src(const DiffFrame &f, int x, int y)
+{
+    const char *row = (const char *)f.src + (long long)y * f.src_pitch;
+    if (SRC == SRC_PAIR)
+        return __ldg((const float2 *)row + x);
+    return load_px(f.src, SRC, f.src_pitch, x, y, f.scale);
+}
+
+// Two horizontally adjacent pixels (x even) in one access where the row
+// pitch and the base pointer allow it: 16 bytes for the float2 iterate, 8 for
+// FP32.
+template <int SRC>
+__device__ __forceinline__ void load_src2(const DiffFrame &f, int x, int y, bool vec, float2 &a,
+                                          float2 &b)
+{
+    const char *row = (const char *)f.src + (long long)y * f.src_pitch;
+    if (SRC == SRC_PAIR && vec) {
+        const float4 v = __ldg((const float4 *)row + (x >> 1));
+        a = make_float2(v.x, v.y);
+        b = make_float2(v.z, v.w);
+        return;
+    }
+    if (SRC == PM_F32_M && vec) {
+        const float2 v = __ldg((const float2 *)row + (x >> 1));
+        const float inf = __int_as_float(0x7f800000);
+        a = make_float2((v.x > 0.0f && v.x < inf) ? v.x : HOLE, 0.0f);
+        b = make_float2((v.y > 0.0f && v.y < inf) ? v.y : HOLE, 0.0f);
+        return;
+    }
+    a = load_src<SRC>(f, x, y);
+    b = load_src<SRC>(f, x + 1, y);
+}
+
 // One iteration over one frame, one pass over HBM.  Block = 32 x 8 threads;
 // lane l of warp w covers the two columns x0 = 64*blockIdx.x + 2l, x0 + 1 and
 // walks STREAM_ROWS rows down: the north link flux of a row is the negated
-// south link flux of the row before (exactly, see link_flux), the link
-// between the two columns is evaluated once, and the west flux of x0 is the
-// negated east flux of the lane to the left (a shuffle); only lane 0 and
-// lane 31 read a column of the neighbouring warp.  Every link appears in the
-// sum of update_pm4 with the same value and in the same order, so the result
-// is bit-identical to the tiled kernel.
+// south link flux of the row before (exactly, see link_flux) and the link
+// between the two columns is evaluated once; the horizontal neighbours come
+// from the adjacent lanes by shuffle, and lanes 0 and 31 fetch the column
+// just outside the warp.  Every link enters the sum of update_pm4 with the
+// same value and in the same order, so the result is bit-identical to the
+// tiled kernel.
 constexpr int STREAM_ROWS = 8;
 
-template <int MODE>
+template <int MODE, int SRC>
 __global__ void __launch_bounds__(256) k_diffuse_stream(DiffFrame f, float lam, float c)
 {
     const int lane = threadIdx.x;
@@ -264,42 +304,60 @@ __global__ void __launch_bounds__(256) k_diffuse_stream(DiffFrame f, float lam, 
     if (y0 >= f.h)
         return;
     const int y1 = min(y0 + STREAM_ROWS, f.h);
-    const float2 Z = make_float2(0.0f, 0.0f);
-    auto ld = [&](int x, int y) -> float2 {
-        return (x >= 0 && x < f.w && y >= 0 && y < f.h)
-                   ? load_px(f.src, f.src_dtype, f.src_pitch, x, y, f.scale) : Z;
+    const float2 Z = make_float2(HOLE, 0.0f);
+    const int vb = SRC == SRC_PAIR ? 16 : 8;
+    const bool vec_ld = (SRC == SRC_PAIR || SRC == PM_F32_M) && f.src_pitch % vb == 0 &&
+                        ((uintptr_t)f.src % vb) == 0;
+    const int ob = f.dst_pair ? 16 : 8;
+    const bool vec_st = ((long long)f.w * (f.dst_pair ? 8 : 4)) % ob == 0 &&
+                        ((uintptr_t)f.dst % ob) == 0;
+    auto ld2 = [&](int y, float2 &a, float2 &b) {
+        a = Z;
+        b = Z;
+        if (y < 0 || y >= f.h)
+            return;
+        if (x0 + 1 < f.w)
+            load_src2<SRC>(f, x0, y, vec_ld, a, b);
+        else if (x0 < f.w)
+            a = load_src<SRC>(f, x0, y);
     };
-    float2 a0 = ld(x0, y0), a1 = ld(x0 + 1, y0);
-    float2 u0 = ld(x0, y0 - 1), u1 = ld(x0 + 1, y0 - 1);
+    // the column just outside the warp: x0 - 1 for lane 0, x0 + 2 for lane 31
+    const int xe = lane == 0 ? x0 - 1 : x0 + 2;
+    const bool edge = (lane == 0 || lane == 31) && xe >= 0 && xe < f.w;
+
+    float2 a0, a1, u0, u1;
+    ld2(y0, a0, a1);
+    ld2(y0 - 1, u0, u1);
     float fN0 = 0.0f, fN1 = 0.0f;
     if (MODE == 0) {
         fN0 = link_flux(a0, u0, c);
         fN1 = link_flux(a1, u1, c);
     }
     for (int y = y0; y < y1; ++y) {
-        const float2 d0 = ld(x0, y + 1), d1 = ld(x0 + 1, y + 1);
+        float2 d0, d1;
+        ld2(y + 1, d0, d1);
+        float2 E = Z;
+        if (edge)
+            E = load_src<SRC>(f, xe, y);
         float2 L = make_float2(__shfl_up_sync(0xffffffffu, a1.x, 1),
                                __shfl_up_sync(0xffffffffu, a1.y, 1));
         float2 R = make_float2(__shfl_down_sync(0xffffffffu, a0.x, 1),
                                __shfl_down_sync(0xffffffffu, a0.y, 1));
         if (lane == 0)
-            L = ld(x0 - 1, y);
+            L = E;
         if (lane == 31)
-            R = ld(x0 + 2, y);
+            R = E;
         float2 n0, n1;
         if (MODE == 0) {
             const float f01 = link_flux(a0, a1, c);              // into x0 from x0+1
             const float fE1 = link_flux(a1, R, c);               // into x0+1 from x0+2
-            const float fEl = __shfl_up_sync(0xffffffffu, fE1, 1);
-            float fW0 = L.x == 0.0f ? 0.0f : -fEl;               // into x0 from x0-1
-            if (lane == 0)
-                fW0 = link_flux(a0, L, c);
-            const float fW1 = a0.x == 0.0f ? 0.0f : -f01;
+            const float fW0 = link_flux(a0, L, c);               // into x0 from x0-1
+            const float fW1 = -f01;
             const float fS0 = link_flux(a0, d0, c), fS1 = link_flux(a1, d1, c);
             n0 = pm4_combine(a0, fN0, fS0, fW0, f01, lam);
             n1 = pm4_combine(a1, fN1, fS1, fW1, fE1, lam);
-            fN0 = a0.x == 0.0f ? 0.0f : -fS0;
-            fN1 = a1.x == 0.0f ? 0.0f : -fS1;
+            fN0 = -fS0;
+            fN1 = -fS1;
         } else {
             n0 = update_alg1(a0, u0, d0, L, a1, lam, c);
             n1 = update_alg1(a1, u1, d1, a0, R, lam, c);
@@ -309,10 +367,18 @@ __global__ void __launch_bounds__(256) k_diffuse_stream(DiffFrame f, float lam, 
             n1 = a1;
         }
         const long long row = (long long)y * f.w;
-        if (x0 < f.w)
-            store_px(f, row + x0, n0);
-        if (x0 + 1 < f.w)
-            store_px(f, row + x0 + 1, n1);
+        if (vec_st && x0 + 1 < f.w) {
+            if (f.dst_pair)
+                reinterpret_cast<float4 *>(f.dst)[(row + x0) >> 1] = make_float4(n0.x, n0.y, n1.x, n1.y);
+            else
+                reinterpret_cast<float2 *>(f.dst)[(row + x0) >> 1] =
+                    make_float2(depth_out(n0), depth_out(n1));
+        } else {
+            if (x0 < f.w)
+                store_px(f, row + x0, n0);
+            if (x0 + 1 < f.w)
+                store_px(f, row + x0 + 1, n1);
+        }
         u0 = a0; u1 = a1;
         a0 = d0; a1 = d1;
     }
@@ -359,11 +425,21 @@ cudaError_t launch_diffuse_stream(const DiffFrame &f, float lambda, float K, int
                                   cudaStream_t s)
 {
     dim3 grid((f.w + 63) / 64, (f.h + 8 * STREAM_ROWS - 1) / (8 * STREAM_ROWS));
+    const dim3 block(32, 8);
     const float c = conductance_scale(K);
-    if (mode == 0)
-        k_diffuse_stream<0><<<grid, dim3(32, 8), 0, s>>>(f, lambda, c);
-    else
-        k_diffuse_stream<1><<<grid, dim3(32, 8), 0, s>>>(f, lambda, c);
+#define PM_STREAM(M, S) k_diffuse_stream<M, S><<<grid, block, 0, s>>>(f, lambda, c)
+    switch (f.src_dtype * 2 + (mode ? 1 : 0)) {
+    case PM_U16_MM * 2: PM_STREAM(0, PM_U16_MM); break;
+    case PM_U16_MM * 2 + 1: PM_STREAM(1, PM_U16_MM); break;
+    case PM_F16_M * 2: PM_STREAM(0, PM_F16_M); break;
+    case PM_F16_M * 2 + 1: PM_STREAM(1, PM_F16_M); break;
+    case PM_F32_M * 2: PM_STREAM(0, PM_F32_M); break;
+    case PM_F32_M * 2 + 1: PM_STREAM(1, PM_F32_M); break;
+    case SRC_PAIR * 2: PM_STREAM(0, SRC_PAIR); break;
+    case SRC_PAIR * 2 + 1: PM_STREAM(1, SRC_PAIR); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef PM_STREAM
     return cudaGetLastError();
 }
 
