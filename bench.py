@@ -33,6 +33,11 @@ WORKLOAD = ('640x480 u16 straight staircase (6 steps + floor + landing), 30 PM4 
             'iterations, central normals, RANSAC 1024 hypotheses x up to 12 planes, 1 cm')
 ITERS, HYP, MAXP, MINI, THR = 30, 1024, 12, 100, 0.01
 FP32_FLOP_PER_PAIR = 8          # 3 FMA residual + 1 FMA squared-threshold test
+# DRAM bytes (read + write) of the scoring kernel per hypothesis-point pair,
+# measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on round 0
+# of 32 frames of this workload: 156.4 MB for 9.73e9 pairs.  With the number
+# of hypotheses fixed, traffic grows with the candidate count, i.e. with pairs.
+SCORE_DRAM_BYTES_PER_PAIR = 156.37e6 / 9.73e9
 SM_COUNT, FP32_LANES = 148, 128
 
 
@@ -331,7 +336,9 @@ def run_ours(args):
     ach = score_pairs * FP32_FLOP_PER_PAIR / (score_ms * 1e-3) / 1e12 if score_ms > 0 else 0.0
     roof = {'kernel': 'k_score', 'bound': 'alu', 'achieved': ach, 'peak': peak_tflops,
             'unit': 'TFLOP/s', 'frac': ach / peak_tflops,
-            'traffic': None,
+            'traffic': SCORE_DRAM_BYTES_PER_PAIR * score_pairs / n_score,
+            'traffic_note': 'bytes per launch, scaled from an ncu capture of round 0 of 32 frames '
+                            'by pairs scored; algorithmic bytes are 16 B per candidate per launch',
             'peak_source': 'derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (%s peaks file)'
                            % (SM_COUNT, FP32_LANES, clock_mhz, pk_kind),
             'work': '%d FLOP per hypothesis-point pair; %.3e pairs over %d launches'
