@@ -150,7 +150,7 @@ void pm_destroy(pm_ctx *ctx);
 pm_status pm_diffuse(pm_ctx *ctx, const void *depth, int dtype, int w, int h, int pitch,
                      float *out, void *stream);
 
-/* Alg. 1, second loop (Eq. 2) and Alg. 2 line 3: from FP32 device depth [h*w]
+/* Alg. 1, second loop (Eq. 2), and the back-projection of Alg. 2: from FP32 device depth [h*w]
  * compute points P = z K^-1 (u, v, 1) and unit normals (SoA, device float
  * [3][h*w] each; holes get 0) and the validity byte per pixel (device
  * uint8 [h*w]: bit 0 = point valid, bit 1 = normal valid).  Normals point

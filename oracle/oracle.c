@@ -160,7 +160,7 @@ int or_diffuse(const double *in, double *out, int w, int h, int iters,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Back-projection and normals: Alg. 1 (normal loop), Eq. 2, Alg. 2 line 3.  */
+/* Back-projection and normals: Alg. 1 (normal loop), Eq. 2, Alg. 2.          */
 /* ------------------------------------------------------------------------ */
 
 /* Reading of Eq. 2 (dimensionally garbled as printed): the normal at a pixel
@@ -571,4 +571,174 @@ int or_ransac(const float *P, const float *N, const unsigned char *valid, int w,
     }
     free(cand); free(counts); free(hyp); free(inl);
     return n_planes;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-region RANSAC in the literal form of Alg. 2 (one model per polygon). */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double n[3];
+    double d;
+    unsigned long long error;   /* sum of distances in units of 2^-32 m */
+    int inliers;
+    int total;
+    int accepted;
+    int hyp_index;
+} or_region_plane;
+
+#define OR_REGION_TRIES 16
+
+/* The point sample of Alg. 2 ("select random subset of 3 points") for
+ * region r: for sample j in {0, 1, 2}, attempt a = 0..15 draws
+ *   Philox4x64-10(key = (seed, 1), counter = (h, r, frame_idx, 16 j + a))
+ * and takes the pixel (u0 + floor(w0 * bw / 2^64), v0 + floor(w1 * bh / 2^64))
+ * of the region's bounding box [u0, u0 + bw) x [v0, v0 + bh); the first
+ * attempt that lands on a valid point of the region is the sample (uniform
+ * over the region's points, by rejection).  Returns 0 if some sample found no
+ * point in 16 attempts. */
+static int region_sample(uint64_t seed, uint64_t frame_idx, int r, int h, int u0, int v0, int bw,
+                         int bh, int w, const int *regions, const unsigned char *valid,
+                         long out[3])
+{
+    for (int j = 0; j < 3; ++j) {
+        out[j] = -1;
+        for (int a = 0; a < OR_REGION_TRIES; ++a) {
+            uint64_t key[2] = {seed, 1};
+            uint64_t ctr[4] = {(uint64_t)h, (uint64_t)r, frame_idx, (uint64_t)(16 * j + a)};
+            uint64_t wd[4];
+            or_philox4x64_10(ctr, key, wd);
+            int u = u0 + (int)(((unsigned __int128)wd[0] * (uint64_t)bw) >> 64);
+            int v = v0 + (int)(((unsigned __int128)wd[1] * (uint64_t)bh) >> 64);
+            long p = (long)v * w + u;
+            if ((valid[p] & 1) && regions[p] == r) {
+                out[j] = p;
+                break;
+            }
+        }
+        if (out[j] < 0)
+            return 0;
+    }
+    return 1;
+}
+
+/* Alg. 2 for every region r in [0, R) of one frame (regions[p] = region of
+ * pixel p, < 0 or >= R: none): for each of H hypotheses, the FP32 plane
+ * through its three samples (hyp_plane_f32) and
+ *   error_h = sum over the region's valid points of d_i,
+ *   d_i = |r_i| with r_i the FP32 residual of is_inlier_f32, truncated to a
+ *         multiple of 2^-32 m (d_i * 2^32 is exact in FP32) and summed exactly
+ *         in 64-bit integers;
+ *   inliers_h = #{ i : fma(r_i, r_i, -thr^2) < 0 }   (Alg. 2 "d < threshold");
+ * the winner minimises error_h (ties: lowest h; degenerate hypotheses never
+ * win); the region's model is accepted when inliers / total > 0.9, i.e.
+ * 10 * inliers > 9 * total (Alg. 2 end, Sec. III-D text).  Regions without a
+ * usable hypothesis report hyp_index = -1. */
+int or_ransac_regions(const float *P, const unsigned char *valid, const int *regions, int w,
+                      int h, int R, int H, float thr, uint64_t seed, uint64_t frame_idx,
+                      or_region_plane *out)
+{
+    long n = (long)w * h;
+    if (w <= 0 || h <= 0 || R <= 0 || H <= 0 || !(thr > 0.0f))
+        return -1;
+    int *u0 = (int *)malloc(4 * (size_t)R * sizeof(int));
+    int *cnt = (int *)calloc((size_t)R, sizeof(int));
+    if (!u0 || !cnt) {
+        free(u0); free(cnt);
+        return -2;
+    }
+    int *v0 = u0 + R, *u1 = u0 + 2 * R, *v1 = u0 + 3 * R;
+    for (int r = 0; r < R; ++r) {
+        u0[r] = w; v0[r] = h; u1[r] = -1; v1[r] = -1;
+    }
+    for (int v = 0; v < h; ++v)
+        for (int u = 0; u < w; ++u) {
+            long p = (long)v * w + u;
+            int r = regions[p];
+            if (r < 0 || r >= R || !(valid[p] & 1))
+                continue;
+            cnt[r]++;
+            if (u < u0[r]) u0[r] = u;
+            if (u > u1[r]) u1[r] = u;
+            if (v < v0[r]) v0[r] = v;
+            if (v > v1[r]) v1[r] = v;
+        }
+    const float thr2 = thr * thr;
+    const float scale = 4294967296.0f;   /* 2^32 */
+    for (int r = 0; r < R; ++r) {
+        or_region_plane *o = &out[r];
+        memset(o, 0, sizeof(*o));
+        o->total = cnt[r];
+        o->hyp_index = -1;
+        if (cnt[r] < 3)
+            continue;
+        unsigned long long best_err = 0;
+        int best = -1, best_in = 0;
+        float best_pl[4] = {0, 0, 0, 0};
+        for (int hh = 0; hh < H; ++hh) {
+            long s[3];
+            if (!region_sample(seed, frame_idx, r, hh, u0[r], v0[r], u1[r] - u0[r] + 1,
+                               v1[r] - v0[r] + 1, w, regions, valid, s))
+                continue;
+            float q[3][3], pl[4];
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k)
+                    q[j][k] = P[k * n + s[j]];
+            if (!hyp_plane_f32(q[0], q[1], q[2], pl))
+                continue;
+            unsigned long long err = 0;
+            int in = 0;
+            for (long p = 0; p < n; ++p) {
+                if (regions[p] != r || !(valid[p] & 1))
+                    continue;
+                float res = fmaf(pl[0], P[p], pl[3]);
+                res = fmaf(pl[1], P[n + p], res);
+                res = fmaf(pl[2], P[2 * n + p], res);
+                float dist = fabsf(res);
+                err += (unsigned long long)(dist * scale);
+                in += fmaf(res, res, -thr2) < 0.0f;
+            }
+            if (best < 0 || err < best_err) {
+                best = hh;
+                best_err = err;
+                best_in = in;
+                memcpy(best_pl, pl, sizeof(pl));
+            }
+        }
+        if (best < 0)
+            continue;
+        for (int k = 0; k < 3; ++k)
+            o->n[k] = best_pl[k];
+        o->d = best_pl[3];
+        o->error = best_err;
+        o->inliers = best_in;
+        o->accepted = 10LL * best_in > 9LL * cnt[r];
+        o->hyp_index = best;
+    }
+    free(u0);
+    free(cnt);
+    return R;
+}
+
+/* The 3 sample pixels of hypothesis h of region r (test access to the
+ * sampling rule).  Returns 1 and fills out[3], or 0 if a sample failed. */
+int or_region_samples(const int *regions, const unsigned char *valid, int w, int h, int R, int r,
+                      int hyp, uint64_t seed, uint64_t frame_idx, long out[3])
+{
+    int u0 = w, v0 = h, u1 = -1, v1 = -1;
+    for (int v = 0; v < h; ++v)
+        for (int u = 0; u < w; ++u) {
+            long p = (long)v * w + u;
+            if (regions[p] != r || !(valid[p] & 1))
+                continue;
+            if (u < u0) u0 = u;
+            if (u > u1) u1 = u;
+            if (v < v0) v0 = v;
+            if (v > v1) v1 = v;
+        }
+    (void)R;
+    if (u1 < 0)
+        return 0;
+    return region_sample(seed, frame_idx, r, hyp, u0, v0, u1 - u0 + 1, v1 - v0 + 1, w, regions,
+                         valid, out);
 }

@@ -1,5 +1,5 @@
 // normals.cu -- fused back-projection and normal image (Sec. III-C, Eq. 2,
-// Alg. 1 second loop; Alg. 2 line 3) for sm_103a.
+// Alg. 1 second loop; the back-projection of Alg. 2) for sm_103a.
 //
 // Eq. 2 as printed mixes depth gradients with a pixel back-projection; the
 // normal computed here is the exact surface normal of the back-projected depth
