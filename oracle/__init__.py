@@ -16,6 +16,9 @@ Parity status per function (what pins it is listed in the test suite):
   eig3            pinned (numpy.linalg.eigh)
   ransac          pinned (brute force over all triplets on <= 30 points,
                   exact counts of given hypotheses, noise-free staircase planes)
+  ransac_regions  pinned (sample uniformity and region membership, FP64 brute-force
+                  distance sums per hypothesis, argmin rule, acceptance on single-
+                  and two-plane regions, ground-truth planes of a staircase)
 """
 from __future__ import annotations
 
@@ -66,6 +69,14 @@ def lib():
                                 ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_double,
                                 ctypes.c_uint64, P, P, P]
         L.or_ransac.restype = ctypes.c_int
+        L.or_ransac_regions.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_float, ctypes.c_uint64,
+                                        ctypes.c_uint64, P]
+        L.or_ransac_regions.restype = ctypes.c_int
+        L.or_region_samples.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                        ctypes.c_uint64, P]
+        L.or_region_samples.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -175,6 +186,55 @@ def ransac(P32: np.ndarray, N32, valid: np.ndarray, hypotheses: int, thr: float,
     f = lambda k: np.array([getattr(planes[i], k) for i in range(n)])
     return RansacResult(pl, f('n_inliers'), f('n_refit'), f('rms'), f('hyp_index'), f('band'),
                         labels, counts)
+
+
+class OrRegionPlane(ctypes.Structure):
+    _fields_ = [('n', ctypes.c_double * 3), ('d', ctypes.c_double),
+                ('error', ctypes.c_ulonglong), ('inliers', ctypes.c_int),
+                ('total', ctypes.c_int), ('accepted', ctypes.c_int), ('hyp_index', ctypes.c_int)]
+
+
+REGION_ERROR_UNIT = 2.0 ** -32      # metres per unit of the integer distance sums
+
+
+@dataclass
+class RegionResult:
+    planes: np.ndarray        # (R, 4) winning hypothesis planes (FP32 values), 0 if none
+    error: np.ndarray         # (R,) uint64 sum of distances in units of 2^-32 m
+    inliers: np.ndarray
+    total: np.ndarray
+    accepted: np.ndarray      # (R,) bool: inliers / total > 0.9
+    hyp_index: np.ndarray     # (R,) -1 if the region had no usable hypothesis
+
+
+def ransac_regions(P32: np.ndarray, valid: np.ndarray, regions: np.ndarray, n_regions: int,
+                   hypotheses: int, thr: float, seed: int, frame_idx: int = 0) -> RegionResult:
+    """Alg. 2 per region: minimum total distance, 0.9 inlier-ratio acceptance."""
+    P = np.ascontiguousarray(P32, dtype=np.float32)
+    _, h, w = P.shape
+    V = np.ascontiguousarray(valid, dtype=np.uint8)
+    Rg = np.ascontiguousarray(regions, dtype=np.int32)
+    out = (OrRegionPlane * n_regions)()
+    rc = lib().or_ransac_regions(_p(P), _p(V), _p(Rg), w, h, n_regions, hypotheses, thr, seed,
+                                 frame_idx, ctypes.cast(out, ctypes.c_void_p))
+    if rc < 0:
+        raise ValueError('or_ransac_regions failed (%d)' % rc)
+    g = lambda k, t: np.array([getattr(out[i], k) for i in range(n_regions)], dtype=t)
+    pl = np.array([[*out[i].n, out[i].d] for i in range(n_regions)]).reshape(-1, 4)
+    return RegionResult(pl, g('error', np.uint64), g('inliers', np.int64), g('total', np.int64),
+                        g('accepted', np.int64).astype(bool), g('hyp_index', np.int64))
+
+
+def region_samples(valid: np.ndarray, regions: np.ndarray, n_regions: int, r: int, hyp: int,
+                   seed: int, frame_idx: int = 0):
+    """Pixel indices of the three samples of hypothesis `hyp` of region r, or None."""
+    V = np.ascontiguousarray(valid, dtype=np.uint8)
+    Rg = np.ascontiguousarray(regions, dtype=np.int32)
+    h, w = Rg.shape
+    out = np.zeros(3, dtype=np.int64)
+    ok = lib().or_region_samples(_p(Rg), _p(V), w, h, n_regions, r, hyp, seed, frame_idx,
+                                 _p(out))
+    return out if ok else None
 
 
 # ---------------------------------------------------------------------------

@@ -587,16 +587,16 @@ typedef struct {
     int hyp_index;
 } or_region_plane;
 
-#define OR_REGION_TRIES 16
+#define OR_REGION_TRIES 64
 
 /* The point sample of Alg. 2 ("select random subset of 3 points") for
- * region r: for sample j in {0, 1, 2}, attempt a = 0..15 draws
- *   Philox4x64-10(key = (seed, 1), counter = (h, r, frame_idx, 16 j + a))
+ * region r: for sample j in {0, 1, 2}, attempt a = 0..63 draws
+ *   Philox4x64-10(key = (seed, 1), counter = (h, r, frame_idx, 64 j + a))
  * and takes the pixel (u0 + floor(w0 * bw / 2^64), v0 + floor(w1 * bh / 2^64))
  * of the region's bounding box [u0, u0 + bw) x [v0, v0 + bh); the first
  * attempt that lands on a valid point of the region is the sample (uniform
  * over the region's points, by rejection).  Returns 0 if some sample found no
- * point in 16 attempts. */
+ * point in 64 attempts (then the hypothesis is degenerate). */
 static int region_sample(uint64_t seed, uint64_t frame_idx, int r, int h, int u0, int v0, int bw,
                          int bh, int w, const int *regions, const unsigned char *valid,
                          long out[3])
@@ -605,7 +605,7 @@ static int region_sample(uint64_t seed, uint64_t frame_idx, int r, int h, int u0
         out[j] = -1;
         for (int a = 0; a < OR_REGION_TRIES; ++a) {
             uint64_t key[2] = {seed, 1};
-            uint64_t ctr[4] = {(uint64_t)h, (uint64_t)r, frame_idx, (uint64_t)(16 * j + a)};
+            uint64_t ctr[4] = {(uint64_t)h, (uint64_t)r, frame_idx, (uint64_t)(64 * j + a)};
             uint64_t wd[4];
             or_philox4x64_10(ctr, key, wd);
             int u = u0 + (int)(((unsigned __int128)wd[0] * (uint64_t)bw) >> 64);
