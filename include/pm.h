@@ -205,6 +205,37 @@ pm_status pm_process_batch_async(pm_ctx *ctx, const pm_frame *frames, int n, int
                                  void *stream);
 pm_status pm_batch_collect(pm_ctx *ctx, pm_plane *planes, int *n_planes, int n);
 
+/* Per-region RANSAC in the literal form of Alg. 2 (Sec. III-D): one plane
+ * model per region (e.g. a polygon of the paper's contour step).  For region r
+ * (regions[p] == r, device int32 [h*w]; values outside [0, n_regions) and
+ * invalid points are ignored), `hypotheses` (1..2048) hypotheses are drawn:
+ * each sample is uniform over the region's valid points, by rejection in the
+ * region's bounding box (Philox4x64-10, key (seed, 1), counter
+ * (hypothesis, region, frame_idx, 64 * sample + attempt), up to 64 attempts;
+ * a sample without a hit makes the hypothesis degenerate).  The hypothesis
+ * with the minimum total distance sum_i |n . p_i + d| over the region's
+ * points wins (each distance, computed in FP32 as the inlier test does, is
+ * truncated to a multiple of 2^-32 m and summed in 64-bit integers, so the
+ * minimum is exact; ties go to the lowest index); the model is accepted when
+ * 10 * inliers > 9 * points (more than 90% inliers, threshold rp->thr_m).
+ * out: host [n_regions] (n, d: the winning FP32 hypothesis plane, not refit;
+ * hyp_index = -1 when the region has fewer than 3 points or no usable
+ * hypothesis).  n_regions in [1, 65535] and n_regions * hypotheses <= 2^22.
+ * Uses the context's seed and threshold; synchronises `stream`. */
+typedef struct {
+    double n[3];
+    double d;
+    unsigned long long error;   /* sum of distances, units of 2^-32 m */
+    int inliers;
+    int total;
+    int accepted;
+    int hyp_index;
+} pm_region_plane;
+
+pm_status pm_ransac_regions(pm_ctx *ctx, const float *points, const unsigned char *valid,
+                            const int *regions, int w, int h, int n_regions, int hypotheses,
+                            unsigned long long frame_idx, pm_region_plane *out, void *stream);
+
 /* Change the diffusion tiling of a context (autotuning): temporal blocking
  * depth iters_per_launch (1..8) and output tile tile_w x tile_h (limits as in
  * pm_diffusion_params; 0 = library choice).  Results are bit-identical for

@@ -41,6 +41,12 @@ class Plane(ctypes.Structure):
                 ('rms', ctypes.c_float), ('hyp_index', ctypes.c_int)]
 
 
+class RegionPlane(ctypes.Structure):
+    _fields_ = [('n', ctypes.c_double * 3), ('d', ctypes.c_double),
+                ('error', ctypes.c_ulonglong), ('inliers', ctypes.c_int),
+                ('total', ctypes.c_int), ('accepted', ctypes.c_int), ('hyp_index', ctypes.c_int)]
+
+
 class Frame(ctypes.Structure):
     _fields_ = [('depth', ctypes.c_void_p), ('dtype', ctypes.c_int), ('w', ctypes.c_int),
                 ('h', ctypes.c_int), ('pitch', ctypes.c_int), ('K', Intrinsics),
@@ -51,7 +57,8 @@ class Frame(ctypes.Structure):
 EXPORTS = ['pm_create', 'pm_destroy', 'pm_diffuse', 'pm_normals', 'pm_ransac_planes',
            'pm_process_frame', 'pm_process_frame_host', 'pm_process_batch',
            'pm_process_batch_async', 'pm_batch_collect', 'pm_scratch_bytes', 'pm_set_timing',
-           'pm_stage_times', 'pm_kernel_stats', 'pm_diffuse_noalloc', 'pm_set_tiling', 'pm_last_error']
+           'pm_stage_times', 'pm_kernel_stats', 'pm_ransac_regions', 'pm_diffuse_noalloc',
+           'pm_set_tiling', 'pm_last_error']
 
 _lib = None
 
@@ -90,6 +97,7 @@ def load(path: str = LIB_PATH):
         'pm_stage_times': ([vp, P(ctypes.c_float)], i),
         'pm_kernel_stats': ([vp, P(ctypes.c_float), P(ctypes.c_longlong), P(i),
                              P(ctypes.c_longlong)], i),
+        'pm_ransac_regions': ([vp, vp, vp, vp, i, i, i, i, u64, P(RegionPlane), vp], i),
         'pm_diffuse_noalloc': ([vp, i, i, i, i, P(DiffusionParams), ctypes.c_float, vp, vp], i),
         'pm_set_tiling': ([vp, i, i, i], i),
         'pm_last_error': ([], ctypes.c_char_p),

@@ -110,6 +110,10 @@ struct pm_ctx {
     cudaEvent_t kev[2 * MAX_PLANES] = {};
     float stage_ms[3] = {0, 0, 0};
     int pending_n = 0;
+    char *rg = nullptr;                   // per-region RANSAC scratch (grown on demand)
+    size_t rg_cap = 0;
+    pm_region_plane *h_rg = nullptr;      // pinned copy of its results
+    int h_rg_cap = 0;
     cudaStream_t gstream = nullptr;       // graph stream when the caller passes the legacy stream
     cudaEvent_t gev[2] = {nullptr, nullptr};
     long long launches = 0;               // kernels launched by the last call
@@ -615,6 +619,10 @@ void pm_destroy(pm_ctx *ctx)
     cudaDeviceSynchronize();
     for (GraphEntry &g : ctx->graphs)
         cudaGraphExecDestroy(g.exec);
+    if (ctx->rg)
+        cudaFree(ctx->rg);
+    if (ctx->h_rg)
+        cudaFreeHost(ctx->h_rg);
     if (ctx->gstream)
         cudaStreamDestroy(ctx->gstream);
     for (int i = 0; i < 2; ++i)
@@ -864,6 +872,81 @@ pm_status pm_batch_collect(pm_ctx *ctx, pm_plane *planes, int *n_planes, int n)
         if (st != PM_OK)
             return st;
     }
+    return PM_OK;
+}
+
+pm_status pm_ransac_regions(pm_ctx *ctx, const float *points, const unsigned char *valid,
+                            const int *regions, int w, int h, int n_regions, int hypotheses,
+                            unsigned long long frame_idx, pm_region_plane *out, void *stream)
+{
+    if (!ctx || !points || !valid || !regions || !out)
+        return fail(PM_ERR_ARG, "null argument");
+    if (w < 1 || h < 1 || (long long)w * h > ctx->max_npx)
+        return fail(PM_ERR_ARG, "image size out of range for this context");
+    if (n_regions < 1 || n_regions > 65535)
+        return fail(PM_ERR_ARG, "n_regions must lie in [1, 65535]");
+    if (hypotheses < 1 || hypotheses > MAX_HYP)
+        return fail(PM_ERR_ARG, "hypotheses must lie in [1, 2048]");
+    if ((long long)n_regions * hypotheses > (1ll << 22))
+        return fail(PM_ERR_ARG, "n_regions * hypotheses above 2^22");
+    if (ctx->pending_n)
+        return fail(PM_ERR_STATE, "an asynchronous batch is still pending on this context");
+    const size_t R = (size_t)n_regions, RH = R * (size_t)hypotheses;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t o_cnt = take(R * 4), o_box = take(R * 16), o_off = take(R * 4),
+                 o_cur = take(R * 4), o_cb = take((R + 1) * 4), o_hyp = take(RH * 16),
+                 o_deg = take(RH), o_err = take(RH * 8), o_inl = take(RH * 4),
+                 o_out = take(R * sizeof(pm_region_plane));
+    if (off > ctx->rg_cap) {
+        if (ctx->rg)
+            cudaFree(ctx->rg);
+        ctx->rg = nullptr;
+        ctx->rg_cap = 0;
+        PM_CK(cudaMalloc(&ctx->rg, off));
+        ctx->rg_cap = off;
+    }
+    if (n_regions > ctx->h_rg_cap) {
+        if (ctx->h_rg)
+            cudaFreeHost(ctx->h_rg);
+        ctx->h_rg = nullptr;
+        ctx->h_rg_cap = 0;
+        PM_CK(cudaMallocHost(&ctx->h_rg, R * sizeof(pm_region_plane)));
+        ctx->h_rg_cap = n_regions;
+    }
+    char *b = ctx->rg;
+    RegionLaunch L;
+    L.P = points;
+    L.valid = valid;
+    L.regions = regions;
+    L.w = w;
+    L.h = h;
+    L.R = n_regions;
+    L.H = hypotheses;
+    L.frame_idx = frame_idx;
+    L.seed = ctx->rp.seed;
+    L.thr2 = ctx->rp.thr_m * ctx->rp.thr_m;
+    L.cnt = reinterpret_cast<int *>(b + o_cnt);
+    L.box = reinterpret_cast<int *>(b + o_box);
+    L.offset = reinterpret_cast<int *>(b + o_off);
+    L.cursor = reinterpret_cast<int *>(b + o_cur);
+    L.chunk_base = reinterpret_cast<int *>(b + o_cb);
+    L.list = ctx->at<float4>(ctx->lay.cpt[0]);
+    L.hyp = reinterpret_cast<float4 *>(b + o_hyp);
+    L.deg = reinterpret_cast<unsigned char *>(b + o_deg);
+    L.err = reinterpret_cast<unsigned long long *>(b + o_err);
+    L.inl = reinterpret_cast<int *>(b + o_inl);
+    L.out = reinterpret_cast<pm_region_plane *>(b + o_out);
+    cudaStream_t s = (cudaStream_t)stream;
+    PM_CK(ransac_regions(L, ctx->sms, s));
+    PM_CK(cudaMemcpyAsync(ctx->h_rg, L.out, R * sizeof(pm_region_plane), cudaMemcpyDeviceToHost,
+                          s));
+    PM_CK(cudaStreamSynchronize(s));
+    std::memcpy(out, ctx->h_rg, R * sizeof(pm_region_plane));
     return PM_OK;
 }
 

@@ -199,6 +199,27 @@ struct RansacLaunch {
     unsigned *d_counter;  // grid-completion counter of the compaction kernel
     bool fine_score;      // finer scoring work items (small batches)
 };
+// Per-region RANSAC (regions.cu): all pointers device memory.
+struct RegionLaunch {
+    const float *P;                 // SoA points [3][w*h]
+    const unsigned char *valid;
+    const int *regions;             // [w*h]
+    int w, h, R, H;
+    unsigned long long frame_idx, seed;
+    float thr2;
+    int *cnt;                       // [R] points per region
+    int *box;                       // [R][4] u0, v0, u1, v1
+    int *offset, *cursor;           // [R] list offsets / scatter cursors
+    int *chunk_base;                // [R + 1] prefix of scoring chunks
+    float4 *list;                   // [w*h] region-grouped points
+    float4 *hyp;                    // [R*H]
+    unsigned char *deg;             // [R*H] degenerate hypotheses
+    unsigned long long *err;        // [R*H] distance sums (units of 2^-32 m)
+    int *inl;                       // [R*H] inlier counts
+    pm_region_plane *out;           // [R]
+};
+cudaError_t ransac_regions(const RegionLaunch &L, int sms, cudaStream_t s);
+
 cudaError_t ransac_init(const RansacLaunch &L, cudaStream_t s);
 // ev_score: optional event pair recorded around the scoring launch.
 cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream_t s,

@@ -59,6 +59,26 @@ class Planes:
                       g('hyp_index', np.int64), labels)
 
 
+@dataclass
+class RegionPlanes:
+    """One model per region (Alg. 2 per polygon): rows (nx, ny, nz, d) of the
+    winning hypothesis, its distance sum (units of 2^-32 m), inlier and point
+    counts, the 90% acceptance flag and the hypothesis index (-1: none)."""
+    planes: np.ndarray
+    error: np.ndarray
+    inliers: np.ndarray
+    total: np.ndarray
+    accepted: np.ndarray
+    hyp_index: np.ndarray
+
+    @staticmethod
+    def from_c(arr, n) -> 'RegionPlanes':
+        pl = np.array([[*arr[i].n, arr[i].d] for i in range(n)], dtype=np.float64).reshape(-1, 4)
+        g = lambda k, t: np.array([getattr(arr[i], k) for i in range(n)], dtype=t)
+        return RegionPlanes(pl, g('error', np.uint64), g('inliers', np.int64), g('total', np.int64),
+                            g('accepted', np.int64).astype(bool), g('hyp_index', np.int64))
+
+
 def _stream_ptr(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -165,6 +185,24 @@ class Pipeline:
             w, h, frame_idx, arr, self.p.max_planes, ctypes.byref(n),
             _dev(lab, 'labels') if lab is not None else None, _stream_ptr(stream)))
         return Planes.from_c(arr, n.value, lab)
+
+    def ransac_regions(self, P: torch.Tensor, valid: torch.Tensor, regions: torch.Tensor,
+                       n_regions: int, hypotheses: int = 256, frame_idx: int = 0,
+                       stream=None) -> RegionPlanes:
+        """Per-region RANSAC (Alg. 2 per polygon); regions: int32 [h, w], -1 = none."""
+        _, h, w = P.shape
+        for t, nm in ((P, 'P'), (valid, 'valid'), (regions, 'regions')):
+            if not t.is_contiguous():
+                raise ValueError('%s must be contiguous' % nm)
+        if P.dtype != torch.float32 or valid.dtype != torch.uint8 or regions.dtype != torch.int32:
+            raise ValueError('P must be float32, valid uint8 and regions int32')
+        if tuple(valid.shape) != (h, w) or tuple(regions.shape) != (h, w):
+            raise ValueError('valid and regions must be [h, w] like P')
+        arr = (_ffi.RegionPlane * max(n_regions, 1))()
+        check(self.lib.pm_ransac_regions(
+            self._h, _dev(P, 'P'), _dev(valid, 'valid'), _dev(regions, 'regions'), w, h, n_regions,
+            hypotheses, frame_idx, arr, _stream_ptr(stream)))
+        return RegionPlanes.from_c(arr, n_regions)
 
     # -- whole path ---------------------------------------------------------
     def process_frame(self, depth: torch.Tensor, K, frame_idx: int = 0, labels: bool = True,

@@ -36,6 +36,7 @@ def test_struct_sizes():
     assert ctypes.sizeof(_ffi.Intrinsics) == 32
     assert ctypes.sizeof(_ffi.RansacParams) == 32
     assert ctypes.sizeof(_ffi.Frame) == 88
+    assert ctypes.sizeof(_ffi.RegionPlane) == 56
 
 
 def test_last_error_initially_empty_or_text():
@@ -73,3 +74,10 @@ def test_scratch_bytes_is_monotone():
     c = pm.scratch_bytes(1280, 720, 1, 1024, 12)
     assert 0 < a < b and a < c
     assert pm.scratch_bytes(0, 480, 1, 1024, 12) == -1
+
+
+def test_region_ransac_rejects_a_null_context():
+    lib = pm.load_library()
+    out = (_ffi.RegionPlane * 1)()
+    st = lib.pm_ransac_regions(None, None, None, None, 64, 48, 1, 64, 0, out, None)
+    assert st == _ffi.PM_ERR_ARG
