@@ -37,7 +37,9 @@ FP32_FLOP_PER_PAIR = 8          # 3 FMA residual + 1 FMA squared-threshold test
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on round 0
 # of 32 frames of this workload: 156.4 MB for 9.73e9 pairs.  With the number
 # of hypotheses fixed, traffic grows with the candidate count, i.e. with pairs.
-SCORE_DRAM_BYTES_PER_PAIR = 156.37e6 / 9.73e9
+SCORE_DRAM_BYTES_PER_PAIR = None   # ncu dram bytes per scored pair (k_score), when captured
+SEGMENT, BOX_TEST_FLOP = 32, 12
+REGION_FLOP_PER_PAIR = 9     # 3 FMA residual, |r| x 2^32, 1 FMA inlier test
 SM_COUNT, FP32_LANES = 148, 128
 
 
@@ -182,6 +184,44 @@ def diffusion_hbm(torch, pm, dev, pk, side=8192, reps=5):
             'achieved': gbs, 'peak': pk['hbm_gbs'], 'unit': 'GB/s', 'frac': gbs / pk['hbm_gbs']}
 
 
+def run_regions(torch, pm, pipe, frames, dframes, pk, n_frames=8, H=256, reps=3):
+    """Per-region RANSAC (one model per region) on 640x480 staircase frames;
+    the regions are the generator's ground-truth plane ids, standing in for
+    the polygons of the contour step.  Points come from the library's own
+    diffusion and normals; only pm_ransac_regions is timed."""
+    s = torch.cuda.current_stream()
+    ms, pairs, regions = [], 0, 0
+    for i in range(n_frames):
+        fr = frames[i]
+        z = pipe.diffuse(dframes[i])
+        P, _, V = pipe.normals(z, fr.cam.intrinsics)
+        lab = torch.from_numpy(np.ascontiguousarray(fr.plane_id, dtype=np.int32)).to(z.device)
+        R = int(fr.plane_id.max()) + 1
+        pipe.ransac_regions(P, V, lab, R, H, i)          # warm-up (scratch allocation)
+        for k in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            out = pipe.ransac_regions(P, V, lab, R, H, i)
+            b.record(s)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        pairs += int(out.total.sum()) * H
+        regions += R
+    per_call = statistics.median(ms)
+    clock_mhz = pk.get('sm_max_mhz', 2032.0)
+    peak = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
+    pairs_per_call = pairs / n_frames
+    tflops = pairs_per_call * REGION_FLOP_PER_PAIR / (per_call * 1e-3) / 1e12
+    return {'frames': n_frames, 'regions_per_frame': regions / n_frames, 'hypotheses': H,
+            'ms_per_frame_p50': per_call, 'frames_per_s': 1e3 / per_call,
+            'regions_per_s': regions / n_frames * 1e3 / per_call,
+            'pairs_per_s': pairs_per_call / (per_call * 1e-3),
+            'alu': {'achieved': tflops, 'peak': peak, 'unit': 'TFLOP/s', 'frac': tflops / peak,
+                    'work': '%d FP32 FLOP per hypothesis-point pair, whole call (7 launches)'
+                            % REGION_FLOP_PER_PAIR},
+            'api': 'pm_ransac_regions (synchronising), regions = ground-truth plane ids'}
+
+
 def run_served(torch, pm, args, c2_frames, c2_dev):
     """The served form: 16 simulated cameras (fixed resolution each from
     424x240 / 640x480 / 848x480 / 1280x720, staircases, camera advancing 5 cm
@@ -264,7 +304,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    step_ms, score_ms, score_pairs, launches = [], 0.0, 0, 0
+    step_ms, score_ms, score_pairs, eval_pairs, launches = [], 0.0, 0, 0, 0
     torch.cuda.nvtx.range_push('timed')
     for k in range(args.steps):
         flush.fill_(float(k))                      # evict L2 between steps
@@ -277,6 +317,7 @@ def run_ours(args):
         st = pipe.kernel_stats()
         score_ms += st['score_ms']
         score_pairs += st['score_pairs']
+        eval_pairs += st['evaluated_pairs']
         launches += st['launches']
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
@@ -324,29 +365,43 @@ def run_ours(args):
         if k > 0:
             e2e_ms.append(a.elapsed_time(b))
     h2d = sum(h.numel() * h.element_size() for h in host)
-    d2h = B * (64 * 48 + 336)   # planes + per-frame state read back by the call
+    d2h = B * (64 * 48 + 352)   # planes + per-frame state read back by the call
     e2e = {'value': B / (statistics.mean(e2e_ms) * 1e-3), 'unit': 'frames/s',
            'h2d_bytes_per_step': h2d, 'd2h_bytes_per_step': d2h,
            'api': 'pm_process_batch after pinned-host copies'}
 
-    # roofline: the scoring kernel (FP32 ALU bound)
+    # roofline: the scoring kernel (FP32 ALU bound).  Executed work = the
+    # pairs it evaluates (8 FLOP each) + one box test per hypothesis and
+    # 32-candidate segment (12 FLOP); the pairs the box test skips are exact
+    # zeros and count only in the effective rate.
     n_score = args.steps * MAXP
     clock_mhz = pk.get('sm_max_mhz', 2032.0)
     peak_tflops = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
-    ach = score_pairs * FP32_FLOP_PER_PAIR / (score_ms * 1e-3) / 1e12 if score_ms > 0 else 0.0
+    tests = score_pairs / SEGMENT
+    flop = eval_pairs * FP32_FLOP_PER_PAIR + tests * BOX_TEST_FLOP
+    ach = flop / (score_ms * 1e-3) / 1e12 if score_ms > 0 else 0.0
+    eff = score_pairs * FP32_FLOP_PER_PAIR / (score_ms * 1e-3) / 1e12 if score_ms > 0 else 0.0
     roof = {'kernel': 'k_score', 'bound': 'alu', 'achieved': ach, 'peak': peak_tflops,
             'unit': 'TFLOP/s', 'frac': ach / peak_tflops,
-            'traffic': SCORE_DRAM_BYTES_PER_PAIR * score_pairs / n_score,
+            'traffic': (SCORE_DRAM_BYTES_PER_PAIR * score_pairs / n_score
+                        if SCORE_DRAM_BYTES_PER_PAIR else None),
             'traffic_note': 'bytes per launch, scaled from an ncu capture of round 0 of 32 frames '
-                            'by pairs scored; algorithmic bytes are 16 B per candidate per launch',
+                            'by pairs scored; algorithmic bytes are 16 B per candidate per '
+                            'hypothesis block',
             'peak_source': 'derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (%s peaks file)'
                            % (SM_COUNT, FP32_LANES, clock_mhz, pk_kind),
-            'work': '%d FLOP per hypothesis-point pair; %.3e pairs over %d launches'
-                    % (FP32_FLOP_PER_PAIR, score_pairs, n_score),
+            'work': '%d FLOP per evaluated hypothesis-candidate pair + %d FLOP per box test '
+                    '(hypothesis x %d-candidate segment); %.3e of %.3e pairs evaluated '
+                    '(%.1f%%) over %d launches'
+                    % (FP32_FLOP_PER_PAIR, BOX_TEST_FLOP, SEGMENT, eval_pairs, score_pairs,
+                       100.0 * eval_pairs / max(1, score_pairs), n_score),
+            'effective': {'achieved': eff, 'frac': eff / peak_tflops,
+                          'note': 'all H x M pairs x 8 FLOP / time, skipped pairs included'},
             'kernel_ms_per_step': score_ms / args.steps,
             'share_of_step': (score_ms / args.steps) / (tot_ms / args.steps) if world == 1 else None}
 
     hbm = diffusion_hbm(torch, pm, dev, pk) if not args.skip_hbm else None
+    regions = run_regions(torch, pm, pipe, frames, dframes, pk) if not args.skip_regions else None
     served = run_served(torch, pm, args, frames, dframes) if args.served_seconds > 0 else None
 
     cpu = None
@@ -368,7 +423,7 @@ def run_ours(args):
             'latency_ms': {'p50': percentile(step_ms, 50), 'p99': percentile(step_ms, 99),
                            'note': 'a batched frame completes with its step'},
             'plain': plain, 'speedup_vs_plain': value / world / plain['value'],
-            'served': served,
+            'served': served, 'regions': regions,
             'e2e': e2e, 'roofline': roof, 'diffusion_hbm': hbm, 'cpu_baseline': cpu,
             'gpu_launches': launches, 'clocks': clk,
             'paper_context': '>30 Hz whole pipeline; 7.5 ms/frame; <15 ms at 640x480 with 10 '
@@ -391,6 +446,7 @@ def main():
     ap.add_argument('--plain-frames', type=int, default=32)
     ap.add_argument('--skip-cpu', action='store_true')
     ap.add_argument('--skip-hbm', action='store_true')
+    ap.add_argument('--skip-regions', action='store_true')
     ap.add_argument('--no-tune', action='store_true')
     ap.add_argument('--served-seconds', type=float, default=60.0)
     args = ap.parse_args()

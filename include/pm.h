@@ -250,13 +250,15 @@ long long pm_scratch_bytes(int max_w, int max_h, int max_frames, int hypotheses,
  * call's [0] diffusion, [1] normals, [2] RANSAC.  pm_set_timing(ctx, 2):
  * events around every scoring launch (captured into graphs too);
  * pm_kernel_stats then returns the scoring kernels' summed device time (ms),
- * the hypothesis-point pairs they scored and their launch count.  In every
+ * the hypothesis-point pairs they scored (H x candidates per round), the
+ * pairs actually evaluated (the rest were proven inlier-free by the box
+ * test) and their launch count.  In every
  * mode pm_kernel_stats returns in *launches the number of kernels the last
  * call launched.  Any output pointer may be NULL. */
 pm_status pm_set_timing(pm_ctx *ctx, int on);
 pm_status pm_stage_times(pm_ctx *ctx, float ms[3]);
 pm_status pm_kernel_stats(pm_ctx *ctx, float *score_ms, long long *score_pairs,
-                          int *score_launches, long long *launches);
+                          long long *evaluated_pairs, int *score_launches, long long *launches);
 
 /* Allocation-free diffusion.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc, e.g. a hard real-time

@@ -95,8 +95,8 @@ def load(path: str = LIB_PATH):
         'pm_scratch_bytes': ([i, i, i, i, i], ctypes.c_longlong),
         'pm_set_timing': ([vp, i], i),
         'pm_stage_times': ([vp, P(ctypes.c_float)], i),
-        'pm_kernel_stats': ([vp, P(ctypes.c_float), P(ctypes.c_longlong), P(i),
-                             P(ctypes.c_longlong)], i),
+        'pm_kernel_stats': ([vp, P(ctypes.c_float), P(ctypes.c_longlong), P(ctypes.c_longlong),
+                             P(i), P(ctypes.c_longlong)], i),
         'pm_ransac_regions': ([vp, vp, vp, vp, i, i, i, i, u64, P(RegionPlane), vp], i),
         'pm_diffuse_noalloc': ([vp, i, i, i, i, P(DiffusionParams), ctypes.c_float, vp, vp], i),
         'pm_set_tiling': ([vp, i, i, i], i),

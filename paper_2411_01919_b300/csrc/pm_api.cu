@@ -350,6 +350,7 @@ RParams ransac_params(const pm_ctx *ctx)
     p.min_inliers = ctx->rp.min_inliers;
     p.seed = ctx->rp.seed;
     p.cos_gate = (float)std::cos((double)ctx->rp.refit_normal_gate_deg * M_PI / 180.0);
+    p.cull_thr = std::nextafter((float)(std::sqrt((double)p.thr2) * (1.0 + 0x1p-20)), INFINITY);
     return p;
 }
 
@@ -363,10 +364,12 @@ pm_status enqueue_ransac(pm_ctx *ctx, RFrame *d_rframes, int n, long long total_
     L.d_chunk_base = ctx->at<int>(ctx->lay.chunk_base);
     L.max_total_chunks = (int)total_chunks;
     L.prm = ransac_params(ctx);
-    long long sb = (long long)ctx->sms * 8, cb = (long long)ctx->sms * 4;
     L.d_counter = ctx->at<unsigned>(ctx->lay.counter);
     L.fine_score = total_chunks < (long long)ctx->sms * 32;
-    const long long score_items = total_chunks * (L.fine_score ? 4 : 1);
+    const int hb = score_hyp_block(L.fine_score, L.prm.H);
+    const long long score_items = total_chunks * ((L.prm.H + hb - 1) / hb);
+    const long long sb = (long long)ctx->sms * score_ctas_per_sm(L.fine_score, L.prm.H);
+    const long long cb = (long long)ctx->sms * 4;
     L.score_blocks = (int)(score_items < sb ? score_items : sb);
     L.chunk_blocks = (int)(total_chunks < cb ? total_chunks : cb);
     if (L.score_blocks < 1)
@@ -583,6 +586,8 @@ pm_status pm_create(const pm_diffusion_params *dp, const pm_ransac_params *rp,
         e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e == cudaSuccess)
         e = diffuse_init();
+    if (e == cudaSuccess)
+        e = score_init();
     if (e != cudaSuccess)
         return bail(fail(PM_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e)));
     e = cudaMalloc(&ctx->arena, ctx->lay.total);
@@ -972,7 +977,7 @@ pm_status pm_set_timing(pm_ctx *ctx, int on)
 }
 
 pm_status pm_kernel_stats(pm_ctx *ctx, float *score_ms, long long *score_pairs,
-                          int *score_launches, long long *launches)
+                          long long *evaluated_pairs, int *score_launches, long long *launches)
 {
     if (!ctx)
         return fail(PM_ERR_ARG, "null context");
@@ -981,7 +986,9 @@ pm_status pm_kernel_stats(pm_ctx *ctx, float *score_ms, long long *score_pairs,
     if (ctx->timing != 2)
         return PM_OK;
     float tot = 0.0f;
-    long long pairs = 0;
+    long long pairs = 0, evaluated = 0;
+    for (int f = 0; f < ctx->last_n; ++f)
+        evaluated += (long long)ctx->h_state[f].pairs_eval;
     for (int r = 0; r < ctx->rp.max_planes; ++r) {
         float ms = 0.0f;
         PM_CK(cudaEventElapsedTime(&ms, ctx->kev[2 * r], ctx->kev[2 * r + 1]));
@@ -993,6 +1000,8 @@ pm_status pm_kernel_stats(pm_ctx *ctx, float *score_ms, long long *score_pairs,
         *score_ms = tot;
     if (score_pairs)
         *score_pairs = pairs;
+    if (evaluated_pairs)
+        *evaluated_pairs = evaluated;
     if (score_launches)
         *score_launches = ctx->rp.max_planes;
     return PM_OK;

@@ -66,6 +66,7 @@ struct RState {
     float4 best_plane;
     float4 p0;        // first sample point of the winner (moment origin)
     int m_hist[MAX_PLANES];  // candidates scored in each round (0 once stopped)
+    unsigned long long pairs_eval;  // hypothesis-candidate pairs evaluated (not culled)
 };
 
 struct RFrame {
@@ -94,6 +95,7 @@ struct RParams {
     int min_inliers;
     unsigned long long seed;
     float cos_gate;
+    float cull_thr;      // >= sqrt(thr2) (1 + 2^-20): threshold of the scoring box test
 };
 
 // ---------------------------------------------------------------------------
@@ -197,7 +199,7 @@ struct RansacLaunch {
     int score_blocks;     // persistent grid sizes
     int chunk_blocks;
     unsigned *d_counter;  // grid-completion counter of the compaction kernel
-    bool fine_score;      // finer scoring work items (small batches)
+    bool fine_score;      // smaller hypothesis blocks, selection fused (small batches)
 };
 // Per-region RANSAC (regions.cu): all pointers device memory.
 struct RegionLaunch {
@@ -221,6 +223,9 @@ struct RegionLaunch {
 cudaError_t ransac_regions(const RegionLaunch &L, int sms, cudaStream_t s);
 
 cudaError_t ransac_init(const RansacLaunch &L, cudaStream_t s);
+cudaError_t score_init();                  // shared-memory opt-in and occupancy of k_score
+int score_hyp_block(bool fine, int H);     // hypotheses per scoring work item
+int score_ctas_per_sm(bool fine, int H);
 // ev_score: optional event pair recorded around the scoring launch.
 cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream_t s,
                          cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);

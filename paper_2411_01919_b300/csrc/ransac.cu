@@ -5,8 +5,9 @@
 //   k_hyp     : Philox4x64-10 -> three candidate indices -> FP32 plane (Alg. 2
 //               "select random subset of 3 points", "fit plane model")
 //   k_score   : every hypothesis against every candidate on FP32 CUDA cores
-//               (Alg. 2 inner parallel loop); integer counters per thread, one
-//               atomic add per (work item, hypothesis).  The CTA that finishes
+//               (Alg. 2 inner parallel loop), skipping the pairs that a box
+//               test proves to hold no inlier; integer counters, one atomic
+//               add per (work item, hypothesis).  The CTA that finishes
 //               a frame's last work item picks the frame's winner: the
 //               maximum count, ties to the lowest index (integer key).
 //   k_remove  : labels of the winner's inliers, keep bitmask of the rest,
@@ -118,6 +119,7 @@ __device__ void plan_round(RFrame *frames, int n, int *chunk_base, int min_inlie
             st->best_count = -1;
             for (int r = 0; r < MAX_PLANES; ++r)
                 st->m_hist[r] = 0;
+            st->pairs_eval = 0ull;
             nc = (F.npx + CHUNK - 1) / CHUNK;
         } else {
             if (!st->done) {
@@ -366,69 +368,228 @@ __device__ void select_winner(const RFrame &F, const RParams &prm)
 }
 
 // ---------------------------------------------------------------------------
-// scoring.  A work item is (chunk, sub-chunk, hypothesis block): SUBS
-// sub-chunks of CHUNK / SUBS candidates, NHB blocks of 128 * HPT hypotheses.
-// HPT hypotheses per thread live in registers, the sub-chunk in shared memory
-// (one broadcast 16-byte load per point).  Per pair: the three residual FMAs,
-// one FMA for r*r - thr^2, and one integer add of that value's sign bit,
-// which is set iff it is negative (an exact zero rounds to +0, a degenerate
-// plane gives +inf): the same decision as is_inlier().  (Packed f32x2 FMAs
-// were measured slower here: they issue to one FMA pipe.)
+// scoring with exact box culling.
+//
+// A work item is (frame, chunk of CHUNK candidates, block of HB hypotheses).
+// The chunk is cut into segments of SEG consecutive candidates (a few pixels
+// of one image row, so a small patch of one surface); each segment gets an
+// axis-aligned box [c - e, c + e] that holds its points.  A hypothesis whose
+// plane stays farther than the threshold from the whole box, by a margin that
+// covers every rounding of the FP32 residual and of the test, has no inlier
+// in the segment: its count there is exactly 0 and the pair is not
+// evaluated.  The counts, and every decision taken from them, are the ones of
+// evaluating all pairs.
+//
+// The margin.  u = 2^-24.  The residual r~ = fma(nz,pz,fma(ny,py,fma(nx,px,d)))
+// is within 3.0000004 u B of n.p + d, B = |n|.|p| + |d| <= |n|.(|c| + e) + |d|.
+// A hypothesis is culled when, in FP32,
+//     |n.c + d|  >  |n|.g + w,   g = e + s (|c| + e),  w = thr' + s |d|,
+// with s = 2^-18 (64 u), thr' >= sqrt(thr2) (1 + 2^-20), and g, w rounded up.
+// Following the roundings through (each FP32 step of the test is off by at
+// most a few u), every point of the box then has |r~| > sqrt(thr2), so
+// fma(r~, r~, -thr2) >= 0: not an inlier.  A NaN anywhere keeps the pair.
+//
+// Per segment a warp tests all HB hypotheses (one per lane, ballot) into a
+// list of survivors, then scores the list up to four hypotheses per lane
+// against the segment's points (broadcast 16-byte loads from shared memory).  Per pair:
+// three residual FMAs, one FMA for r*r - thr2 and one integer add of its sign
+// bit, which is set iff it is negative (an exact zero rounds to +0): the
+// decision of is_inlier().  Counts go to shared memory, then once per work
+// item to global memory.
 // ---------------------------------------------------------------------------
-template <int HPT, int NHB, int SUBS, bool FUSE>
-__global__ void __launch_bounds__(128) k_score(RFrame *frames, int n, const int *chunk_base,
-                                               RParams prm, int round)
+constexpr int SEG = 32;
+constexpr int NSEG = CHUNK / SEG;
+constexpr int SCORE_THREADS = 256;
+constexpr int SCORE_WARPS = SCORE_THREADS / 32;
+constexpr float CULL_SLACK = 0x1p-18f;
+
+template <int HB>
+constexpr size_t score_smem_bytes()
 {
-    constexpr int SUB = CHUNK / SUBS;
-    constexpr int PER = NHB * SUBS;
-    __shared__ float4 pts[SUB];
-    const int total = chunk_base[n] * PER;
-    const float nthr2 = -prm.thr2;
+    return (size_t)CHUNK * 16 + (size_t)HB * 16 + (size_t)HB * 4 + (size_t)NSEG * 32 +
+           (size_t)HB * 4 + (size_t)SCORE_WARPS * HB * 2;
+}
+
+// E surviving hypotheses per lane (list entries e0 + lane + 32 i) against the
+// sc points of one segment; counts added to shared memory.
+template <int E, bool FULL>
+__device__ __forceinline__ void score_batch(const float4 *__restrict__ hpl,
+                                            const unsigned short *__restrict__ lst, int e0,
+                                            int len, const float4 *__restrict__ sp, int sc,
+                                            float nthr2, int *hcnt, int lane)
+{
     const float4 none = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+    int k[E];
+    float4 pl[E];
+    unsigned acc[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int e = e0 + lane + 32 * i;
+        k[i] = e < len ? (int)lst[e] : -1;
+        pl[i] = k[i] >= 0 ? hpl[k[i]] : none;
+        acc[i] = 0u;
+    }
+    const int n = FULL ? SEG : sc;
+#pragma unroll(FULL ? 8 : 1)
+    for (int j = 0; j < n; ++j) {
+        const float4 p = sp[j];
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            float r = __fmaf_rn(pl[i].x, p.x, pl[i].w);
+            r = __fmaf_rn(pl[i].y, p.y, r);
+            r = __fmaf_rn(pl[i].z, p.z, r);
+            acc[i] += __float_as_uint(__fmaf_rn(r, r, nthr2)) >> 31;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < E; ++i)
+        if (acc[i])
+            atomicAdd(hcnt + k[i], (int)acc[i]);
+}
+
+template <bool FULL>
+__device__ __forceinline__ void score_list(const float4 *hpl, const unsigned short *lst, int len,
+                                           const float4 *sp, int sc, float nthr2, int *hcnt,
+                                           int lane)
+{
+    int e0 = 0;
+    while (len - e0 >= 128) {
+        score_batch<4, FULL>(hpl, lst, e0, len, sp, sc, nthr2, hcnt, lane);
+        e0 += 128;
+    }
+    while (len - e0 > 32) {
+        score_batch<2, FULL>(hpl, lst, e0, len, sp, sc, nthr2, hcnt, lane);
+        e0 += 64;
+    }
+    if (len - e0 > 0)
+        score_batch<1, FULL>(hpl, lst, e0, len, sp, sc, nthr2, hcnt, lane);
+}
+
+template <int HB, bool FUSE>
+__global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
+                                                         const int *chunk_base, RParams prm,
+                                                         int round)
+{
+    extern __shared__ float4 sm[];
+    float4 *pts = sm;                  // [CHUNK] candidates of the chunk
+    float4 *hpl = pts + CHUNK;         // [HB] planes (nx, ny, nz, d)
+    float4 *box = hpl + HB;            // [NSEG][2] centre c; widened half-size g
+    float *hw = reinterpret_cast<float *>(box + 2 * NSEG);               // [HB] w
+    int *hcnt = reinterpret_cast<int *>(hw + HB);                        // [HB]
+    unsigned short *lst = reinterpret_cast<unsigned short *>(hcnt + HB);  // [warps][HB]
+    __shared__ int next_seg;
+    __shared__ unsigned long long evaluated;
+    const int nhb = (prm.H + HB - 1) / HB;
+    const int total = chunk_base[n] * nhb;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const float nthr2 = -prm.thr2;
+    unsigned short *my = lst + wid * HB;
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
-        const int wi = it / PER, rem = it - wi * PER;
-        const int sub = rem / NHB, hb = rem - sub * NHB;
+        const int wi = it / nhb, hb = it - wi * nhb;
         const int f = frame_of(chunk_base, n, wi);
         const RFrame &F = frames[f];
         RState *st = F.st;
         const int c = wi - chunk_base[f];
-        const int M = st->M;
-        const int base = c * CHUNK + sub * SUB;
-        const int cnt = max(0, min(SUB, M - base));
+        const int base = c * CHUNK;
+        const int cnt = max(0, min(CHUNK, st->M - base));
+        const int h0 = hb * HB;
+        const int nh = min(HB, prm.H - h0);
         const float4 *src = F.cpt[round & 1] + base;
         __syncthreads();
-        for (int j = threadIdx.x; j < cnt; j += blockDim.x)
+        for (int j = threadIdx.x; j < cnt; j += SCORE_THREADS)
             pts[j] = src[j];
-        float4 pl[HPT];
-        const int h0 = hb * (128 * HPT) + threadIdx.x;
-#pragma unroll
-        for (int k = 0; k < HPT; ++k) {
-            const int h = h0 + k * 128;
-            pl[k] = h < prm.H ? F.hyp[h] : none;
+        for (int k = threadIdx.x; k < HB; k += SCORE_THREADS) {
+            float4 pl = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+            float w = -1.0f;                     // culls everywhere
+            if (k < nh) {
+                const float4 q = F.hyp[h0 + k];
+                if (fabsf(q.w) <= 3.0e38f) {     // degenerate planes carry d = +inf
+                    pl = q;
+                    w = __fmaf_ru(CULL_SLACK, fabsf(q.w), prm.cull_thr);
+                }
+            }
+            hpl[k] = pl;
+            hw[k] = w;
+            hcnt[k] = 0;
+        }
+        if (threadIdx.x == 0) {
+            next_seg = 0;
+            evaluated = 0ull;
         }
         __syncthreads();
-        unsigned acc[HPT];
+        const int nseg = (cnt + SEG - 1) / SEG;
+        for (int sg = wid; sg < nseg; sg += SCORE_WARPS) {
+            const float4 p = pts[min(sg * SEG + lane, cnt - 1)];
+            float lx = p.x, ly = p.y, lz = p.z, ux = p.x, uy = p.y, uz = p.z;
 #pragma unroll
-        for (int k = 0; k < HPT; ++k)
-            acc[k] = 0u;
-#pragma unroll 2
-        for (int j = 0; j < cnt; ++j) {
-            const float4 p = pts[j];
-#pragma unroll
-            for (int k = 0; k < HPT; ++k) {
-                float r = __fmaf_rn(pl[k].x, p.x, pl[k].w);
-                r = __fmaf_rn(pl[k].y, p.y, r);
-                r = __fmaf_rn(pl[k].z, p.z, r);
-                acc[k] += __float_as_uint(__fmaf_rn(r, r, nthr2)) >> 31;
+            for (int o = 16; o > 0; o >>= 1) {
+                lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+                ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+                lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+                ux = fmaxf(ux, __shfl_xor_sync(0xffffffffu, ux, o));
+                uy = fmaxf(uy, __shfl_xor_sync(0xffffffffu, uy, o));
+                uz = fmaxf(uz, __shfl_xor_sync(0xffffffffu, uz, o));
+            }
+            if (lane < 3) {
+                // lane k handles axis k: centre, half-size rounded up and
+                // widened by the centre's rounding, then g = e + s (|c| + e)
+                const float lo = lane == 0 ? lx : lane == 1 ? ly : lz;
+                const float hi = lane == 0 ? ux : lane == 1 ? uy : uz;
+                const float cc = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+                const float e = __fadd_ru(__fmul_ru(__fsub_ru(hi, lo), 0.5f),
+                                          __fmul_ru(fabsf(cc), 0x1p-23f));
+                const float g = __fmaf_ru(CULL_SLACK, __fadd_ru(fabsf(cc), e), e);
+                float *b = reinterpret_cast<float *>(box + 2 * sg);
+                b[lane] = cc;
+                b[4 + lane] = g;
             }
         }
-#pragma unroll
-        for (int k = 0; k < HPT; ++k) {
-            const int h = h0 + k * 128;
-            if (h < prm.H && acc[k] > 0u)
-                atomicAdd(F.counts + h, (int)acc[k]);
+        __syncthreads();
+        unsigned long long mine = 0ull;
+        for (;;) {
+            int sg = 0;
+            if (lane == 0)
+                sg = atomicAdd(&next_seg, 1);
+            sg = __shfl_sync(0xffffffffu, sg, 0);
+            if (sg >= nseg)
+                break;
+            const float4 bc = box[2 * sg], bg = box[2 * sg + 1];
+            int len = 0;
+            for (int k = lane; k < nh + ((32 - (nh & 31)) & 31); k += 32) {
+                const float4 pl = hpl[k];
+                float t = __fmaf_rn(pl.x, bc.x, pl.w);
+                t = __fmaf_rn(pl.y, bc.y, t);
+                t = __fmaf_rn(pl.z, bc.z, t);
+                float lim = __fmaf_rn(fabsf(pl.x), bg.x, hw[k]);
+                lim = __fmaf_rn(fabsf(pl.y), bg.y, lim);
+                lim = __fmaf_rn(fabsf(pl.z), bg.z, lim);
+                const bool keep = !(fabsf(t) > lim);
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (keep)
+                    my[len + __popc(m & lt)] = (unsigned short)k;
+                len += __popc(m);
+            }
+            __syncwarp();
+            const int sc = min(SEG, cnt - sg * SEG);
+            mine += (unsigned long long)len * (unsigned)sc;
+            if (sc == SEG)
+                score_list<true>(hpl, my, len, pts + sg * SEG, sc, nthr2, hcnt, lane);
+            else
+                score_list<false>(hpl, my, len, pts + sg * SEG, sc, nthr2, hcnt, lane);
+            __syncwarp();   // the list is rewritten for the next segment
         }
-        if (FUSE && last_item_of_frame(&st->score_done, st->nchunks * PER))
+        if (lane == 0 && mine)
+            atomicAdd(&evaluated, mine);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nh; k += SCORE_THREADS) {
+            const int v = hcnt[k];
+            if (v)
+                atomicAdd(F.counts + h0 + k, v);
+        }
+        if (threadIdx.x == 0 && evaluated)
+            atomicAdd(&st->pairs_eval, evaluated);
+        if (FUSE && last_item_of_frame(&st->score_done, st->nchunks * nhb))
             select_winner(F, prm);
     }
 }
@@ -807,11 +968,43 @@ cudaError_t ransac_init(const RansacLaunch &L, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int HPT, int NHB, int SUBS, bool FUSE>
+template <int HB, bool FUSE>
 static void launch_score(const RansacLaunch &L, int round, cudaStream_t s)
 {
-    k_score<HPT, NHB, SUBS, FUSE><<<L.score_blocks, 128, 0, s>>>(L.d_frames, L.n,
-                                                                 L.d_chunk_base, L.prm, round);
+    k_score<HB, FUSE><<<L.score_blocks, SCORE_THREADS, score_smem_bytes<HB>(), s>>>(
+        L.d_frames, L.n, L.d_chunk_base, L.prm, round);
+}
+
+template <int HB, bool FUSE>
+static cudaError_t score_attr(int *ctas)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_score<HB, FUSE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)score_smem_bytes<HB>());
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_score<HB, FUSE>, SCORE_THREADS,
+                                                          score_smem_bytes<HB>());
+    return e;
+}
+
+static int g_score_ctas[3] = {1, 1, 1};   // CTAs per SM: <256,true>, <256,false>, <512,false>
+
+cudaError_t score_init()
+{
+    cudaError_t e = score_attr<256, true>(&g_score_ctas[0]);
+    if (e == cudaSuccess)
+        e = score_attr<256, false>(&g_score_ctas[1]);
+    if (e == cudaSuccess)
+        e = score_attr<512, false>(&g_score_ctas[2]);
+    return e;
+}
+
+int score_hyp_block(bool fine, int H) { return fine || H <= 256 ? 256 : 512; }
+
+int score_ctas_per_sm(bool fine, int H)
+{
+    const int v = fine ? g_score_ctas[0] : H <= 256 ? g_score_ctas[1] : g_score_ctas[2];
+    return v > 0 ? v : 1;
 }
 
 cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream_t s,
@@ -827,15 +1020,12 @@ cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream
     // small batches also fold the selection into the scoring launch and the
     // refit into the removal launch
     const bool fine = L.fine_score;
-    if (p.H <= 256) {
-        if (fine) launch_score<2, 1, 2, true>(L, round, s); else launch_score<2, 1, 1, false>(L, round, s);
-    } else if (p.H <= 512) {
-        if (fine) launch_score<4, 1, 2, true>(L, round, s); else launch_score<4, 1, 1, false>(L, round, s);
-    } else if (p.H <= 1024) {
-        if (fine) launch_score<4, 2, 2, true>(L, round, s); else launch_score<8, 1, 1, false>(L, round, s);
-    } else {
-        if (fine) launch_score<8, 2, 2, true>(L, round, s); else launch_score<16, 1, 1, false>(L, round, s);
-    }
+    if (fine)
+        launch_score<256, true>(L, round, s);
+    else if (p.H <= 256)
+        launch_score<256, false>(L, round, s);
+    else
+        launch_score<512, false>(L, round, s);
     if (ev_after)
         record_event(ev_after, s);
     if (!fine)

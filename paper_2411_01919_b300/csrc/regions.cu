@@ -58,20 +58,41 @@ __global__ void k_reg_reset(RegionLaunch L)
     }
 }
 
+// Pixel -> region of a valid member, or -1.
+__device__ __forceinline__ int member_region(const RegionLaunch &L, int u, int v)
+{
+    if (u >= L.w || v >= L.h)
+        return -1;
+    const long long p = (long long)v * L.w + u;
+    const int r = L.regions[p];
+    return (r < 0 || r >= L.R || !(L.valid[p] & 1)) ? -1 : r;
+}
+
+// Point count and bounding box of every region.  The lanes of a warp that
+// hold the same region are combined first (a warp covers 32 pixels of one
+// row, mostly of one region), so a region gets one atomic per warp instead
+// of one per pixel.
 __global__ void k_reg_stats(RegionLaunch L)
 {
     const int u = blockIdx.x * 32 + threadIdx.x, v = blockIdx.y * 8 + threadIdx.y;
-    if (u >= L.w || v >= L.h)
-        return;
-    const long long p = (long long)v * L.w + u;
-    const int r = L.regions[p];
-    if (r < 0 || r >= L.R || !(L.valid[p] & 1))
-        return;
-    atomicAdd(L.cnt + r, 1);
-    atomicMin(L.box + 4 * r + 0, u);
-    atomicMin(L.box + 4 * r + 1, v);
-    atomicMax(L.box + 4 * r + 2, u);
-    atomicMax(L.box + 4 * r + 3, v);
+    const int r = member_region(L, u, v);
+    unsigned todo = __ballot_sync(0xffffffffu, r >= 0);
+    while (todo) {
+        const int lead = __ffs(todo) - 1;
+        const int rr = __shfl_sync(0xffffffffu, r, lead);
+        const bool in = r == rr;
+        const unsigned grp = __ballot_sync(0xffffffffu, in);
+        const unsigned u0 = __reduce_min_sync(0xffffffffu, in ? (unsigned)u : 0xffffffffu);
+        const unsigned u1 = __reduce_max_sync(0xffffffffu, in ? (unsigned)u : 0u);
+        if ((int)threadIdx.x == lead) {
+            atomicAdd(L.cnt + rr, __popc(grp));
+            atomicMin(L.box + 4 * rr + 0, (int)u0);
+            atomicMin(L.box + 4 * rr + 1, v);
+            atomicMax(L.box + 4 * rr + 2, (int)u1);
+            atomicMax(L.box + 4 * rr + 3, v);
+        }
+        todo &= ~grp;
+    }
 }
 
 // One block: exclusive prefix of the point counts (list offsets, scatter
@@ -138,18 +159,29 @@ __global__ void __launch_bounds__(1024) k_reg_scan(RegionLaunch L)
         L.chunk_base[L.R] = carry_b;
 }
 
+// Region-grouped point list: one cursor atomic per (warp, region).
 __global__ void k_reg_scatter(RegionLaunch L)
 {
     const int u = blockIdx.x * 32 + threadIdx.x, v = blockIdx.y * 8 + threadIdx.y;
-    if (u >= L.w || v >= L.h)
-        return;
-    const long long p = (long long)v * L.w + u;
-    const int r = L.regions[p];
-    if (r < 0 || r >= L.R || !(L.valid[p] & 1))
-        return;
-    const int pos = atomicAdd(L.cursor + r, 1);
-    const long long npx = (long long)L.w * L.h;
-    L.list[pos] = make_float4(L.P[p], L.P[npx + p], L.P[2 * npx + p], 0.0f);
+    const int r = member_region(L, u, v);
+    const unsigned lt = (1u << threadIdx.x) - 1u;
+    unsigned todo = __ballot_sync(0xffffffffu, r >= 0);
+    while (todo) {
+        const int lead = __ffs(todo) - 1;
+        const int rr = __shfl_sync(0xffffffffu, r, lead);
+        const bool in = r == rr;
+        const unsigned grp = __ballot_sync(0xffffffffu, in);
+        int pos = 0;
+        if ((int)threadIdx.x == lead)
+            pos = atomicAdd(L.cursor + rr, __popc(grp));
+        pos = __shfl_sync(0xffffffffu, pos, lead) + __popc(grp & lt);
+        if (in) {
+            const long long p = (long long)v * L.w + u;
+            const long long npx = (long long)L.w * L.h;
+            L.list[pos] = make_float4(L.P[p], L.P[npx + p], L.P[2 * npx + p], 0.0f);
+        }
+        todo &= ~grp;
+    }
 }
 
 __global__ void __launch_bounds__(128) k_reg_hyp(RegionLaunch L)

@@ -308,11 +308,14 @@ class Pipeline:
     def kernel_stats(self):
         ms = ctypes.c_float(0)
         pairs = ctypes.c_longlong(0)
+        evaluated = ctypes.c_longlong(0)
         nl = ctypes.c_int(0)
         launches = ctypes.c_longlong(0)
         check(self.lib.pm_kernel_stats(self._h, ctypes.byref(ms), ctypes.byref(pairs),
-                                       ctypes.byref(nl), ctypes.byref(launches)))
-        return {'score_ms': ms.value, 'score_pairs': pairs.value, 'score_launches': nl.value,
+                                       ctypes.byref(evaluated), ctypes.byref(nl),
+                                       ctypes.byref(launches)))
+        return {'score_ms': ms.value, 'score_pairs': pairs.value,
+                'evaluated_pairs': evaluated.value, 'score_launches': nl.value,
                 'launches': launches.value}
 
     def stage_times(self):

@@ -348,4 +348,5 @@ def test_graph_replay_records_kernel_timing_events():
                 pipe.process_batch(batch, use_graph=True)       # replay
             st = pipe.kernel_stats()
             assert st['score_ms'] > 0 and st['score_pairs'] > 0
+            assert 0 < st['evaluated_pairs'] <= st['score_pairs']
             assert st['launches'] >= 3 + 4 * p.max_planes - 1
