@@ -37,7 +37,7 @@ FP32_FLOP_PER_PAIR = 8          # 3 FMA residual + 1 FMA squared-threshold test
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on round 0
 # of 32 frames of this workload: 156.4 MB for 9.73e9 pairs.  With the number
 # of hypotheses fixed, traffic grows with the candidate count, i.e. with pairs.
-SCORE_DRAM_BYTES_PER_PAIR = None   # ncu dram bytes per scored pair (k_score), when captured
+SCORE_DRAM_BYTES_PER_PAIR = (152.73e6 + 3.60e6) / 9.73e9   # ncu, k_score round 0, 32 frames
 SEGMENT, BOX_TEST_FLOP = 32, 12
 REGION_FLOP_PER_PAIR = 9     # 3 FMA residual, |r| x 2^32, 1 FMA inlier test
 SM_COUNT, FP32_LANES = 148, 128

@@ -233,6 +233,48 @@ def test_ransac_without_normals_uses_all_inliers():
     assert np.array_equal(g.n_refit, orc.n_refit)
 
 
+def threshold_slab_scene(z0, half_w, thr, h=64, w=128):
+    """Points on the plane z = z0 (rows 0-39) and rows of points offset along
+    z by thr (1 -/+ 2^-22), above or below, just inside or just outside the
+    threshold: each row is four whole 32-point segments whose boxes lie at
+    the threshold distance from planes near z = z0."""
+    xs = np.linspace(-half_w, half_w, w, dtype=np.float64)
+    ys = np.linspace(-0.6 * half_w, 0.6 * half_w, h, dtype=np.float64)
+    X, Y = np.meshgrid(xs, ys)
+    Z = np.full((h, w), z0, dtype=np.float64)
+    t32 = float(np.float32(thr))
+    for v in range(40, h):
+        k = v - 40
+        sign = 1.0 if k % 2 == 0 else -1.0          # above / below the plane
+        rel = (1.0 - 2.0 ** -22) if (k // 2) % 2 == 0 else (1.0 + 2.0 ** -22)
+        Z[v, :] = z0 + sign * t32 * rel
+    P = np.stack([X, Y, Z]).astype(np.float32)
+    V = np.ones((h, w), dtype=np.uint8)
+    return P, V
+
+
+@pytest.mark.parametrize('z0,half_w', [(1.5, 0.5), (9.5, 6.0)])
+def test_box_culling_keeps_threshold_inliers(z0, half_w):
+    """The scoring kernel skips pairs by a box test; segments that sit at the
+    threshold distance from the winning plane must be decided exactly as
+    the oracle (which evaluates every pair) decides them."""
+    thr = 0.01
+    P, V = threshold_slab_scene(z0, half_w, thr)
+    h, w = V.shape
+    p = Params(iters=0, hypotheses=512, thr=thr, max_planes=2, min_inliers=50, seed=4)
+    orc = oracle.ransac(P, None, V, p.hypotheses, p.thr, p.max_planes, p.min_inliers, p.seed,
+                        p.gate_deg, 0)
+    with Pipeline(p, w, h) as pipe:
+        g = pipe.ransac_planes(to_dev(P), None, to_dev(V), frame_idx=0)
+        lab = g.labels.cpu().numpy()
+    assert np.array_equal(g.hyp_index, orc.hyp_index)
+    assert np.array_equal(g.n_inliers, orc.n_inliers)
+    assert np.array_equal(lab, orc.labels)
+    # the scene does put points of the winning plane within 1e-6 m of the
+    # threshold, where a box test without a sound margin would drop inliers
+    assert orc.band[0] > 0
+
+
 # ---------------------------------------------------------------------------
 # the whole path
 # ---------------------------------------------------------------------------
