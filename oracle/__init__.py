@@ -19,6 +19,11 @@ Parity status per function (what pins it is listed in the test suite):
   ransac_regions  pinned (sample uniformity and region membership, FP64 brute-force
                   distance sums per hypothesis, argmin rule, acceptance on single-
                   and two-plane regions, ground-truth planes of a staircase)
+  canny           pinned (step edges of known position and width, sector test
+                  against atan2, hysteresis against scipy.ndimage.label, edges of
+                  straight lines at many angles are thin and on the line)
+  segment         pinned (scipy.ndimage.label with 4-connectivity, size filter,
+                  raster numbering)
 """
 from __future__ import annotations
 
@@ -77,6 +82,12 @@ def lib():
                                         ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                         ctypes.c_uint64, P]
         L.or_region_samples.restype = ctypes.c_int
+        L.or_canny.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
+        L.or_canny_sector.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.or_canny_sector.restype = ctypes.c_int
+        L.or_canny.restype = ctypes.c_long
+        L.or_segment.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+        L.or_segment.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -235,6 +246,38 @@ def region_samples(valid: np.ndarray, regions: np.ndarray, n_regions: int, r: in
     ok = lib().or_region_samples(_p(Rg), _p(V), w, h, n_regions, r, hyp, seed, frame_idx,
                                  _p(out))
     return out if ok else None
+
+
+def canny(N32: np.ndarray, valid: np.ndarray, low: int = 60, high: int = 150,
+          states: bool = False):
+    """Canny edges of the 8-bit normal image (Sec. III-D); u8 [h, w], 1 = edge.
+    states=True also returns the pre-hysteresis state image (0/1/2)."""
+    N = np.ascontiguousarray(N32, dtype=np.float32)
+    _, h, w = N.shape
+    V = np.ascontiguousarray(valid, dtype=np.uint8)
+    out = np.zeros((h, w), dtype=np.uint8)
+    st = np.zeros((h, w), dtype=np.uint8) if states else None
+    rc = lib().or_canny(_p(N), _p(V), w, h, low, high, _p(out), _p(st))
+    if rc < 0:
+        raise ValueError('or_canny failed (%d)' % rc)
+    return (out, st) if states else out
+
+
+def canny_sector(gx: int, gy: int) -> int:
+    """The gradient direction sector of the non-maximum suppression."""
+    return lib().or_canny_sector(int(gx), int(gy))
+
+
+def segment(edges: np.ndarray, valid: np.ndarray, min_pixels: int = 200, gap: int = 1):
+    """4-connected regions of valid pixels away from edges: (int32 labels [h, w], R)."""
+    E = np.ascontiguousarray(edges, dtype=np.uint8)
+    V = np.ascontiguousarray(valid, dtype=np.uint8)
+    h, w = E.shape
+    out = np.zeros((h, w), dtype=np.int32)
+    R = lib().or_segment(_p(E), _p(V), w, h, gap, min_pixels, _p(out))
+    if R < 0:
+        raise ValueError('or_segment failed (%d)' % R)
+    return out, R
 
 
 # ---------------------------------------------------------------------------

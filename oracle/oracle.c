@@ -742,3 +742,209 @@ int or_region_samples(const int *regions, const unsigned char *valid, int w, int
     return region_sample(seed, frame_idx, r, hyp, u0, v0, u1 - u0 + 1, v1 - v0 + 1, w, regions,
                          valid, out);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Canny edges on the normal image and the regions they bound (Sec. III-D:  */
+/* edge detection on the normal vector image, then the planar regions).     */
+/* ------------------------------------------------------------------------ */
+
+/* 8-bit code of one normal component n in [-1, 1]:
+ *   q = clamp(floor(fma(n, 127.5, 128)), 0, 255)  (FP32 fused multiply-add);
+ * an invalid pixel is the zero vector, q = 128 in every channel. */
+static int canny_code(float n)
+{
+    float t = fmaf(n, 127.5f, 128.0f);
+    int q = (int)floorf(t);
+    return q < 0 ? 0 : q > 255 ? 255 : q;
+}
+
+/* Direction sector of the gradient (gx, gy), step 4 below:
+ *   0: |gy| < tan(22.5 deg) |gx|  <=>  (|gx| + |gy|)^2 < 2 gx^2   (neighbours (u-1, v), (u+1, v))
+ *   2: |gx| < tan(22.5 deg) |gy|  <=>  (|gx| + |gy|)^2 < 2 gy^2   (neighbours (u, v-1), (u, v+1))
+ *   1: otherwise, gx gy > 0                                    (neighbours (u-1, v-1), (u+1, v+1))
+ *   3: otherwise                                               (neighbours (u-1, v+1), (u+1, v-1)) */
+int or_canny_sector(int gx, int gy)
+{
+    long a = labs((long)gx), b = labs((long)gy), s2 = (a + b) * (a + b);
+    if (s2 < 2 * a * a)
+        return 0;
+    if (s2 < 2 * b * b)
+        return 2;
+    return (long)gx * gy > 0 ? 1 : 3;
+}
+
+/* Edge map of the normal image N (FP32 SoA [3][h][w], validity bit 0 of
+ * valid):
+ *  1. q_c = canny_code(N_c) per channel (128 where invalid); no smoothing of
+ *     its own: the depth was smoothed by the anisotropic diffusion, which
+ *     the method applies to make the normal image smooth (Sec. III-C);
+ *  2. per channel the 3x3 Sobel derivatives gx (along u, to the right) and
+ *     gy (along v, downwards), image borders replicated;
+ *  3. per pixel the channel with the largest |gx| + |gy| (ties: the lowest
+ *     channel); m = |gx| + |gy|;
+ *  4. direction sector of (gx, gy): along u when |gy| < tan(22.5 deg) |gx|,
+ *     i.e. (|gx| + |gy|)^2 < 2 gx^2 (exact in integers, never an equality
+ *     unless gx = gy = 0); along v when (|gx| + |gy|)^2 < 2 gy^2; otherwise
+ *     the diagonal through (u+1, v+1) if gx gy > 0, through (u+1, v-1) if not;
+ *  5. non-maximum suppression: kept when m > m(behind) and m >= m(ahead)
+ *     along the sector (m = 0 outside the image);
+ *  6. kept pixels with m > high are strong, with m > low weak; the edges
+ *     are the strong pixels and the weak pixels 8-connected to a strong one
+ *     through weak pixels (hysteresis).
+ * edges: u8 [h][w], 1 = edge; states (may be NULL): u8 [h][w], the state of
+ * step 6 before hysteresis (0 none, 1 weak, 2 strong), for tests.  Returns
+ * the number of edge pixels, < 0 on error. */
+long or_canny(const float *N, const unsigned char *valid, int w, int h, int low, int high,
+              unsigned char *edges, unsigned char *states)
+{
+    if (w <= 0 || h <= 0 || low < 0 || high < low)
+        return -1;
+    long n = (long)w * h;
+    int *q = (int *)malloc(3 * n * sizeof(int));
+    int *m = (int *)malloc(n * sizeof(int));
+    unsigned char *sec = (unsigned char *)malloc(n);
+    unsigned char *st = (unsigned char *)malloc(n);
+    long *stack = (long *)malloc(n * sizeof(long));
+    if (!q || !m || !sec || !st || !stack) {
+        free(q); free(m); free(sec); free(st); free(stack);
+        return -2;
+    }
+    for (int c = 0; c < 3; ++c)
+        for (long p = 0; p < n; ++p)
+            q[c * n + p] = (valid[p] & 1) ? canny_code(N[c * n + p]) : 128;
+    for (int v = 0; v < h; ++v)
+        for (int u = 0; u < w; ++u) {
+            int um = u > 0 ? u - 1 : 0, up = u < w - 1 ? u + 1 : w - 1;
+            int vm = v > 0 ? v - 1 : 0, vp = v < h - 1 ? v + 1 : h - 1;
+            int best = -1, bgx = 0, bgy = 0;
+            for (int c = 0; c < 3; ++c) {
+                const int *Q = q + c * n;
+#define QQ(uu, vv) Q[(long)(vv) * w + (uu)]
+                int gx = (QQ(up, vm) + 2 * QQ(up, v) + QQ(up, vp)) -
+                         (QQ(um, vm) + 2 * QQ(um, v) + QQ(um, vp));
+                int gy = (QQ(um, vp) + 2 * QQ(u, vp) + QQ(up, vp)) -
+                         (QQ(um, vm) + 2 * QQ(u, vm) + QQ(up, vm));
+#undef QQ
+                int mag = abs(gx) + abs(gy);
+                if (mag > best) {
+                    best = mag;
+                    bgx = gx;
+                    bgy = gy;
+                }
+            }
+            long p = (long)v * w + u;
+            m[p] = best;
+            sec[p] = (unsigned char)or_canny_sector(bgx, bgy);
+        }
+    static const int du[4][2] = {{-1, 1}, {-1, 1}, {0, 0}, {-1, 1}};
+    static const int dv[4][2] = {{0, 0}, {-1, 1}, {-1, 1}, {1, -1}};
+    for (int v = 0; v < h; ++v)
+        for (int u = 0; u < w; ++u) {
+            long p = (long)v * w + u;
+            int s = sec[p];
+            int nb[2];
+            for (int k = 0; k < 2; ++k) {
+                int uu = u + du[s][k], vv = v + dv[s][k];
+                nb[k] = (uu < 0 || uu >= w || vv < 0 || vv >= h) ? 0 : m[(long)vv * w + uu];
+            }
+            int keep = m[p] > nb[0] && m[p] >= nb[1];
+            st[p] = !keep ? 0 : m[p] > high ? 2 : m[p] > low ? 1 : 0;
+        }
+    if (states)
+        memcpy(states, st, n);
+    long top = 0, count = 0;
+    for (long p = 0; p < n; ++p) {
+        edges[p] = st[p] == 2;
+        if (edges[p])
+            stack[top++] = p;
+    }
+    while (top > 0) {
+        long p = stack[--top];
+        int u = (int)(p % w), v = (int)(p / w);
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int uu = u + dx, vv = v + dy;
+                if (uu < 0 || uu >= w || vv < 0 || vv >= h)
+                    continue;
+                long r = (long)vv * w + uu;
+                if (st[r] == 1 && !edges[r]) {
+                    edges[r] = 1;
+                    stack[top++] = r;
+                }
+            }
+    }
+    for (long p = 0; p < n; ++p)
+        count += edges[p];
+    free(q); free(m); free(sec); free(st); free(stack);
+    return count;
+}
+
+/* Planar regions bounded by the edges: the 4-connected components of the
+ * eligible pixels, which are valid, not edges and, when gap = 1, have no
+ * edge among their 8 neighbours (this closes the one-pixel breaks that
+ * non-maximum suppression leaves where edge lines meet).  Components with
+ * fewer than min_pixels pixels get -1; the others are numbered 0, 1, ... in
+ * the raster order of their first pixel.  labels: int32 [h][w].  Returns
+ * the number of regions. */
+int or_segment(const unsigned char *edges, const unsigned char *valid, int w, int h, int gap,
+               int min_pixels, int *labels)
+{
+    if (w <= 0 || h <= 0 || min_pixels < 1 || gap < 0 || gap > 1)
+        return -1;
+    long n = (long)w * h;
+    long *stack = (long *)malloc(n * sizeof(long));
+    long *comp = (long *)malloc(n * sizeof(long));
+    unsigned char *ok = (unsigned char *)malloc(n);
+    if (!stack || !comp || !ok) {
+        free(stack); free(comp); free(ok);
+        return -2;
+    }
+    for (int v = 0; v < h; ++v)
+        for (int u = 0; u < w; ++u) {
+            long p = (long)v * w + u;
+            int e = 0;
+            for (int dy = -gap; dy <= gap; ++dy)
+                for (int dx = -gap; dx <= gap; ++dx) {
+                    int uu = u + dx, vv = v + dy;
+                    if (uu >= 0 && uu < w && vv >= 0 && vv < h && edges[(long)vv * w + uu])
+                        e = 1;
+                }
+            ok[p] = (valid[p] & 1) && !e;
+        }
+    for (long p = 0; p < n; ++p)
+        labels[p] = -2;                            /* -2: not visited */
+    int R = 0;
+    for (long s = 0; s < n; ++s) {
+        if (labels[s] != -2)
+            continue;
+        if (!ok[s]) {
+            labels[s] = -1;
+            continue;
+        }
+        long top = 0, k = 0;
+        stack[top++] = s;
+        labels[s] = -3;                            /* queued */
+        while (top > 0) {
+            long p = stack[--top];
+            comp[k++] = p;
+            int u = (int)(p % w), v = (int)(p / w);
+            const int nu[4] = {u - 1, u + 1, u, u}, nv[4] = {v, v, v - 1, v + 1};
+            for (int j = 0; j < 4; ++j) {
+                if (nu[j] < 0 || nu[j] >= w || nv[j] < 0 || nv[j] >= h)
+                    continue;
+                long r = (long)nv[j] * w + nu[j];
+                if (labels[r] == -2 && ok[r]) {
+                    labels[r] = -3;
+                    stack[top++] = r;
+                }
+            }
+        }
+        int lab = k >= min_pixels ? R++ : -1;
+        for (long i = 0; i < k; ++i)
+            labels[comp[i]] = lab;
+    }
+    free(stack);
+    free(comp);
+    free(ok);
+    return R;
+}
