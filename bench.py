@@ -185,41 +185,52 @@ def diffusion_hbm(torch, pm, dev, pk, side=8192, reps=5):
 
 
 def run_regions(torch, pm, pipe, frames, dframes, pk, n_frames=8, H=256, reps=3):
-    """Per-region RANSAC (one model per region) on 640x480 staircase frames;
-    the regions are the generator's ground-truth plane ids, standing in for
-    the polygons of the contour step.  Points come from the library's own
-    diffusion and normals; only pm_ransac_regions is timed."""
+    """The step after the path, all on the GPU: Canny edges of the normal image,
+    the regions they bound, and per-region RANSAC (one model per region) on
+    640x480 staircase frames.  Points and normals come from the library's own
+    diffusion and normals; the three calls are timed with CUDA events (the
+    region count and the planes are read back, so those two synchronise)."""
     s = torch.cuda.current_stream()
-    ms, pairs, regions = [], 0, 0
+    t_edge, t_seg, t_rr, pairs, regions, accepted = [], [], [], 0, 0, 0
     for i in range(n_frames):
         fr = frames[i]
         z = pipe.diffuse(dframes[i])
-        P, _, V = pipe.normals(z, fr.cam.intrinsics)
-        lab = torch.from_numpy(np.ascontiguousarray(fr.plane_id, dtype=np.int32)).to(z.device)
-        R = int(fr.plane_id.max()) + 1
-        pipe.ransac_regions(P, V, lab, R, H, i)          # warm-up (scratch allocation)
+        P, N, V = pipe.normals(z, fr.cam.intrinsics)
+        E = pipe.canny(N, V)                                # warm-up (scratch allocation)
+        lab, R = pipe.segment(E, V)
+        out = pipe.ransac_regions(P, V, lab, R, H, i)
         for k in range(reps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(s)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(s)
+            E = pipe.canny(N, V)
+            ev[1].record(s)
+            lab, R = pipe.segment(E, V)
+            ev[2].record(s)
             out = pipe.ransac_regions(P, V, lab, R, H, i)
-            b.record(s)
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
+            ev[3].record(s)
+            ev[3].synchronize()
+            t_edge.append(ev[0].elapsed_time(ev[1]))
+            t_seg.append(ev[1].elapsed_time(ev[2]))
+            t_rr.append(ev[2].elapsed_time(ev[3]))
         pairs += int(out.total.sum()) * H
         regions += R
-    per_call = statistics.median(ms)
+        accepted += int(out.accepted.sum())
+    med = statistics.median
+    chain = med(t_edge) + med(t_seg) + med(t_rr)
     clock_mhz = pk.get('sm_max_mhz', 2032.0)
     peak = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
-    pairs_per_call = pairs / n_frames
-    tflops = pairs_per_call * REGION_FLOP_PER_PAIR / (per_call * 1e-3) / 1e12
-    return {'frames': n_frames, 'regions_per_frame': regions / n_frames, 'hypotheses': H,
-            'ms_per_frame_p50': per_call, 'frames_per_s': 1e3 / per_call,
-            'regions_per_s': regions / n_frames * 1e3 / per_call,
-            'pairs_per_s': pairs_per_call / (per_call * 1e-3),
-            'alu': {'achieved': tflops, 'peak': peak, 'unit': 'TFLOP/s', 'frac': tflops / peak,
-                    'work': '%d FP32 FLOP per hypothesis-point pair, whole call (7 launches)'
-                            % REGION_FLOP_PER_PAIR},
-            'api': 'pm_ransac_regions (synchronising), regions = ground-truth plane ids'}
+    tflops = pairs / n_frames * REGION_FLOP_PER_PAIR / (med(t_rr) * 1e-3) / 1e12
+    return {'frames': n_frames, 'regions_per_frame': regions / n_frames,
+            'accepted_per_frame': accepted / n_frames, 'hypotheses': H,
+            'canny_ms': med(t_edge), 'segment_ms': med(t_seg), 'ransac_regions_ms': med(t_rr),
+            'chain_ms_per_frame': chain, 'frames_per_s': 1e3 / chain,
+            'regions_per_s': regions / n_frames * 1e3 / med(t_rr),
+            'ransac_regions_alu': {'achieved': tflops, 'peak': peak, 'unit': 'TFLOP/s',
+                                   'frac': tflops / peak,
+                                   'work': '%d FP32 FLOP per hypothesis-point pair, whole call '
+                                           '(7 launches)' % REGION_FLOP_PER_PAIR},
+            'api': 'pm_canny (60/150) -> pm_segment (gap 1, 200 px) -> pm_ransac_regions, '
+                   'one frame per call'}
 
 
 def run_served(torch, pm, args, c2_frames, c2_dev):

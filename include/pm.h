@@ -236,6 +236,33 @@ pm_status pm_ransac_regions(pm_ctx *ctx, const float *points, const unsigned cha
                             const int *regions, int w, int h, int n_regions, int hypotheses,
                             unsigned long long frame_idx, pm_region_plane *out, void *stream);
 
+/* Canny edges of the normal image (Sec. III-D: edge detection on the normal
+ * vector image).  normals: device FP32 SoA [3][h*w] (pm_normals' layout),
+ * valid: device u8 [h*w] (bit 0), edges: device u8 [h*w] out, 1 = edge.
+ * Each normal component is coded to 8 bits, q = clamp(floor(fma(n, 127.5,
+ * 128)), 0, 255) in FP32 (an invalid pixel codes as the zero vector, 128);
+ * per channel the 3x3 Sobel derivatives (borders replicated); per pixel the
+ * channel with the largest |gx| + |gy| = m (ties: lowest channel);
+ * non-maximum suppression across the 22.5-degree sector of (gx, gy), decided
+ * exactly in integers (kept when m > m behind and m >= m ahead, m = 0 outside
+ * the image); kept pixels with m > high are strong, with m > low weak, and
+ * the edges are the 8-connected components of weak and strong pixels that
+ * hold a strong pixel.  No smoothing of its own: the anisotropic diffusion
+ * is the smoothing step.  0 <= low <= high.  Asynchronous on `stream`. */
+pm_status pm_canny(pm_ctx *ctx, const float *normals, const unsigned char *valid, int w, int h,
+                   int low, int high, unsigned char *edges, void *stream);
+
+/* Planar regions bounded by the edges: the 4-connected components of the
+ * pixels that are valid, not edges and (gap = 1) have no edge among their 8
+ * neighbours, which closes the one-pixel breaks non-maximum suppression
+ * leaves where edge lines meet (gap = 0: only the edge pixels themselves are
+ * excluded).  labels: device int32 [h*w] out: components of at least
+ * min_pixels pixels numbered 0 .. n_regions - 1 in the raster order of their
+ * first pixel, -1 elsewhere (the region image pm_ransac_regions takes).
+ * *n_regions: host.  Synchronises `stream`. */
+pm_status pm_segment(pm_ctx *ctx, const unsigned char *edges, const unsigned char *valid, int w,
+                     int h, int gap, int min_pixels, int *labels, int *n_regions, void *stream);
+
 /* Change the diffusion tiling of a context (autotuning): temporal blocking
  * depth iters_per_launch (1..8) and output tile tile_w x tile_h (limits as in
  * pm_diffusion_params; 0 = library choice).  Results are bit-identical for

@@ -57,7 +57,8 @@ class Frame(ctypes.Structure):
 EXPORTS = ['pm_create', 'pm_destroy', 'pm_diffuse', 'pm_normals', 'pm_ransac_planes',
            'pm_process_frame', 'pm_process_frame_host', 'pm_process_batch',
            'pm_process_batch_async', 'pm_batch_collect', 'pm_scratch_bytes', 'pm_set_timing',
-           'pm_stage_times', 'pm_kernel_stats', 'pm_ransac_regions', 'pm_diffuse_noalloc',
+           'pm_stage_times', 'pm_kernel_stats', 'pm_ransac_regions', 'pm_canny', 'pm_segment',
+           'pm_diffuse_noalloc',
            'pm_set_tiling', 'pm_last_error']
 
 _lib = None
@@ -98,6 +99,8 @@ def load(path: str = LIB_PATH):
         'pm_kernel_stats': ([vp, P(ctypes.c_float), P(ctypes.c_longlong), P(ctypes.c_longlong),
                              P(i), P(ctypes.c_longlong)], i),
         'pm_ransac_regions': ([vp, vp, vp, vp, i, i, i, i, u64, P(RegionPlane), vp], i),
+        'pm_canny': ([vp, vp, vp, i, i, i, i, vp, vp], i),
+        'pm_segment': ([vp, vp, vp, i, i, i, i, vp, P(i), vp], i),
         'pm_diffuse_noalloc': ([vp, i, i, i, i, P(DiffusionParams), ctypes.c_float, vp, vp], i),
         'pm_set_tiling': ([vp, i, i, i], i),
         'pm_last_error': ([], ctypes.c_char_p),

@@ -7,7 +7,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, 'csrc')
 LIB = os.path.join(HERE, 'libpm.so')
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
-SOURCES = ['pm_api.cu', 'diffuse.cu', 'normals.cu', 'ransac.cu', 'regions.cu', 'noalloc.cu']
+SOURCES = ['pm_api.cu', 'diffuse.cu', 'normals.cu', 'ransac.cu', 'regions.cu', 'canny.cu',
+           'noalloc.cu']
 
 
 def _nvcc():

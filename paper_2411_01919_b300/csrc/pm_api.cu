@@ -114,6 +114,8 @@ struct pm_ctx {
     size_t rg_cap = 0;
     pm_region_plane *h_rg = nullptr;      // pinned copy of its results
     int h_rg_cap = 0;
+    char *eg = nullptr;                   // edge / region scratch for max_npx (on first use)
+    int *h_eg = nullptr;                  // pinned: region count, error flag
     cudaStream_t gstream = nullptr;       // graph stream when the caller passes the legacy stream
     cudaEvent_t gev[2] = {nullptr, nullptr};
     long long launches = 0;               // kernels launched by the last call
@@ -628,6 +630,10 @@ void pm_destroy(pm_ctx *ctx)
         cudaFree(ctx->rg);
     if (ctx->h_rg)
         cudaFreeHost(ctx->h_rg);
+    if (ctx->eg)
+        cudaFree(ctx->eg);
+    if (ctx->h_eg)
+        cudaFreeHost(ctx->h_eg);
     if (ctx->gstream)
         cudaStreamDestroy(ctx->gstream);
     for (int i = 0; i < 2; ++i)
@@ -952,6 +958,122 @@ pm_status pm_ransac_regions(pm_ctx *ctx, const float *points, const unsigned cha
                           s));
     PM_CK(cudaStreamSynchronize(s));
     std::memcpy(out, ctx->h_rg, R * sizeof(pm_region_plane));
+    return PM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Scratch of the edge and region passes, carved from one allocation sized
+// for the context's largest image.
+struct EdgeScratch {
+    unsigned char *state, *strong;
+    int *L, *size, *pre, *bsum, *err;
+};
+
+pm_status edge_scratch(pm_ctx *ctx, EdgeScratch &x)
+{
+    const size_t n = (size_t)ctx->max_npx, nb = (n + 1023) / 1024 + 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t o_state = take(n), o_strong = take(n), o_L = take(n * 4), o_size = take(n * 4),
+                 o_pre = take(n * 4), o_bsum = take(nb * 4), o_err = take(4);
+    if (!ctx->eg) {
+        PM_CK(cudaMalloc(&ctx->eg, off));
+        PM_CK(cudaMemset(ctx->eg + o_err, 0, 4));
+    }
+    if (!ctx->h_eg)
+        PM_CK(cudaMallocHost(&ctx->h_eg, 2 * sizeof(int)));
+    char *b = ctx->eg;
+    x.state = reinterpret_cast<unsigned char *>(b + o_state);
+    x.strong = reinterpret_cast<unsigned char *>(b + o_strong);
+    x.L = reinterpret_cast<int *>(b + o_L);
+    x.size = reinterpret_cast<int *>(b + o_size);
+    x.pre = reinterpret_cast<int *>(b + o_pre);
+    x.bsum = reinterpret_cast<int *>(b + o_bsum);
+    x.err = reinterpret_cast<int *>(b + o_err);
+    return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_canny(pm_ctx *ctx, const float *normals, const unsigned char *valid, int w, int h,
+                   int low, int high, unsigned char *edges, void *stream)
+{
+    if (!ctx || !normals || !valid || !edges)
+        return fail(PM_ERR_ARG, "null argument");
+    if (w < 1 || h < 1 || (long long)w * h > ctx->max_npx)
+        return fail(PM_ERR_ARG, "image size out of range for this context");
+    if (low < 0 || high < low)
+        return fail(PM_ERR_ARG, "thresholds must satisfy 0 <= low <= high");
+    if (ctx->pending_n)
+        return fail(PM_ERR_STATE, "an asynchronous batch is still pending on this context");
+    EdgeScratch x;
+    const pm_status st = edge_scratch(ctx, x);
+    if (st != PM_OK)
+        return st;
+    EdgeLaunch E;
+    E.N = normals;
+    E.valid = valid;
+    E.w = w;
+    E.h = h;
+    E.low = low;
+    E.high = high;
+    E.state = x.state;
+    E.strong = x.strong;
+    E.edges = edges;
+    E.L = x.L;
+    E.err = x.err;
+    PM_CK(canny_edges(E, (cudaStream_t)stream));
+    ctx->launches = 5;
+    return PM_OK;
+}
+
+pm_status pm_segment(pm_ctx *ctx, const unsigned char *edges, const unsigned char *valid, int w,
+                     int h, int gap, int min_pixels, int *labels, int *n_regions, void *stream)
+{
+    if (!ctx || !edges || !valid || !labels || !n_regions)
+        return fail(PM_ERR_ARG, "null argument");
+    if (w < 1 || h < 1 || (long long)w * h > ctx->max_npx)
+        return fail(PM_ERR_ARG, "image size out of range for this context");
+    if (gap < 0 || gap > 1 || min_pixels < 1)
+        return fail(PM_ERR_ARG, "gap must be 0 or 1 and min_pixels >= 1");
+    if (ctx->pending_n)
+        return fail(PM_ERR_STATE, "an asynchronous batch is still pending on this context");
+    EdgeScratch x;
+    const pm_status st = edge_scratch(ctx, x);
+    if (st != PM_OK)
+        return st;
+    SegLaunch S;
+    S.edges = edges;
+    S.valid = valid;
+    S.w = w;
+    S.h = h;
+    S.gap = gap;
+    S.min_pixels = min_pixels;
+    S.L = x.L;
+    S.size = x.size;
+    S.pre = x.pre;
+    S.bsum = x.bsum;
+    S.labels = labels;
+    S.err = x.err;
+    cudaStream_t s = (cudaStream_t)stream;
+    PM_CK(segment_regions(S, s));
+    const long long nb = ((long long)w * h + 1023) / 1024;
+    PM_CK(cudaMemcpyAsync(ctx->h_eg, x.bsum + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PM_CK(cudaMemcpyAsync(ctx->h_eg + 1, x.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PM_CK(cudaStreamSynchronize(s));
+    ctx->launches = 6;
+    if (ctx->h_eg[1])
+        return fail(PM_ERR_CUDA, "union-find walk exceeded its bound");
+    *n_regions = ctx->h_eg[0];
     return PM_OK;
 }
 

@@ -222,6 +222,30 @@ struct RegionLaunch {
 };
 cudaError_t ransac_regions(const RegionLaunch &L, int sms, cudaStream_t s);
 
+// Canny edges of the normal image and the regions they bound (canny.cu); all
+// pointers device memory, [w*h] unless noted.
+struct EdgeLaunch {
+    const float *N;                 // SoA normals [3][w*h]
+    const unsigned char *valid;
+    int w, h, low, high;
+    unsigned char *state;           // 0 / 1 weak / 2 strong after suppression
+    unsigned char *strong;          // per root: component holds a strong pixel
+    unsigned char *edges;           // output, 1 = edge
+    int *L;                         // union-find parents
+    int *err;                       // set if a union-find walk overran (never expected)
+};
+cudaError_t canny_edges(const EdgeLaunch &E, cudaStream_t s);
+
+struct SegLaunch {
+    const unsigned char *edges, *valid;
+    int w, h, gap, min_pixels;
+    int *L, *size, *pre;            // parents, component sizes, in-block prefix of roots
+    int *bsum;                      // [ceil(w*h / 1024) + 1]; [last] = number of regions
+    int *labels;                    // output
+    int *err;
+};
+cudaError_t segment_regions(const SegLaunch &S, cudaStream_t s);
+
 cudaError_t ransac_init(const RansacLaunch &L, cudaStream_t s);
 cudaError_t score_init();                  // shared-memory opt-in and occupancy of k_score
 int score_hyp_block(bool fine, int H);     // hypotheses per scoring work item

@@ -204,6 +204,32 @@ class Pipeline:
             hypotheses, frame_idx, arr, _stream_ptr(stream)))
         return RegionPlanes.from_c(arr, n_regions)
 
+    def canny(self, N: torch.Tensor, valid: torch.Tensor, low: int = 60, high: int = 150,
+              stream=None) -> torch.Tensor:
+        """Canny edges of the normal image (Sec. III-D): u8 [h, w], 1 = edge."""
+        _, h, w = N.shape
+        if N.dtype != torch.float32 or valid.dtype != torch.uint8 or not N.is_contiguous() \
+                or not valid.is_contiguous() or tuple(valid.shape) != (h, w):
+            raise ValueError('N must be contiguous float32 [3, h, w] and valid uint8 [h, w]')
+        E = torch.empty((h, w), dtype=torch.uint8, device=N.device)
+        check(self.lib.pm_canny(self._h, _dev(N, 'N'), _dev(valid, 'valid'), w, h, low, high,
+                                _dev(E, 'edges'), _stream_ptr(stream)))
+        return E
+
+    def segment(self, edges: torch.Tensor, valid: torch.Tensor, min_pixels: int = 200,
+                gap: int = 1, stream=None):
+        """Regions bounded by the edges: (int32 labels [h, w], number of regions)."""
+        h, w = edges.shape
+        if edges.dtype != torch.uint8 or valid.dtype != torch.uint8 or not edges.is_contiguous() \
+                or not valid.is_contiguous() or tuple(valid.shape) != (h, w):
+            raise ValueError('edges and valid must be contiguous uint8 [h, w]')
+        lab = torch.empty((h, w), dtype=torch.int32, device=edges.device)
+        n = ctypes.c_int(0)
+        check(self.lib.pm_segment(self._h, _dev(edges, 'edges'), _dev(valid, 'valid'), w, h, gap,
+                                  min_pixels, _dev(lab, 'labels'), ctypes.byref(n),
+                                  _stream_ptr(stream)))
+        return lab, n.value
+
     # -- whole path ---------------------------------------------------------
     def process_frame(self, depth: torch.Tensor, K, frame_idx: int = 0, labels: bool = True,
                       stream=None) -> Planes:

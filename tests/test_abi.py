@@ -81,3 +81,11 @@ def test_region_ransac_rejects_a_null_context():
     out = (_ffi.RegionPlane * 1)()
     st = lib.pm_ransac_regions(None, None, None, None, 64, 48, 1, 64, 0, out, None)
     assert st == _ffi.PM_ERR_ARG
+
+
+def test_edge_and_region_calls_reject_a_null_context():
+    lib = pm.load_library()
+    n = ctypes.c_int(0)
+    assert lib.pm_canny(None, None, None, 64, 48, 60, 150, None, None) == _ffi.PM_ERR_ARG
+    assert lib.pm_segment(None, None, None, 64, 48, 1, 200, None, ctypes.byref(n),
+                          None) == _ffi.PM_ERR_ARG
