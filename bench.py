@@ -233,6 +233,99 @@ def run_regions(torch, pm, pipe, frames, dframes, pk, n_frames=8, H=256, reps=3)
                    'one frame per call'}
 
 
+def run_sweep(torch, pm, pk, frames, dframes, flush):
+    """Sec. IV-B's component timing: single-frame time at 320x240 and 640x480
+    for 10 / 20 / 40 diffusion iterations (more than 20 for noisier depth),
+    both diffusion forms (PM4, Alg. 1 literal) and both normal stencils
+    (central, Sobel); the batched 640x480 step with Alg. 1 and with Sobel
+    normals (each autotuned); and per-region RANSAC time against the number
+    of regions (the paper fits polygons one after another, so its time grows
+    linearly with their number)."""
+    import synth
+    from paper_2411_01919_b300.tune import DiffusionTuner
+    s = torch.cuda.current_stream()
+    out = {'single_frame': [], 'batched': [], 'regions_vs_count': []}
+    for (w, h) in ((320, 240), (640, 480)):
+        fr = [synth.frame_straight(sd, w, h) for sd in range(12)]
+        dev = [torch.from_numpy(f.encoded).to(dframes[0].device) for f in fr]
+        K = fr[0].cam.intrinsics
+        for iters in (10, 20, 40):
+            for mode in (0, 1):
+                for stencil in (0, 1):
+                    p = pm.Params(iters=iters, mode=mode, stencil=stencil, hypotheses=HYP, thr=THR,
+                                  max_planes=MAXP, min_inliers=MINI, seed=0)
+                    with pm.Pipeline(p, w, h, 1) as pipe:
+                        for i in range(3):
+                            pipe.process_frame(dev[i], K, frame_idx=i, labels=False)
+                        ms = []
+                        for i in range(len(dev)):
+                            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+                                enable_timing=True)
+                            a.record(s)
+                            pipe.process_frame(dev[i], K, frame_idx=i, labels=False)
+                            b.record(s)
+                            b.synchronize()
+                            ms.append(a.elapsed_time(b))
+                        pipe.set_timing(1)
+                        st = []
+                        for i in range(6):
+                            pipe.process_frame(dev[i], K, frame_idx=i, labels=False)
+                            st.append(pipe.stage_times())
+                    out['single_frame'].append({
+                        'res': '%dx%d' % (w, h), 'iters': iters, 'mode': ['pm4', 'alg1'][mode],
+                        'stencil': ['central', 'sobel'][stencil], 'ms_p50': percentile(ms, 50),
+                        'diffuse_ms': statistics.median(x['diffuse_ms'] for x in st),
+                        'normals_ms': statistics.median(x['normals_ms'] for x in st),
+                        'ransac_ms': statistics.median(x['ransac_ms'] for x in st)})
+    B = len(frames)
+    K = frames[0].cam.intrinsics
+    for mode, stencil in ((1, 0), (0, 1)):
+        p = pm.Params(iters=ITERS, mode=mode, stencil=stencil, hypotheses=HYP, thr=THR,
+                      max_planes=MAXP, min_inliers=MINI, seed=0)
+        with pm.Pipeline(p, 640, 480, B) as pipe:
+            batch = [dict(depth=dframes[i], K=K, frame_idx=i) for i in range(B)]
+            tuned = DiffusionTuner().tune(pipe, batch)
+            for _ in range(3):
+                pipe.process_batch(batch, use_graph=True)
+            ms = []
+            for k in range(5):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                pipe.process_batch(batch, use_graph=True)
+                b.record(s)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        out['batched'].append({'mode': ['pm4', 'alg1'][mode], 'stencil': ['central', 'sobel'][stencil],
+                               'frames_per_s': B / (statistics.median(ms) * 1e-3),
+                               'ms_per_step': statistics.median(ms),
+                               'tiling': list(tuned['best'])})
+    p = pm.Params(iters=ITERS, hypotheses=HYP, thr=THR, max_planes=MAXP, min_inliers=MINI, seed=0)
+    with pm.Pipeline(p, 640, 480, 1) as pipe:
+        z = pipe.diffuse(dframes[0])
+        P, N, V = pipe.normals(z, K)
+        cols = torch.arange(640, device=z.device).view(1, -1).expand(480, 640)
+        rows = torch.arange(480, device=z.device).view(-1, 1).expand(480, 640)
+        for R in (1, 2, 4, 8, 16, 32, 64, 128):
+            gx = int(round(R ** 0.5)) if R > 1 else 1
+            while R % gx:
+                gx -= 1
+            gy = R // gx
+            lab = ((rows * gy // 480) * gx + cols * gx // 640).to(torch.int32).contiguous()
+            pipe.ransac_regions(P, V, lab, R, 256)
+            ms = []
+            for k in range(5):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                pipe.ransac_regions(P, V, lab, R, 256)
+                b.record(s)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            out['regions_vs_count'].append({'regions': R, 'hypotheses': 256,
+                                            'ms': statistics.median(ms)})
+    return out
+
+
 def run_served(torch, pm, args, c2_frames, c2_dev):
     """The served form: 16 simulated cameras (fixed resolution each from
     424x240 / 640x480 / 848x480 / 1280x720, staircases, camera advancing 5 cm
@@ -413,6 +506,7 @@ def run_ours(args):
 
     hbm = diffusion_hbm(torch, pm, dev, pk) if not args.skip_hbm else None
     regions = run_regions(torch, pm, pipe, frames, dframes, pk) if not args.skip_regions else None
+    sweep = run_sweep(torch, pm, pk, frames, dframes, flush) if not args.skip_sweep else None
     served = run_served(torch, pm, args, frames, dframes) if args.served_seconds > 0 else None
 
     cpu = None
@@ -434,7 +528,7 @@ def run_ours(args):
             'latency_ms': {'p50': percentile(step_ms, 50), 'p99': percentile(step_ms, 99),
                            'note': 'a batched frame completes with its step'},
             'plain': plain, 'speedup_vs_plain': value / world / plain['value'],
-            'served': served, 'regions': regions,
+            'served': served, 'regions': regions, 'sweep': sweep,
             'e2e': e2e, 'roofline': roof, 'diffusion_hbm': hbm, 'cpu_baseline': cpu,
             'gpu_launches': launches, 'clocks': clk,
             'paper_context': '>30 Hz whole pipeline; 7.5 ms/frame; <15 ms at 640x480 with 10 '
@@ -458,6 +552,7 @@ def main():
     ap.add_argument('--skip-cpu', action='store_true')
     ap.add_argument('--skip-hbm', action='store_true')
     ap.add_argument('--skip-regions', action='store_true')
+    ap.add_argument('--skip-sweep', action='store_true')
     ap.add_argument('--no-tune', action='store_true')
     ap.add_argument('--served-seconds', type=float, default=60.0)
     args = ap.parse_args()

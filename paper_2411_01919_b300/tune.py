@@ -23,11 +23,11 @@ CANDIDATES: List[Tuple[int, int, int]] = [
 ]
 
 
-def batch_key(frames: Sequence[dict], default_iters: int) -> str:
+def batch_key(frames: Sequence[dict], default_iters: int, mode: int = 0) -> str:
     shapes = sorted((int(f['depth'].shape[1]), int(f['depth'].shape[0]),
                      int(f.get('iters', -1)) if int(f.get('iters', -1)) >= 0 else default_iters)
                     for f in frames)
-    return json.dumps(shapes)
+    return json.dumps({'mode': int(mode), 'frames': shapes})
 
 
 class DiffusionTuner:
@@ -52,7 +52,7 @@ class DiffusionTuner:
     def tune(self, pipe, frames: Sequence[dict]) -> dict:
         """Measure every candidate on `frames`, leave the best set on `pipe` and
         return {'best': (T, tw, th), 'ms': {candidate: median diffusion ms}}."""
-        key = batch_key(frames, pipe.p.iters)
+        key = batch_key(frames, pipe.p.iters, pipe.p.mode)
         if key in self.cache:
             best = tuple(self.cache[key])
             pipe.set_tiling(*best)

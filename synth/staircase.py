@@ -404,6 +404,20 @@ def frame_c2(seed: int) -> Frame:
                  rendered=_C2_CACHE['gt'])
 
 
+def frame_straight(seed: int, w: int, h: int, sigma_coeff: float = 0.002,
+                   hole_frac: float = 0.02, dtype: str = 'u16') -> Frame:
+    """The 640x480 straight staircase scene (6 steps + floor + landing, camera
+    1.0 m high pitched 45 deg down) seen at w x h (intrinsics scaled with the
+    width) with noise sigma = sigma_coeff z^2, random holes and 5-pixel hole
+    bands at depth edges.  Used for resolution and noise sweeps."""
+    rng = np.random.Generator(np.random.PCG64([seed, w, h]))
+    fx, fy, cx, cy = _scaled_intrinsics(w, h)
+    cam = make_camera(w, h, fx, fy, cx, cy, [0.0, 0.0, 1.0], 0.0, np.pi / 4)
+    sc = straight_staircase(6, 0.15, 0.28, 1.0, first_riser_y=0.8)
+    return sense(sc, cam, rng, sigma_coeff, hole_frac, True, dtype,
+                 meta={'config': 'straight', 'seed': seed, 'sigma_coeff': sigma_coeff})
+
+
 def _spiral_camera(rng, w, h, fx, fy, cx, cy, height=1.2):
     dist = rng.uniform(2.2, 2.8)
     phi = rng.uniform(-0.3, 0.3) - np.pi / 2          # camera stands on the -y side

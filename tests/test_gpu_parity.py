@@ -165,6 +165,37 @@ def test_normals_match_oracle(name, stencil):
     assert np.abs(P.astype(np.float64) - Po).max() <= 1e-5
 
 
+@functools.lru_cache(maxsize=None)
+def high_noise(mode):
+    """Three times the noise of the 640x480 workload (sigma = 0.006 z^2)."""
+    fr = synth.frame_straight(5, 640, 480, 0.006)
+    ref = oracle.diffuse(oracle.decode(fr.encoded, fr.dtype, SCALE), 40, LAM, KC, mode)
+    return fr, ref
+
+
+@pytest.mark.parametrize('mode', [0, 1])
+@pytest.mark.parametrize('stencil', [0, 1])
+def test_high_noise_forty_iterations(mode, stencil):
+    """Sec. IV-B: more than 20 diffusion iterations for noisier depth.  Both
+    diffusion forms, both normal stencils, 40 iterations at three times the
+    workload's noise, against the oracle."""
+    fr, ref = high_noise(mode)
+    p = Params(iters=40, mode=mode, stencil=stencil)
+    with Pipeline(p, fr.w, fr.h) as pipe:
+        z = pipe.diffuse(to_dev(fr.encoded)).cpu().numpy().astype(np.float64)
+        z32 = ref.astype(np.float32)
+        P, N, V = pipe.normals(to_dev(z32), fr.cam.intrinsics)
+        N, V = N.cpu().numpy(), V.cpu().numpy()
+    err = np.abs(z - ref).max()
+    print('high noise mode %d: max |gpu - oracle| = %.3e m' % (mode, err))
+    assert err <= DIFF_TOL
+    assert np.array_equal(z == 0, ref == 0)
+    Po, No, Vo = oracle.normals(z32.astype(np.float64), fr.cam.intrinsics, stencil)
+    assert np.array_equal(V, Vo)
+    ok = (V & 2) > 0
+    assert ang_deg(N[:, ok].astype(np.float64), No[:, ok]).max() <= NORMAL_TOL_DEG
+
+
 # ---------------------------------------------------------------------------
 # RANSAC (Eq. 3, Alg. 2), same FP32 points on both sides
 # ---------------------------------------------------------------------------
