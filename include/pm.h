@@ -263,6 +263,65 @@ pm_status pm_canny(pm_ctx *ctx, const float *normals, const unsigned char *valid
 pm_status pm_segment(pm_ctx *ctx, const unsigned char *edges, const unsigned char *valid, int w,
                      int h, int gap, int min_pixels, int *labels, int *n_regions, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Polygon map manager (Sec. III-E, Eq. 4-10).  Host code; no GPU.
+ *
+ * Each frame hands over the frame's planar polygons in the camera frame and
+ * the camera pose (map <- camera, row-major 4x4 [R t; 0 1], from odometry).
+ * Polygons whose plane normal in the map frame is within acos(horizontal_cos)
+ * of vertical enter the map as convex footprints in the map's x-y plane with
+ * the plane's height at the footprint's area centroid; others are skipped.
+ * A new polygon matches the map polygon whose footprint overlaps it by more
+ * than min_overlap_m2 and whose height differs from the new height minus the
+ * current drift estimate by at most drift_tolerance_m (Eq. 4-5; closest
+ * height wins, ties to the older polygon).  The frame's drift measurement is
+ * the mean over its matches of (new height - map height); the scalar Kalman
+ * filter predicts P += sigma_p every frame and, when the frame matched,
+ * updates K = P / (P + sigma_m), x += K (z - x), P = (1 - K) P (Eq. 6-10).
+ * New polygons are then lowered by the updated drift x and either merged
+ * into their match (the footprint grows to the hull of both; the map
+ * polygon keeps its height, the reference the drift is measured against) or
+ * added.  Variances in m^2.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double drift_tolerance_m;   /* Eq. 5: 0.05 */
+    double sigma_p;             /* process variance per frame */
+    double sigma_m;             /* measurement variance */
+    double initial_variance;    /* P before the first frame */
+    double horizontal_cos;      /* cos of the largest tilt of a map polygon, e.g. cos 20 deg */
+    double min_overlap_m2;      /* footprint overlap that counts as overlapping */
+} pm_map_params;
+
+typedef struct {
+    double n[3];                /* plane n . X + d = 0 in the camera frame */
+    double d;
+    const double *vertices;     /* host [n_vertices][3], camera frame, on or near the plane */
+    int n_vertices;             /* >= 3 */
+} pm_polygon;
+
+typedef struct {
+    int matched, merged, added, skipped;
+    double measurement;         /* z_k (0 when nothing matched) */
+    double gain;                /* K_k (0 when nothing matched) */
+    double drift_prior, drift;  /* x before and after this frame */
+    double variance;            /* P after this frame */
+} pm_map_step;
+
+typedef struct pm_map pm_map;
+
+pm_status pm_map_create(const pm_map_params *params, pm_map **out);
+void pm_map_destroy(pm_map *map);
+/* One frame: pose (16 doubles), polygons [n] (n may be 0); step may be NULL. */
+pm_status pm_map_integrate(pm_map *map, const double *pose, const pm_polygon *polygons, int n,
+                           pm_map_step *step);
+int pm_map_size(const pm_map *map);
+/* Map polygon i: height, footprint area, observation count, and up to cap
+ * footprint vertices (x, y pairs, counter-clockwise) in xy; *n_vertices gets
+ * the full count.  Any output but n_vertices may be NULL. */
+pm_status pm_map_polygon(const pm_map *map, int i, double *height, double *area,
+                         int *observations, double *xy, int cap, int *n_vertices);
+pm_status pm_map_drift(const pm_map *map, double *drift, double *variance);
+
 /* Change the diffusion tiling of a context (autotuning): temporal blocking
  * depth iters_per_launch (1..8) and output tile tile_w x tile_h (limits as in
  * pm_diffusion_params; 0 = library choice).  Results are bit-identical for

@@ -47,6 +47,24 @@ class RegionPlane(ctypes.Structure):
                 ('total', ctypes.c_int), ('accepted', ctypes.c_int), ('hyp_index', ctypes.c_int)]
 
 
+class MapParams(ctypes.Structure):
+    _fields_ = [('drift_tolerance_m', ctypes.c_double), ('sigma_p', ctypes.c_double),
+                ('sigma_m', ctypes.c_double), ('initial_variance', ctypes.c_double),
+                ('horizontal_cos', ctypes.c_double), ('min_overlap_m2', ctypes.c_double)]
+
+
+class Polygon(ctypes.Structure):
+    _fields_ = [('n', ctypes.c_double * 3), ('d', ctypes.c_double),
+                ('vertices', ctypes.c_void_p), ('n_vertices', ctypes.c_int)]
+
+
+class MapStep(ctypes.Structure):
+    _fields_ = [('matched', ctypes.c_int), ('merged', ctypes.c_int), ('added', ctypes.c_int),
+                ('skipped', ctypes.c_int), ('measurement', ctypes.c_double),
+                ('gain', ctypes.c_double), ('drift_prior', ctypes.c_double),
+                ('drift', ctypes.c_double), ('variance', ctypes.c_double)]
+
+
 class Frame(ctypes.Structure):
     _fields_ = [('depth', ctypes.c_void_p), ('dtype', ctypes.c_int), ('w', ctypes.c_int),
                 ('h', ctypes.c_int), ('pitch', ctypes.c_int), ('K', Intrinsics),
@@ -58,7 +76,8 @@ EXPORTS = ['pm_create', 'pm_destroy', 'pm_diffuse', 'pm_normals', 'pm_ransac_pla
            'pm_process_frame', 'pm_process_frame_host', 'pm_process_batch',
            'pm_process_batch_async', 'pm_batch_collect', 'pm_scratch_bytes', 'pm_set_timing',
            'pm_stage_times', 'pm_kernel_stats', 'pm_ransac_regions', 'pm_canny', 'pm_segment',
-           'pm_diffuse_noalloc',
+           'pm_map_create', 'pm_map_destroy', 'pm_map_integrate', 'pm_map_size',
+           'pm_map_polygon', 'pm_map_drift', 'pm_diffuse_noalloc',
            'pm_set_tiling', 'pm_last_error']
 
 _lib = None
@@ -101,6 +120,12 @@ def load(path: str = LIB_PATH):
         'pm_ransac_regions': ([vp, vp, vp, vp, i, i, i, i, u64, P(RegionPlane), vp], i),
         'pm_canny': ([vp, vp, vp, i, i, i, i, vp, vp], i),
         'pm_segment': ([vp, vp, vp, i, i, i, i, vp, P(i), vp], i),
+        'pm_map_create': ([P(MapParams), P(vp)], i),
+        'pm_map_destroy': ([vp], None),
+        'pm_map_integrate': ([vp, vp, P(Polygon), i, P(MapStep)], i),
+        'pm_map_size': ([vp], i),
+        'pm_map_polygon': ([vp, i, P(ctypes.c_double), P(ctypes.c_double), P(i), vp, i, P(i)], i),
+        'pm_map_drift': ([vp, P(ctypes.c_double), P(ctypes.c_double)], i),
         'pm_diffuse_noalloc': ([vp, i, i, i, i, P(DiffusionParams), ctypes.c_float, vp, vp], i),
         'pm_set_tiling': ([vp, i, i, i], i),
         'pm_last_error': ([], ctypes.c_char_p),
