@@ -34,7 +34,7 @@ int elem_size(int dtype) { return dtype == PM_F32_M ? 4 : 2; }
 
 // Layout of the device scratch arena: every region is 256-byte aligned.
 struct Layout {
-    size_t buf[2], depth, P, N, valid, labels, cidx[2], cpt[2], input;
+    size_t buf[2], depth, P, N, valid, labels, cpt[2], input;
     size_t hyp, hyp_p0, counts, kept, keepbits, partial, state, planes, chunk_base, counter;
     size_t total;
 };
@@ -56,8 +56,6 @@ Layout make_layout(long long npx, int frames, int H, int max_chunks)
     L.N = take(F * P * 12);
     L.valid = take(F * P);
     L.labels = take(F * P * 2);
-    L.cidx[0] = take(F * P * 4);
-    L.cidx[1] = take(F * P * 4);
     L.cpt[0] = take(F * P * 16);
     L.cpt[1] = take(F * P * 16);
     L.input = take(F * P * 4);
@@ -324,7 +322,6 @@ Plan build_tables(pm_ctx *ctx, const std::vector<FrameJob> &jobs, int T, bool ra
             r.npx = j.w * j.h;
             r.frame_idx = j.frame_idx;
             for (int b = 0; b < 2; ++b) {
-                r.cidx[b] = ctx->at<int>(Ly.cidx[b]) + slot;
                 r.cpt[b] = ctx->at<float4>(Ly.cpt[b]) + slot;
             }
             r.hyp = ctx->at<float4>(Ly.hyp) + (size_t)f * ctx->rp.hypotheses;
@@ -729,7 +726,6 @@ pm_status pm_ransac_planes(pm_ctx *ctx, const float *points, const float *normal
     r.npx = w * h;
     r.frame_idx = frame_idx;
     for (int b = 0; b < 2; ++b) {
-        r.cidx[b] = ctx->at<int>(Ly.cidx[b]);
         r.cpt[b] = ctx->at<float4>(Ly.cpt[b]);
     }
     r.hyp = ctx->at<float4>(Ly.hyp);

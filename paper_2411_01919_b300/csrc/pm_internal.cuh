@@ -76,8 +76,7 @@ struct RFrame {
     short *labels;            // [npx]
     int w, h, npx;
     unsigned long long frame_idx;
-    int *cidx[2];             // candidate pixel indices
-    float4 *cpt[2];           // candidate points (x, y, z, 0)
+    float4 *cpt[2];           // candidates (x, y, z, pixel index as int bits)
     float4 *hyp;              // [H] hypothesis planes (nx, ny, nz, d); d = +inf when degenerate
     float4 *hyp_p0;           // [H] first sample point
     int *counts;              // [H]

@@ -261,16 +261,13 @@ __device__ void compact_chunk(const RFrame &F, int c, int nchunks, int src, int 
         unsigned word = F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)];
         if (word >> (j & 31) & 1u) {
             int pos = off + s_wpre[j >> 5] + __popc(word & ((1u << (j & 31)) - 1u));
-            int pix;
             float4 pt;
             if (src_image) {
-                pix = (int)(base + j);
-                pt = make_float4(F.P[pix], F.P[npx + pix], F.P[2 * npx + pix], 0.0f);
+                const int pix = (int)(base + j);
+                pt = make_float4(F.P[pix], F.P[npx + pix], F.P[2 * npx + pix], __int_as_float(pix));
             } else {
-                pix = F.cidx[src][base + j];
                 pt = F.cpt[src][base + j];
             }
-            F.cidx[dst][pos] = pix;
             F.cpt[dst][pos] = pt;
         }
     }
@@ -309,6 +306,9 @@ __global__ void __launch_bounds__(128) k_hyp(RFrame *frames, RParams prm, int ro
         return;
     if (blockIdx.x == 0 && threadIdx.x == 0)
         st->score_done = 0;
+    // the removal adds each chunk's kept candidates warp by warp
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < st->nchunks; c += gridDim.x * blockDim.x)
+        F.kept[c] = 0;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= prm.H)
         return;
@@ -609,33 +609,39 @@ __device__ __forceinline__ void nadd(float &s, float &c, float x)
     s = t;
 }
 
-struct Mom {
-    float s[2][NMOM], c[2][NMOM];
-    int n[2];
-};
-
-template <int SET>
-__device__ __forceinline__ void mom_add(Mom &m, float x, float y, float z)
+// The nine moment values of a centred inlier (x, y, z, then the products in
+// the order Sxx Sxy Sxz Syy Syz Szz), added to v[off ..].
+__device__ __forceinline__ void mom_values(float (&v)[32], int off, float x, float y, float z)
 {
-    const float v[NMOM] = {x, y, z, __fmul_rn(x, x), __fmul_rn(x, y), __fmul_rn(x, z),
+    const float m[NMOM] = {x, y, z, __fmul_rn(x, x), __fmul_rn(x, y), __fmul_rn(x, z),
                            __fmul_rn(y, y), __fmul_rn(y, z), __fmul_rn(z, z)};
 #pragma unroll
-    for (int k = 0; k < NMOM; ++k)
-        nadd(m.s[SET][k], m.c[SET][k], v[k]);
-    m.n[SET] += 1;
+    for (int k = 0; k < NMOM; ++k) {
+        if (off == 0)
+            v[k] = __fadd_rn(v[k], m[k]);
+        else
+            v[NMOM + k] = __fadd_rn(v[NMOM + k], m[k]);
+    }
 }
 
-__device__ __forceinline__ void mom_merge(Mom &a, const float *os, const float *oc, const int *on)
+// Sum over the warp of every one of a lane's 32 values, transposed: lane l
+// returns the sum of the lanes' a[l].  Five butterfly steps; at the step of
+// offset o each lane keeps the half of its live values selected by its bit o
+// and adds the partner's copy of that half (31 shuffles in all).  The order
+// of the additions is fixed by the lane, not by the data.
+__device__ __forceinline__ float warp_transpose_sum(float (&a)[32], int lane)
 {
 #pragma unroll
-    for (int set = 0; set < 2; ++set) {
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
 #pragma unroll
-        for (int k = 0; k < NMOM; ++k) {
-            nadd(a.s[set][k], a.c[set][k], os[set * NMOM + k]);
-            a.c[set][k] = __fadd_rn(a.c[set][k], oc[set * NMOM + k]);
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? a[i] : a[i + o];
+            const float keep = up ? a[i + o] : a[i];
+            a[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
         }
-        a.n[set] += on[set];
     }
+    return a[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -796,7 +802,7 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
                                                            int round, bool fuse_refit)
 {
     __shared__ float sh_s[8][2 * NMOM], sh_c[8][2 * NMOM];
-    __shared__ int sh_n[8][2], sh_kept_w[CHUNK / REMOVE_THREADS][8];
+    __shared__ int sh_n[8][2];
     const int total = chunk_base[n];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nwarps = REMOVE_THREADS >> 5;
@@ -815,14 +821,11 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
         const float4 p0 = st->p0;
         const int cur = round & 1;
         const long long npx = F.npx;
-        Mom m;
-#pragma unroll
-        for (int set = 0; set < 2; ++set) {
-#pragma unroll
-            for (int k = 0; k < NMOM; ++k)
-                m.s[set][k] = m.c[set][k] = 0.0f;
-            m.n[set] = 0;
-        }
+        // per warp: lane v < 2 NMOM holds the compensated sum of moment value v
+        // (gated inliers' values 0 .. NMOM-1, the other inliers' NMOM ..);
+        // the gated / other counts are warp-uniform (ballots)
+        float acc_s = 0.0f, acc_c = 0.0f;
+        int cnt_g = 0, cnt_o = 0;
         const int c1 = min(c0 + GROUP, nch);
         for (int c = c0; c < c1; ++c) {
             const int base = c * CHUNK;
@@ -836,81 +839,67 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
                 const int j = threadIdx.x + u * REMOVE_THREADS;
                 p[u] = j < cnt ? F.cpt[cur][base + j] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            unsigned any = 0u;
+            int kept_w = 0;
 #pragma unroll
             for (int u = 0; u < PER_THREAD; ++u) {
                 const int j = threadIdx.x + u * REMOVE_THREADS;
                 inl[u] = j < cnt && is_inlier(pl, p[u].x, p[u].y, p[u].z, prm.thr2);
                 const unsigned word = __ballot_sync(0xffffffffu, j < cnt && !inl[u]);
-                if (lane == 0) {
+                any |= __ballot_sync(0xffffffffu, inl[u]);
+                kept_w += __popc(word);
+                if (lane == 0)
                     F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)] = word;
-                    sh_kept_w[u][wid] = __popc(word);
+            }
+            if (lane == 0 && kept_w)
+                atomicAdd(F.kept + c, kept_w);
+            if (any) {
+                // validity and normal of every inlier fetched together (one
+                // round trip); the validity bit decides whether the normal counts
+                int pix[PER_THREAD];
+                unsigned char vb[PER_THREAD];
+                float3 nrm[PER_THREAD];
+#pragma unroll
+                for (int u = 0; u < PER_THREAD; ++u) {
+                    pix[u] = __float_as_int(p[u].w);
+                    const bool g = inl[u] && F.N;
+                    vb[u] = g ? F.valid[pix[u]] : 0;
+                    nrm[u] = g ? make_float3(F.N[pix[u]], F.N[npx + pix[u]], F.N[2 * npx + pix[u]])
+                               : make_float3(0.f, 0.f, 0.f);
                 }
-            }
-            int pix[PER_THREAD];
-            unsigned char vb[PER_THREAD];
+                // this lane's candidates, summed per value in registers
+                float v[32];
 #pragma unroll
-            for (int u = 0; u < PER_THREAD; ++u) {
-                const int j = threadIdx.x + u * REMOVE_THREADS;
-                pix[u] = inl[u] ? F.cidx[cur][base + j] : 0;
-            }
+                for (int k = 0; k < 32; ++k)
+                    v[k] = 0.0f;
 #pragma unroll
-            for (int u = 0; u < PER_THREAD; ++u)
-                vb[u] = (inl[u] && F.N) ? F.valid[pix[u]] : 0;
-#pragma unroll
-            for (int u = 0; u < PER_THREAD; ++u) {
-                if (!inl[u])
-                    continue;
-                F.labels[pix[u]] = (short)round;
-                bool gated = false;
-                if (vb[u] & 2) {
-                    const float nx = F.N[pix[u]], ny = F.N[npx + pix[u]], nz = F.N[2 * npx + pix[u]];
-                    const float dot = nx * pl.x + ny * pl.y + nz * pl.z;
-                    gated = fabsf(dot) >= prm.cos_gate;
+                for (int u = 0; u < PER_THREAD; ++u) {
+                    bool gated = false;
+                    if (inl[u]) {
+                        F.labels[pix[u]] = (short)round;
+                        if (vb[u] & 2) {
+                            const float dot = nrm[u].x * pl.x + nrm[u].y * pl.y + nrm[u].z * pl.z;
+                            gated = fabsf(dot) >= prm.cos_gate;
+                        }
+                    }
+                    cnt_g += __popc(__ballot_sync(0xffffffffu, inl[u] && gated));
+                    cnt_o += __popc(__ballot_sync(0xffffffffu, inl[u] && !gated));
+                    if (inl[u])
+                        mom_values(v, gated ? 0 : NMOM, __fsub_rn(p[u].x, p0.x),
+                                   __fsub_rn(p[u].y, p0.y), __fsub_rn(p[u].z, p0.z));
                 }
-                const float qx = __fsub_rn(p[u].x, p0.x), qy = __fsub_rn(p[u].y, p0.y),
-                            qz = __fsub_rn(p[u].z, p0.z);
-                if (gated)
-                    mom_add<0>(m, qx, qy, qz);
-                else
-                    mom_add<1>(m, qx, qy, qz);
+                const float t = warp_transpose_sum(v, lane);
+                if (lane < 2 * NMOM)
+                    nadd(acc_s, acc_c, t);
             }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int kk = 0;
-                for (int u = 0; u < PER_THREAD; ++u)
-                    for (int w = 0; w < nwarps; ++w)
-                        kk += sh_kept_w[u][w];
-                F.kept[c] = kk;
-            }
-            __syncthreads();
         }
-        // warp reduction in a fixed order
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float os[2 * NMOM], oc[2 * NMOM];
-            int on[2];
-#pragma unroll
-            for (int set = 0; set < 2; ++set) {
-#pragma unroll
-                for (int k = 0; k < NMOM; ++k) {
-                    os[set * NMOM + k] = __shfl_down_sync(0xffffffffu, m.s[set][k], o);
-                    oc[set * NMOM + k] = __shfl_down_sync(0xffffffffu, m.c[set][k], o);
-                }
-                on[set] = __shfl_down_sync(0xffffffffu, m.n[set], o);
-            }
-            if (lane < o)
-                mom_merge(m, os, oc, on);
+        if (lane < 2 * NMOM) {
+            sh_s[wid][lane] = acc_s;
+            sh_c[wid][lane] = acc_c;
         }
         if (lane == 0) {
-#pragma unroll
-            for (int set = 0; set < 2; ++set) {
-#pragma unroll
-                for (int k = 0; k < NMOM; ++k) {
-                    sh_s[wid][set * NMOM + k] = m.s[set][k];
-                    sh_c[wid][set * NMOM + k] = m.c[set][k];
-                }
-                sh_n[wid][set] = m.n[set];
-            }
+            sh_n[wid][0] = cnt_g;
+            sh_n[wid][1] = cnt_o;
         }
         __syncthreads();
         // across warps: one thread per moment value, warps merged in order
