@@ -152,10 +152,9 @@ __device__ __forceinline__ float2 pm4_combine(float2 Ip, float fN, float fS, flo
 // with a T-pixel halo, (dx + 2T) x (dy + 2T) float2 cells in shared memory,
 // two buffers.  Iteration it updates the region shrunk by it + 1 on every
 // side.  Each warp (one threadIdx.y) walks a band of rows top to bottom for
-// its columns: the south link flux of a row is the negated north link flux
-// of the next row, and a lane's west link is its left neighbour's east link
-// negated (exactly, see link_flux), so each link is evaluated once, two per
-// pixel instead of four.
+// its columns (lane, lane + 32, ...): the south link flux of a row is the
+// negated north link flux of the next row (exactly, see link_flux), so each
+// pixel evaluates three links (N reused) instead of four.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restrict__ frames,
                                                        int n_frames, int T, int dx, int dy,
@@ -199,57 +198,32 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
         const int y1 = min(y0 + band, SY - r0);
         if (y0 < y1) {
             if (MODE == 0) {
-                // each lane owns the column pairs (x0, x0 + 1), x0 = r0 + 2 lane + 64 g,
-                // walked down together: per row it evaluates the two south links,
-                // the link inside the pair and the one to its right; the link to
-                // its left is the right link of the lane before (or, for lane 0,
-                // of the last lane of the group before), negated.  Every link of
-                // the region is evaluated once, two per pixel.
-                constexpr int G2 = (TILE_MAX_DX + 63) / 64;
-                const int xe = SX - r0;                  // end of the region's columns
-                float2 c0[G2], c1[G2];
-                float fN0[G2], fN1[G2];
+                // the (up to) three column groups of this lane, walked down together
+                constexpr int G = TILE_MAX_DX / 32;
+                float2 cen[G];
+                float fN[G];
 #pragma unroll
-                for (int g = 0; g < G2; ++g) {
-                    const int xa = min(r0 + 2 * lane + 64 * g, SX - 2);
-                    c0[g] = A[y0 * SX + xa];
-                    c1[g] = A[y0 * SX + xa + 1];
-                    fN0[g] = link_flux(c0[g], A[(y0 - 1) * SX + xa], c);
-                    fN1[g] = link_flux(c1[g], A[(y0 - 1) * SX + xa + 1], c);
+                for (int g = 0; g < G; ++g) {
+                    const int x = r0 + lane + 32 * g;
+                    if (x < SX - r0) {
+                        cen[g] = A[y0 * SX + x];
+                        fN[g] = link_flux(cen[g], A[(y0 - 1) * SX + x], c);
+                    }
                 }
                 for (int y = y0; y < y1; ++y) {
-                    float fR_prev = 0.0f;
 #pragma unroll
-                    for (int g = 0; g < G2; ++g) {
-                        const int x0 = r0 + 2 * lane + 64 * g;
-                        if (r0 + 64 * g >= xe)           // the whole group is outside (warp-uniform)
-                            continue;
-                        const int xa = min(x0, SX - 2);
-                        const int k0 = y * SX + xa;
-                        const float2 d0 = A[k0 + SX], d1 = A[k0 + 1 + SX];
-                        const float2 rt = A[min(xa + 2, SX - 1) + y * SX];
-                        const float fS0 = link_flux(c0[g], d0, c);
-                        const float fS1 = link_flux(c1[g], d1, c);
-                        const float fM = link_flux(c0[g], c1[g], c);
-                        const float fR = link_flux(c1[g], rt, c);
-                        const float fR_left = __shfl_up_sync(0xffffffffu, fR, 1);
-                        const float fR_last = __shfl_sync(0xffffffffu, fR, 31);
-                        float fW0;
-                        if (lane > 0)
-                            fW0 = -fR_left;
-                        else if (g > 0)
-                            fW0 = -fR_prev;
-                        else
-                            fW0 = link_flux(c0[g], A[k0 - 1], c);
-                        fR_prev = fR_last;
-                        if (x0 < xe)
-                            B[k0] = pm4_combine(c0[g], fN0[g], fS0, fW0, fM, lam);
-                        if (x0 + 1 < xe)
-                            B[k0 + 1] = pm4_combine(c1[g], fN1[g], fS1, -fM, fR, lam);
-                        fN0[g] = -fS0;
-                        fN1[g] = -fS1;
-                        c0[g] = d0;
-                        c1[g] = d1;
+                    for (int g = 0; g < G; ++g) {
+                        const int x = r0 + lane + 32 * g;
+                        if (x < SX - r0) {
+                            const int k = y * SX + x;
+                            const float2 dn = A[k + SX];
+                            const float fS = link_flux(cen[g], dn, c);
+                            const float fW = link_flux(cen[g], A[k - 1], c);
+                            const float fE = link_flux(cen[g], A[k + 1], c);
+                            B[k] = pm4_combine(cen[g], fN[g], fS, fW, fE, lam);
+                            fN[g] = -fS;
+                            cen[g] = dn;
+                        }
                     }
                 }
             } else {
