@@ -711,47 +711,57 @@ __device__ void smallest_eigenpair(const double a[3][3], double &lmin, double v[
 // run by one block of REMOVE_THREADS threads.
 __device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
 {
+    // The group records are reduced in compensated FP32, in a fixed order
+    // (warp w takes records w, w + 8, ...; lane v value v; then the warps in
+    // order); only the final sums are widened to FP64 for the eigen-solve.
     RState *st = F.st;
     const int ngroups = (st->nchunks + GROUP - 1) / GROUP;
-    double acc[2 * NMOM];
-    long long cnt[2] = {0, 0};
-#pragma unroll
-    for (int k = 0; k < 2 * NMOM; ++k)
-        acc[k] = 0.0;
-    for (int c = threadIdx.x; c < ngroups; c += blockDim.x) {
-        const float *rec = F.partial + (long long)c * PART_WORDS;
-#pragma unroll
-        for (int k = 0; k < 2 * NMOM; ++k)
-            acc[k] += (double)__ldcg(rec + 2 * k) + (double)__ldcg(rec + 2 * k + 1);
-        cnt[0] += __float_as_int(__ldcg(rec + 36));
-        cnt[1] += __float_as_int(__ldcg(rec + 37));
-    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int k = 0; k < 2 * NMOM; ++k)
-            acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
-        cnt[0] += __shfl_down_sync(0xffffffffu, cnt[0], o);
-        cnt[1] += __shfl_down_sync(0xffffffffu, cnt[1], o);
+    const int nw = (int)(blockDim.x >> 5);
+    float vs = 0.0f, vc = 0.0f;
+    int vn = 0;
+    for (int g = wid; g < ngroups; g += nw) {
+        const float *rec = F.partial + (long long)g * PART_WORDS;
+        if (lane < 2 * NMOM) {
+            nadd(vs, vc, __ldcg(rec + 2 * lane));
+            vc = __fadd_rn(vc, __ldcg(rec + 2 * lane + 1));
+        } else if (lane < 2 * NMOM + 2) {
+            vn += __float_as_int(__ldcg(rec + 36 + (lane - 2 * NMOM)));
+        }
     }
-    __shared__ double sacc[8][2 * NMOM];
-    __shared__ long long scnt[8][2];
-    if (lane == 0) {
-        for (int k = 0; k < 2 * NMOM; ++k)
-            sacc[wid][k] = acc[k];
-        scnt[wid][0] = cnt[0];
-        scnt[wid][1] = cnt[1];
+    __shared__ float ss[32][2 * NMOM], sc[32][2 * NMOM];
+    __shared__ int sn[32][2];
+    if (lane < 2 * NMOM) {
+        ss[wid][lane] = vs;
+        sc[wid][lane] = vc;
+    } else if (lane < 2 * NMOM + 2) {
+        sn[wid][lane - 2 * NMOM] = vn;
+    }
+    __syncthreads();
+    __shared__ double acc_sh[2 * NMOM];
+    __shared__ long long cnt_sh[2];
+    if (wid == 0) {
+        if (lane < 2 * NMOM) {
+            float s0 = ss[0][lane], c0 = sc[0][lane];
+            for (int w = 1; w < nw; ++w) {
+                nadd(s0, c0, ss[w][lane]);
+                c0 = __fadd_rn(c0, sc[w][lane]);
+            }
+            acc_sh[lane] = (double)s0 + (double)c0;
+        } else if (lane < 2 * NMOM + 2) {
+            long long t = 0;
+            for (int w = 0; w < nw; ++w)
+                t += sn[w][lane - 2 * NMOM];
+            cnt_sh[lane - 2 * NMOM] = t;
+        }
     }
     __syncthreads();
     if (threadIdx.x != 0)
         return;   // (the caller does not synchronise the block after this)
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-        for (int k = 0; k < 2 * NMOM; ++k)
-            acc[k] += sacc[w][k];
-        cnt[0] += scnt[w][0];
-        cnt[1] += scnt[w][1];
-    }
+    double acc[2 * NMOM];
+    long long cnt[2] = {cnt_sh[0], cnt_sh[1]};
+    for (int k = 0; k < 2 * NMOM; ++k)
+        acc[k] = acc_sh[k];
     // gated inliers if at least 3 pass the gate, else all inliers (set 0 + set 1)
     const bool gated = cnt[0] >= 3;
     const long long nsel = gated ? cnt[0] : cnt[0] + cnt[1];
