@@ -115,6 +115,8 @@ struct pm_ctx {
     char *eg = nullptr;                   // edge / region scratch for max_npx (on first use)
     int *h_eg = nullptr;                  // pinned: region count, error flag
     cudaStream_t gstream = nullptr;       // graph stream when the caller passes the legacy stream
+    cudaStream_t rstream = nullptr;       // side stream of the plane refits
+    cudaEvent_t rev[2] = {nullptr, nullptr};
     cudaEvent_t gev[2] = {nullptr, nullptr};
     long long launches = 0;               // kernels launched by the last call
     int last_n = 0;                       // frames of the last call
@@ -375,6 +377,14 @@ pm_status enqueue_ransac(pm_ctx *ctx, RFrame *d_rframes, int n, long long total_
         L.score_blocks = 1;
     if (L.chunk_blocks < 1)
         L.chunk_blocks = 1;
+    if (!ctx->rstream) {
+        PM_CK(cudaStreamCreateWithFlags(&ctx->rstream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i)
+            PM_CK(cudaEventCreateWithFlags(&ctx->rev[i], cudaEventDisableTiming));
+    }
+    L.side = ctx->rstream;
+    L.ev_fork = ctx->rev[0];
+    L.ev_join = ctx->rev[1];
     PM_CK(ransac_init(L, s));
     ctx->launches += RANSAC_INIT_LAUNCHES;
     for (int r = 0; r < ctx->rp.max_planes; ++r) {
@@ -633,6 +643,11 @@ void pm_destroy(pm_ctx *ctx)
         cudaFreeHost(ctx->h_eg);
     if (ctx->gstream)
         cudaStreamDestroy(ctx->gstream);
+    if (ctx->rstream)
+        cudaStreamDestroy(ctx->rstream);
+    for (int i = 0; i < 2; ++i)
+        if (ctx->rev[i])
+            cudaEventDestroy(ctx->rev[i]);
     for (int i = 0; i < 2; ++i)
         if (ctx->gev[i])
             cudaEventDestroy(ctx->gev[i]);

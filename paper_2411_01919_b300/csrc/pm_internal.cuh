@@ -60,9 +60,10 @@ struct RState {
     int n_planes;
     int nchunks;      // chunks of the current list (0 when done)
     int score_done;   // scoring work items finished this round
-    int remove_done;  // removal groups finished this round
     int best_h;
     int best_count;
+    int refit_pending;  // 1 from an accepted selection until its refit
+    int refit_groups;   // moment records of that round
     float4 best_plane;
     float4 p0;        // first sample point of the winner (moment origin)
     int m_hist[MAX_PLANES];  // candidates scored in each round (0 once stopped)
@@ -199,6 +200,8 @@ struct RansacLaunch {
     int chunk_blocks;
     unsigned *d_counter;  // grid-completion counter of the compaction kernel
     bool fine_score;      // smaller hypothesis blocks, selection fused (small batches)
+    cudaStream_t side;    // the refit's stream
+    cudaEvent_t ev_fork, ev_join;   // removal done -> refit; refit done -> next selection
 };
 // Per-region RANSAC (regions.cu): all pointers device memory.
 struct RegionLaunch {
@@ -253,8 +256,8 @@ int score_ctas_per_sm(bool fine, int H);
 cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream_t s,
                          cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
 constexpr int RANSAC_INIT_LAUNCHES = 3;
-// launches per round: 4 with selection/refit fused (small batches), 6 without;
-// the last round skips compaction
-inline int ransac_round_launches(bool fine) { return fine ? 4 : 6; }
+// launches per round: 5 with the selection fused into scoring (small
+// batches), 6 without; the last round skips compaction
+inline int ransac_round_launches(bool fine) { return fine ? 5 : 6; }
 
 }  // namespace pm

@@ -1,19 +1,23 @@
 // ransac.cu -- sequential multi-plane RANSAC (Sec. III-D, Eq. 3, Alg. 2) for
 // sm_103a, batched over frames.
 //
-// One plane round of every frame still running takes four launches:
+// One plane round of every frame still running:
 //   k_hyp     : Philox4x64-10 -> three candidate indices -> FP32 plane (Alg. 2
 //               "select random subset of 3 points", "fit plane model")
 //   k_score   : every hypothesis against every candidate on FP32 CUDA cores
 //               (Alg. 2 inner parallel loop), skipping the pairs that a box
 //               test proves to hold no inlier; integer counters, one atomic
-//               add per (work item, hypothesis).  The CTA that finishes
-//               a frame's last work item picks the frame's winner: the
-//               maximum count, ties to the lowest index (integer key).
+//               add per (work item, hypothesis).  For small batches the CTA
+//               that finishes a frame's last work item picks the frame's
+//               winner (maximum count, ties to the lowest index: an integer
+//               key); for large ones k_select does, one block per frame.
 //   k_remove  : labels of the winner's inliers, keep bitmask of the rest,
-//               compensated-FP32 moments of the inliers; the CTA that finishes
-//               a frame's last group reduces the moments in FP64 in a fixed
-//               order and solves the 3x3 eigenproblem -> plane.
+//               compensated-FP32 moments of the inliers per group of chunks.
+//   k_refit   : the group records reduced in compensated FP32 in a fixed
+//               order, the 3x3 eigenproblem solved in FP64 -> plane.  It runs
+//               on a side stream beside the compaction and the next round's
+//               hypotheses (and, for large batches, scoring): the next
+//               selection, which overwrites the winner it reads, waits for it.
 //   k_compact : order-preserving compaction of the kept candidates; the last
 //               CTA of the grid plans the next round (candidate counts, stop
 //               rule, cross-frame prefix of chunks).
@@ -117,6 +121,8 @@ __device__ void plan_round(RFrame *frames, int n, int *chunk_base, int min_inlie
             st->n_planes = 0;
             st->best_h = -1;
             st->best_count = -1;
+            st->refit_pending = 0;
+            st->refit_groups = 0;
             for (int r = 0; r < MAX_PLANES; ++r)
                 st->m_hist[r] = 0;
             st->pairs_eval = 0ull;
@@ -354,7 +360,6 @@ __device__ void select_winner(const RFrame &F, const RParams &prm)
             key = wk[w] > key ? wk[w] : key;
         const int best_h = (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
         const int best_count = (int)(key >> 32) - 1;
-        st->remove_done = 0;
         if (best_count < prm.min_inliers || best_count < 3) {
             st->done = 1;
         } else {
@@ -362,6 +367,10 @@ __device__ void select_winner(const RFrame &F, const RParams &prm)
             st->best_count = best_count;
             st->best_plane = __ldcg(F.hyp + best_h);
             st->p0 = __ldcg(F.hyp_p0 + best_h);
+            // what this round's refit needs, fixed before the next round's
+            // planning changes the frame's state
+            st->refit_groups = (st->nchunks + GROUP - 1) / GROUP;
+            st->refit_pending = 1;
         }
     }
     __syncthreads();
@@ -595,7 +604,7 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
 }
 
 // ---------------------------------------------------------------------------
-// removal + compensated moments, refit by the last CTA of each frame
+// removal + compensated moments; refit of each frame's plane
 // ---------------------------------------------------------------------------
 
 // Neumaier compensated accumulation in FP32.
@@ -715,7 +724,7 @@ __device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
     // (warp w takes records w, w + 8, ...; lane v value v; then the warps in
     // order); only the final sums are widened to FP64 for the eigen-solve.
     RState *st = F.st;
-    const int ngroups = (st->nchunks + GROUP - 1) / GROUP;
+    const int ngroups = st->refit_groups;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = (int)(blockDim.x >> 5);
     float vs = 0.0f, vc = 0.0f;
@@ -795,6 +804,7 @@ __device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
     out.rms = (float)sqrt(fmax(lmin, 0.0));
     out.hyp_index = st->best_h;
     st->n_planes += 1;
+    st->refit_pending = 0;
     if (round + 1 >= prm.max_planes)
         st->done = 1;
 }
@@ -805,11 +815,10 @@ __device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
 // rest of the batch.  Per chunk: labels, keep bitmask and kept count.  Per
 // group: one record of compensated moments of the inliers, centred at the
 // winner's first sample point, in two disjoint sets -- set 0: inliers whose
-// normal passes the refit gate, set 1: the other inliers.  The CTA that
-// finishes a frame's last group refits the frame's plane.
+// normal passes the refit gate, set 1: the other inliers.
 __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n,
                                                            const int *chunk_base, RParams prm,
-                                                           int round, bool fuse_refit)
+                                                           int round)
 {
     __shared__ float sh_s[8][2 * NMOM], sh_c[8][2 * NMOM];
     __shared__ int sh_n[8][2];
@@ -930,8 +939,6 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
                 nn += sh_n[w][set];
             rec[36 + set] = __int_as_float(nn);
         }
-        if (fuse_refit && last_item_of_frame(&st->remove_done, (st->nchunks + GROUP - 1) / GROUP))
-            refit_frame(F, prm, round);
         __syncthreads();
     }
 }
@@ -947,10 +954,12 @@ __global__ void __launch_bounds__(1024) k_select(RFrame *frames, RParams prm)
     select_winner(F, prm);
 }
 
+// Runs beside the next round's planning, which may already stop the frame:
+// it refits the frames whose selection accepted a winner this round.
 __global__ void __launch_bounds__(REMOVE_THREADS) k_refit(RFrame *frames, RParams prm, int round)
 {
     const RFrame &F = frames[blockIdx.x];
-    if (F.st->done)
+    if (!F.st->refit_pending)
         return;
     refit_frame(F, prm, round);
 }
@@ -1013,29 +1022,45 @@ cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream
     k_hyp<<<dim3((p.H + 127) / 128, L.n), 128, 0, s>>>(L.d_frames, p, round);
     if (ev_before)
         record_event(ev_before, s);
-    // coarse work items (whole chunks, all hypotheses per CTA) when there are
-    // enough of them to fill the GPU; finer ones (half chunks, half of the
-    // hypotheses) for small batches and late rounds
-    // small batches also fold the selection into the scoring launch and the
-    // refit into the removal launch
+    // coarse work items (512-hypothesis blocks, separate selection) when there
+    // are enough chunks to fill the GPU; 256-hypothesis blocks with the
+    // selection folded into the scoring launch for small batches.  The
+    // selection overwrites the winner the previous round's refit reads, so it
+    // waits for that refit.
     const bool fine = L.fine_score;
-    if (fine)
+    cudaError_t e = cudaSuccess;
+    if (fine) {
+        if (round > 0)
+            e = cudaStreamWaitEvent(s, L.ev_join, 0);
         launch_score<256, true>(L, round, s);
-    else if (p.H <= 256)
-        launch_score<256, false>(L, round, s);
-    else
-        launch_score<512, false>(L, round, s);
+    } else {
+        if (p.H <= 256)
+            launch_score<256, false>(L, round, s);
+        else
+            launch_score<512, false>(L, round, s);
+        if (round > 0)
+            e = cudaStreamWaitEvent(s, L.ev_join, 0);
+    }
+    if (e != cudaSuccess)
+        return e;
     if (ev_after)
         record_event(ev_after, s);
     if (!fine)
         k_select<<<L.n, 1024, 0, s>>>(L.d_frames, p);
-    k_remove<<<L.chunk_blocks, REMOVE_THREADS, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round,
-                                                       fine);
-    if (!fine)
-        k_refit<<<L.n, REMOVE_THREADS, 0, s>>>(L.d_frames, p, round);
+    k_remove<<<L.chunk_blocks, REMOVE_THREADS, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
+    // the refit runs beside the compaction (and the next round's hypotheses
+    // and scoring) on the side stream: nothing there reads its result
+    if ((e = cudaEventRecord(L.ev_fork, s)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(L.side, L.ev_fork, 0)) != cudaSuccess)
+        return e;
+    k_refit<<<L.n, REMOVE_THREADS, 0, L.side>>>(L.d_frames, p, round);
+    if ((e = cudaEventRecord(L.ev_join, L.side)) != cudaSuccess)
+        return e;
     if (!last)
         k_compact<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, round, false,
                                                  round + 1, p.min_inliers, L.d_counter);
+    else if ((e = cudaStreamWaitEvent(s, L.ev_join, 0)) != cudaSuccess)
+        return e;
     return cudaGetLastError();
 }
 
