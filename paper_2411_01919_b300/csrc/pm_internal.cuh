@@ -17,7 +17,7 @@ constexpr int CHUNK_WORDS = CHUNK / 32;  // keep-bitmask words per chunk
 constexpr int MAX_HYP = 2048;            // hypotheses per round (score kernel register budget)
 constexpr int MAX_PLANES = 64;
 constexpr int NMOM = 9;                  // Sx Sy Sz Sxx Sxy Sxz Syy Syz Szz
-constexpr int GROUP = 4;                 // chunks per moment record
+constexpr int GROUP = 1;                 // chunks per moment record
 constexpr int REMOVE_THREADS = 256;      // threads of the removal kernel (CHUNK / 4 candidates each)
 // per-group moment record: gated inliers then the other inliers, each NMOM
 // (sum, comp) float pairs, then two int counts (as float bit patterns), padded

@@ -729,13 +729,28 @@ __device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
     const int nw = (int)(blockDim.x >> 5);
     float vs = 0.0f, vc = 0.0f;
     int vn = 0;
-    for (int g = wid; g < ngroups; g += nw) {
-        const float *rec = F.partial + (long long)g * PART_WORDS;
-        if (lane < 2 * NMOM) {
-            nadd(vs, vc, __ldcg(rec + 2 * lane));
-            vc = __fadd_rn(vc, __ldcg(rec + 2 * lane + 1));
-        } else if (lane < 2 * NMOM + 2) {
-            vn += __float_as_int(__ldcg(rec + 36 + (lane - 2 * NMOM)));
+    // lane v < 2 NMOM: (sum, compensation) of value v; lanes 2 NMOM, +1: counts
+    const int word = lane < 2 * NMOM ? 2 * lane : 36 + min(lane - 2 * NMOM, 1);
+    constexpr int UNR = 4;   // records loaded together
+    for (int g0 = wid * UNR; g0 < ngroups; g0 += nw * UNR) {
+        float a[UNR], b[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const float *rec = F.partial + (long long)(g0 + u) * PART_WORDS;
+            const bool ok = g0 + u < ngroups;
+            a[u] = ok ? __ldcg(rec + word) : 0.0f;
+            b[u] = ok && lane < 2 * NMOM ? __ldcg(rec + word + 1) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            if (g0 + u >= ngroups)
+                break;
+            if (lane < 2 * NMOM) {
+                nadd(vs, vc, a[u]);
+                vc = __fadd_rn(vc, b[u]);
+            } else if (lane < 2 * NMOM + 2) {
+                vn += __float_as_int(a[u]);
+            }
         }
     }
     __shared__ float ss[32][2 * NMOM], sc[32][2 * NMOM];
