@@ -368,7 +368,7 @@ pm_status enqueue_ransac(pm_ctx *ctx, RFrame *d_rframes, int n, long long total_
     L.d_counter = ctx->at<unsigned>(ctx->lay.counter);
     L.fine_score = total_chunks < (long long)ctx->sms * 32;
     const int hb = score_hyp_block(L.fine_score, L.prm.H);
-    const long long score_items = total_chunks * ((L.prm.H + hb - 1) / hb);
+    const long long score_items = total_chunks * (L.fine_score ? (L.prm.H + hb - 1) / hb : 1);
     const long long sb = (long long)ctx->sms * score_ctas_per_sm(L.fine_score, L.prm.H);
     const long long cb = (long long)ctx->sms * 4;
     L.score_blocks = (int)(score_items < sb ? score_items : sb);

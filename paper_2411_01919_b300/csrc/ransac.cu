@@ -474,7 +474,11 @@ __device__ __forceinline__ void score_list(const float4 *hpl, const unsigned sho
         score_batch<1, FULL>(hpl, lst, e0, len, sp, sc, nthr2, hcnt, lane);
 }
 
-template <int HB, bool FUSE>
+// INNER: a work item is a whole chunk, its hypothesis blocks scored one
+// after another on the same points and boxes (large batches); otherwise a
+// work item is one (chunk, hypothesis block) pair (more items for small
+// batches).
+template <int HB, bool FUSE, bool INNER>
 __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
                                                          const int *chunk_base, RParams prm,
                                                          int round)
@@ -489,116 +493,123 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
     __shared__ int next_seg;
     __shared__ unsigned long long evaluated;
     const int nhb = (prm.H + HB - 1) / HB;
-    const int total = chunk_base[n] * nhb;
+    const int per_chunk = INNER ? 1 : nhb;
+    const int total = chunk_base[n] * per_chunk;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const float nthr2 = -prm.thr2;
     unsigned short *my = lst + wid * HB;
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
-        const int wi = it / nhb, hb = it - wi * nhb;
+        const int wi = it / per_chunk;
+        const int hb_first = INNER ? 0 : it - wi * nhb, hb_end = INNER ? nhb : hb_first + 1;
         const int f = frame_of(chunk_base, n, wi);
         const RFrame &F = frames[f];
         RState *st = F.st;
         const int c = wi - chunk_base[f];
         const int base = c * CHUNK;
         const int cnt = max(0, min(CHUNK, st->M - base));
-        const int h0 = hb * HB;
-        const int nh = min(HB, prm.H - h0);
         const float4 *src = F.cpt[round & 1] + base;
+        const int nseg = (cnt + SEG - 1) / SEG;
         __syncthreads();
         for (int j = threadIdx.x; j < cnt; j += SCORE_THREADS)
             pts[j] = src[j];
-        for (int k = threadIdx.x; k < HB; k += SCORE_THREADS) {
-            float4 pl = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
-            float w = -1.0f;                     // culls everywhere
-            if (k < nh) {
-                const float4 q = F.hyp[h0 + k];
-                if (fabsf(q.w) <= 3.0e38f) {     // degenerate planes carry d = +inf
-                    pl = q;
-                    w = __fmaf_ru(CULL_SLACK, fabsf(q.w), prm.cull_thr);
+        for (int hb = hb_first; hb < hb_end; ++hb) {
+            const int h0 = hb * HB;
+            const int nh = min(HB, prm.H - h0);
+            for (int k = threadIdx.x; k < HB; k += SCORE_THREADS) {
+                float4 pl = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+                float w = -1.0f;                     // culls everywhere
+                if (k < nh) {
+                    const float4 q = F.hyp[h0 + k];
+                    if (fabsf(q.w) <= 3.0e38f) {     // degenerate planes carry d = +inf
+                        pl = q;
+                        w = __fmaf_ru(CULL_SLACK, fabsf(q.w), prm.cull_thr);
+                    }
                 }
+                hpl[k] = pl;
+                hw[k] = w;
+                hcnt[k] = 0;
             }
-            hpl[k] = pl;
-            hw[k] = w;
-            hcnt[k] = 0;
-        }
-        if (threadIdx.x == 0) {
-            next_seg = 0;
-            evaluated = 0ull;
-        }
-        __syncthreads();
-        const int nseg = (cnt + SEG - 1) / SEG;
-        for (int sg = wid; sg < nseg; sg += SCORE_WARPS) {
-            const float4 p = pts[min(sg * SEG + lane, cnt - 1)];
-            float lx = p.x, ly = p.y, lz = p.z, ux = p.x, uy = p.y, uz = p.z;
+            if (threadIdx.x == 0) {
+                next_seg = 0;
+                evaluated = 0ull;
+            }
+            __syncthreads();
+            if (hb == hb_first) {
+                for (int sg = wid; sg < nseg; sg += SCORE_WARPS) {
+                    const float4 p = pts[min(sg * SEG + lane, cnt - 1)];
+                    float lx = p.x, ly = p.y, lz = p.z, ux = p.x, uy = p.y, uz = p.z;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
-                ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
-                lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
-                ux = fmaxf(ux, __shfl_xor_sync(0xffffffffu, ux, o));
-                uy = fmaxf(uy, __shfl_xor_sync(0xffffffffu, uy, o));
-                uz = fmaxf(uz, __shfl_xor_sync(0xffffffffu, uz, o));
+                    for (int o = 16; o > 0; o >>= 1) {
+                        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+                        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+                        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+                        ux = fmaxf(ux, __shfl_xor_sync(0xffffffffu, ux, o));
+                        uy = fmaxf(uy, __shfl_xor_sync(0xffffffffu, uy, o));
+                        uz = fmaxf(uz, __shfl_xor_sync(0xffffffffu, uz, o));
+                    }
+                    if (lane < 3) {
+                        // lane k handles axis k: centre, half-size rounded up and
+                        // widened by the centre's rounding, then g = e + s (|c| + e)
+                        const float lo = lane == 0 ? lx : lane == 1 ? ly : lz;
+                        const float hi = lane == 0 ? ux : lane == 1 ? uy : uz;
+                        const float cc = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+                        const float e = __fadd_ru(__fmul_ru(__fsub_ru(hi, lo), 0.5f),
+                                                  __fmul_ru(fabsf(cc), 0x1p-23f));
+                        const float g = __fmaf_ru(CULL_SLACK, __fadd_ru(fabsf(cc), e), e);
+                        float *b = reinterpret_cast<float *>(box + 2 * sg);
+                        b[lane] = cc;
+                        b[4 + lane] = g;
+                    }
+                }
+                __syncthreads();
             }
-            if (lane < 3) {
-                // lane k handles axis k: centre, half-size rounded up and
-                // widened by the centre's rounding, then g = e + s (|c| + e)
-                const float lo = lane == 0 ? lx : lane == 1 ? ly : lz;
-                const float hi = lane == 0 ? ux : lane == 1 ? uy : uz;
-                const float cc = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
-                const float e = __fadd_ru(__fmul_ru(__fsub_ru(hi, lo), 0.5f),
-                                          __fmul_ru(fabsf(cc), 0x1p-23f));
-                const float g = __fmaf_ru(CULL_SLACK, __fadd_ru(fabsf(cc), e), e);
-                float *b = reinterpret_cast<float *>(box + 2 * sg);
-                b[lane] = cc;
-                b[4 + lane] = g;
+            unsigned long long mine = 0ull;
+            for (;;) {
+                int sg = 0;
+                if (lane == 0)
+                    sg = atomicAdd(&next_seg, 1);
+                sg = __shfl_sync(0xffffffffu, sg, 0);
+                if (sg >= nseg)
+                    break;
+                const float4 bc = box[2 * sg], bg = box[2 * sg + 1];
+                int len = 0;
+                for (int k = lane; k < nh + ((32 - (nh & 31)) & 31); k += 32) {
+                    const float4 pl = hpl[k];
+                    float t = __fmaf_rn(pl.x, bc.x, pl.w);
+                    t = __fmaf_rn(pl.y, bc.y, t);
+                    t = __fmaf_rn(pl.z, bc.z, t);
+                    float lim = __fmaf_rn(fabsf(pl.x), bg.x, hw[k]);
+                    lim = __fmaf_rn(fabsf(pl.y), bg.y, lim);
+                    lim = __fmaf_rn(fabsf(pl.z), bg.z, lim);
+                    const bool keep = !(fabsf(t) > lim);
+                    const unsigned m = __ballot_sync(0xffffffffu, keep);
+                    if (keep)
+                        my[len + __popc(m & lt)] = (unsigned short)k;
+                    len += __popc(m);
+                }
+                __syncwarp();
+                const int sc = min(SEG, cnt - sg * SEG);
+                mine += (unsigned long long)len * (unsigned)sc;
+                if (sc == SEG)
+                    score_list<true>(hpl, my, len, pts + sg * SEG, sc, nthr2, hcnt, lane);
+                else
+                    score_list<false>(hpl, my, len, pts + sg * SEG, sc, nthr2, hcnt, lane);
+                __syncwarp();   // the list is rewritten for the next segment
             }
-        }
-        __syncthreads();
-        unsigned long long mine = 0ull;
-        for (;;) {
-            int sg = 0;
-            if (lane == 0)
-                sg = atomicAdd(&next_seg, 1);
-            sg = __shfl_sync(0xffffffffu, sg, 0);
-            if (sg >= nseg)
-                break;
-            const float4 bc = box[2 * sg], bg = box[2 * sg + 1];
-            int len = 0;
-            for (int k = lane; k < nh + ((32 - (nh & 31)) & 31); k += 32) {
-                const float4 pl = hpl[k];
-                float t = __fmaf_rn(pl.x, bc.x, pl.w);
-                t = __fmaf_rn(pl.y, bc.y, t);
-                t = __fmaf_rn(pl.z, bc.z, t);
-                float lim = __fmaf_rn(fabsf(pl.x), bg.x, hw[k]);
-                lim = __fmaf_rn(fabsf(pl.y), bg.y, lim);
-                lim = __fmaf_rn(fabsf(pl.z), bg.z, lim);
-                const bool keep = !(fabsf(t) > lim);
-                const unsigned m = __ballot_sync(0xffffffffu, keep);
-                if (keep)
-                    my[len + __popc(m & lt)] = (unsigned short)k;
-                len += __popc(m);
+            if (lane == 0 && mine)
+                atomicAdd(&evaluated, mine);
+            __syncthreads();
+            for (int k = threadIdx.x; k < nh; k += SCORE_THREADS) {
+                const int v = hcnt[k];
+                if (v)
+                    atomicAdd(F.counts + h0 + k, v);
             }
-            __syncwarp();
-            const int sc = min(SEG, cnt - sg * SEG);
-            mine += (unsigned long long)len * (unsigned)sc;
-            if (sc == SEG)
-                score_list<true>(hpl, my, len, pts + sg * SEG, sc, nthr2, hcnt, lane);
-            else
-                score_list<false>(hpl, my, len, pts + sg * SEG, sc, nthr2, hcnt, lane);
-            __syncwarp();   // the list is rewritten for the next segment
+            if (threadIdx.x == 0 && evaluated)
+                atomicAdd(&st->pairs_eval, evaluated);
+            __syncthreads();   // hpl, hw, hcnt are refilled for the next block
         }
-        if (lane == 0 && mine)
-            atomicAdd(&evaluated, mine);
-        __syncthreads();
-        for (int k = threadIdx.x; k < nh; k += SCORE_THREADS) {
-            const int v = hcnt[k];
-            if (v)
-                atomicAdd(F.counts + h0 + k, v);
-        }
-        if (threadIdx.x == 0 && evaluated)
-            atomicAdd(&st->pairs_eval, evaluated);
-        if (FUSE && last_item_of_frame(&st->score_done, st->nchunks * nhb))
+        if (FUSE && last_item_of_frame(&st->score_done, st->nchunks * per_chunk))
             select_winner(F, prm);
     }
 }
@@ -991,22 +1002,22 @@ cudaError_t ransac_init(const RansacLaunch &L, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int HB, bool FUSE>
+template <int HB, bool FUSE, bool INNER>
 static void launch_score(const RansacLaunch &L, int round, cudaStream_t s)
 {
-    k_score<HB, FUSE><<<L.score_blocks, SCORE_THREADS, score_smem_bytes<HB>(), s>>>(
+    k_score<HB, FUSE, INNER><<<L.score_blocks, SCORE_THREADS, score_smem_bytes<HB>(), s>>>(
         L.d_frames, L.n, L.d_chunk_base, L.prm, round);
 }
 
-template <int HB, bool FUSE>
+template <int HB, bool FUSE, bool INNER>
 static cudaError_t score_attr(int *ctas)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_score<HB, FUSE>,
+    cudaError_t e = cudaFuncSetAttribute(k_score<HB, FUSE, INNER>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)score_smem_bytes<HB>());
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_score<HB, FUSE>, SCORE_THREADS,
-                                                          score_smem_bytes<HB>());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_score<HB, FUSE, INNER>,
+                                                          SCORE_THREADS, score_smem_bytes<HB>());
     return e;
 }
 
@@ -1014,11 +1025,11 @@ static int g_score_ctas[3] = {1, 1, 1};   // CTAs per SM: <256,true>, <256,false
 
 cudaError_t score_init()
 {
-    cudaError_t e = score_attr<256, true>(&g_score_ctas[0]);
+    cudaError_t e = score_attr<256, true, false>(&g_score_ctas[0]);
     if (e == cudaSuccess)
-        e = score_attr<256, false>(&g_score_ctas[1]);
+        e = score_attr<256, false, true>(&g_score_ctas[1]);
     if (e == cudaSuccess)
-        e = score_attr<512, false>(&g_score_ctas[2]);
+        e = score_attr<512, false, true>(&g_score_ctas[2]);
     return e;
 }
 
@@ -1047,12 +1058,12 @@ cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream
     if (fine) {
         if (round > 0)
             e = cudaStreamWaitEvent(s, L.ev_join, 0);
-        launch_score<256, true>(L, round, s);
+        launch_score<256, true, false>(L, round, s);
     } else {
         if (p.H <= 256)
-            launch_score<256, false>(L, round, s);
+            launch_score<256, false, true>(L, round, s);
         else
-            launch_score<512, false>(L, round, s);
+            launch_score<512, false, true>(L, round, s);
         if (round > 0)
             e = cudaStreamWaitEvent(s, L.ev_join, 0);
     }
