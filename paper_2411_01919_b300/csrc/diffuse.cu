@@ -198,32 +198,28 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
         const int y1 = min(y0 + band, SY - r0);
         if (y0 < y1) {
             if (MODE == 0) {
-                // the (up to) three column groups of this lane, walked down together
-                constexpr int G = TILE_MAX_DX / 32;
-                float2 cen[G];
-                float fN[G];
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
+                // the lane's columns x = r0 + lane + 32 g, one group at a time,
+                // each walked down the band with running pointers; lanes past
+                // the region's right edge compute on a clamped column and do
+                // not store
+                const int xe = SX - r0;
+                for (int g = 0; r0 + 32 * g < xe; ++g) {
                     const int x = r0 + lane + 32 * g;
-                    if (x < SX - r0) {
-                        cen[g] = A[y0 * SX + x];
-                        fN[g] = link_flux(cen[g], A[(y0 - 1) * SX + x], c);
-                    }
-                }
-                for (int y = y0; y < y1; ++y) {
-#pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        const int x = r0 + lane + 32 * g;
-                        if (x < SX - r0) {
-                            const int k = y * SX + x;
-                            const float2 dn = A[k + SX];
-                            const float fS = link_flux(cen[g], dn, c);
-                            const float fW = link_flux(cen[g], A[k - 1], c);
-                            const float fE = link_flux(cen[g], A[k + 1], c);
-                            B[k] = pm4_combine(cen[g], fN[g], fS, fW, fE, lam);
-                            fN[g] = -fS;
-                            cen[g] = dn;
-                        }
+                    const bool act = x < xe;
+                    const float2 *pa = A + y0 * SX + (act ? x : xe - 1);
+                    float2 *pb = B + y0 * SX + (act ? x : xe - 1);
+                    float2 cen = pa[0];
+                    float fN = link_flux(cen, pa[-SX], c);
+                    for (int y = y0; y < y1; ++y, pa += SX, pb += SX) {
+                        const float2 dn = pa[SX];
+                        const float fS = link_flux(cen, dn, c);
+                        const float fW = link_flux(cen, pa[-1], c);
+                        const float fE = link_flux(cen, pa[1], c);
+                        const float2 v = pm4_combine(cen, fN, fS, fW, fE, lam);
+                        if (act)
+                            *pb = v;
+                        fN = -fS;
+                        cen = dn;
                     }
                 }
             } else {
