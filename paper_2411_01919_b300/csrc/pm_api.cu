@@ -303,7 +303,8 @@ Plan build_tables(pm_ctx *ctx, const std::vector<FrameJob> &jobs, int T, bool ra
             nt[f] = NormFrame{j.depth_out, ctx->at<float>(ctx->lay.P) + 3 * slot,
                               ctx->at<float>(ctx->lay.N) + 3 * slot,
                               ctx->at<unsigned char>(ctx->lay.valid) + slot, j.w, j.h,
-                              j.fx, j.fy, j.cx, j.cy};
+                              j.fx, j.fy, j.cx, j.cy, (float)(1.0 / (double)j.fx),
+                              (float)(1.0 / (double)j.fy)};
         }
     }
     off += align_up(n * sizeof(NormFrame), 256);

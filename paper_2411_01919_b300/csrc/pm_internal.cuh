@@ -187,6 +187,7 @@ struct NormFrame {
     unsigned char *valid;
     int w, h;
     float fx, fy, cx, cy;
+    float ifx, ify;          // 1/fx, 1/fy (rounded from FP64)
 };
 
 // RANSAC round structure (ransac.cu)

@@ -229,44 +229,35 @@ __global__ void __launch_bounds__(256) k_mark0(RFrame *frames, int n, const int 
     }
 }
 
-// Order-preserving compaction of chunk c of the source list into list `dst`.
+// Order-preserving compaction of chunk c of the source list into list `dst`;
+// `off` is the number of candidates kept in the frame's chunks before c.
 // src_image: the source is the pixel array itself (round 0).
 __device__ void compact_chunk(const RFrame &F, int c, int nchunks, int src, int dst,
-                              bool src_image)
+                              bool src_image, int off)
 {
-    __shared__ int s_off;
     __shared__ int s_wpre[CHUNK_WORDS + 1];
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < 32) {
-        int s = 0;
-        for (int k = lane; k < c; k += 32)
-            s += F.kept[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-        unsigned wbits = F.keepbits[(long long)c * CHUNK_WORDS + lane];
-        int x = __popc(wbits);
+        const unsigned wbits = F.keepbits[(long long)c * CHUNK_WORDS + lane];
+        const int x = __popc(wbits);
         int incl = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o)
                 incl += y;
         }
         s_wpre[lane] = incl - x;
         if (lane == 31)
             s_wpre[CHUNK_WORDS] = incl;
-        if (lane == 0)
-            s_off = s;
     }
     __syncthreads();
-    const int off = s_off;
     const long long base = (long long)c * CHUNK;
     const long long npx = F.npx;
     for (int j = threadIdx.x; j < CHUNK; j += blockDim.x) {
-        unsigned word = F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)];
+        const unsigned word = F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)];
         if (word >> (j & 31) & 1u) {
-            int pos = off + s_wpre[j >> 5] + __popc(word & ((1u << (j & 31)) - 1u));
+            const int pos = off + s_wpre[j >> 5] + __popc(word & ((1u << (j & 31)) - 1u));
             float4 pt;
             if (src_image) {
                 const int pix = (int)(base + j);
@@ -282,20 +273,57 @@ __device__ void compact_chunk(const RFrame &F, int c, int nchunks, int src, int 
     __syncthreads();
 }
 
+// Kept candidates of chunks [0, c) of a frame, summed by the whole block.
+__device__ int kept_before(const RFrame &F, int c)
+{
+    __shared__ int s_part[32];
+    __shared__ int s_sum;
+    int s = 0;
+    for (int k = threadIdx.x; k < c; k += blockDim.x)
+        s += F.kept[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0)
+        s_part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int t = (int)threadIdx.x < (int)(blockDim.x >> 5) ? s_part[threadIdx.x] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0)
+            s_sum = t;
+    }
+    __syncthreads();
+    return s_sum;
+}
+
 // Compaction of every chunk; the last CTA of the grid plans round `next`.
 // src_image: round 0 (the source list is the pixel array itself).
 __global__ void __launch_bounds__(256) k_compact(RFrame *frames, int n, int *chunk_base,
                                                  int round, bool src_image, int next,
                                                  int min_inliers, unsigned *grid_counter)
 {
+    // each CTA takes a contiguous run of chunks, so the running offset within
+    // a frame is summed once per run and then advanced chunk by chunk
     const int total = chunk_base[n];
     const int src = round & 1, dst = src_image ? 0 : src ^ 1;
-    for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
+    const int per = (total + gridDim.x - 1) / gridDim.x;
+    const int w0 = blockIdx.x * per, w1 = min(total, w0 + per);
+    int cur_f = -1, off = 0;
+    for (int wi = w0; wi < w1; ++wi) {
         const int f = frame_of(chunk_base, n, wi);
         const RFrame &F = frames[f];
         if (F.st->done)
             continue;
-        compact_chunk(F, wi - chunk_base[f], F.st->nchunks, src, dst, src_image);
+        const int c = wi - chunk_base[f];
+        if (f != cur_f) {
+            off = kept_before(F, c);
+            cur_f = f;
+        }
+        compact_chunk(F, c, F.st->nchunks, src, dst, src_image, off);
+        off += __ldcg(F.kept + c);
     }
     if (last_cta_of_grid(grid_counter))
         plan_round(frames, n, chunk_base, min_inliers, next, false);
