@@ -231,46 +231,42 @@ __global__ void __launch_bounds__(256) k_mark0(RFrame *frames, int n, const int 
 
 // Order-preserving compaction of chunk c of the source list into list `dst`;
 // `off` is the number of candidates kept in the frame's chunks before c.
+// Every warp scans the chunk's 32 keep words itself (lane = word) and moves
+// the candidates of words wid, wid + 8, ...: no block barrier per chunk.
 // src_image: the source is the pixel array itself (round 0).
 __device__ void compact_chunk(const RFrame &F, int c, int nchunks, int src, int dst,
                               bool src_image, int off)
 {
-    __shared__ int s_wpre[CHUNK_WORDS + 1];
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x < 32) {
-        const unsigned wbits = F.keepbits[(long long)c * CHUNK_WORDS + lane];
-        const int x = __popc(wbits);
-        int incl = x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned mine = F.keepbits[(long long)c * CHUNK_WORDS + lane];
+    const int x = __popc(mine);
+    int incl = x;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o)
-                incl += y;
-        }
-        s_wpre[lane] = incl - x;
-        if (lane == 31)
-            s_wpre[CHUNK_WORDS] = incl;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += y;
     }
-    __syncthreads();
+    const int excl = incl - x;
     const long long base = (long long)c * CHUNK;
     const long long npx = F.npx;
-    for (int j = threadIdx.x; j < CHUNK; j += blockDim.x) {
-        const unsigned word = F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)];
-        if (word >> (j & 31) & 1u) {
-            const int pos = off + s_wpre[j >> 5] + __popc(word & ((1u << (j & 31)) - 1u));
+    const unsigned lt = (1u << lane) - 1u;
+    for (int w = wid; w < CHUNK_WORDS; w += (int)(blockDim.x >> 5)) {
+        const unsigned word = __shfl_sync(0xffffffffu, mine, w);
+        const int wpre = __shfl_sync(0xffffffffu, excl, w);
+        if (word >> lane & 1u) {
+            const int pos = off + wpre + __popc(word & lt);
+            const long long j = base + 32 * w + lane;
             float4 pt;
-            if (src_image) {
-                const int pix = (int)(base + j);
-                pt = make_float4(F.P[pix], F.P[npx + pix], F.P[2 * npx + pix], __int_as_float(pix));
-            } else {
-                pt = F.cpt[src][base + j];
-            }
+            if (src_image)
+                pt = make_float4(F.P[j], F.P[npx + j], F.P[2 * npx + j], __int_as_float((int)j));
+            else
+                pt = F.cpt[src][j];
             F.cpt[dst][pos] = pt;
         }
     }
-    if (threadIdx.x == 0 && c == nchunks - 1)
-        F.st->M_next = off + s_wpre[CHUNK_WORDS];
-    __syncthreads();
+    if (threadIdx.x == 31 && c == nchunks - 1)
+        F.st->M_next = off + incl;
 }
 
 // Kept candidates of chunks [0, c) of a frame, summed by the whole block.
