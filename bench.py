@@ -37,7 +37,7 @@ FP32_FLOP_PER_PAIR = 8          # 3 FMA residual + 1 FMA squared-threshold test
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on round 0
 # of 32 frames of this workload: 156.4 MB for 9.73e9 pairs.  With the number
 # of hypotheses fixed, traffic grows with the candidate count, i.e. with pairs.
-SCORE_DRAM_BYTES_PER_PAIR = (152.73e6 + 3.60e6) / 9.73e9   # ncu, k_score round 0, 32 frames
+SCORE_DRAM_BYTES_PER_PAIR = (152.80e6 + 3.58e6) / 9.73e9   # ncu, k_score round 0, 32 frames
 SEGMENT, BOX_TEST_FLOP = 32, 12
 REGION_FLOP_PER_PAIR = 9     # 3 FMA residual, |r| x 2^32, 1 FMA inlier test
 SM_COUNT, FP32_LANES = 148, 128
@@ -437,10 +437,12 @@ def run_ours(args):
         pipe1.process_frame(dframes[i], K, frame_idx=i, labels=False)
     lat = []
     n_plain = min(args.plain_frames, B)
+    torch.cuda.nvtx.range_push('plain')
     for i in range(n_plain):
         t0 = time.perf_counter()
         pipe1.process_frame(dframes[i], K, frame_idx=i, labels=False)
         lat.append(1e3 * (time.perf_counter() - t0))
+    torch.cuda.nvtx.range_pop()
     pipe1.set_timing(1)
     stage = []
     for i in range(min(8, B)):
