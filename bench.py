@@ -131,7 +131,10 @@ def run_reference(args):
             'n_gpus': world, 'steps': args.steps, 'warmup': args.warmup,
             'ms_per_step': 1e3 * tot / args.steps, 'higher_is_better': True, 'scaling': 'weak',
             'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-            'config': {'workload': WORKLOAD, 'batch_per_step': 1},
+            'config': {'workload': WORKLOAD, 'batch_per_gpu': args.batch,
+                       'form': 'FP64 CPU oracle; each step times one frame of the batch (a '
+                               'bounded sample), frames/s from those frames',
+                       'parallelism': 'one host core'},
             'cpu_baseline': {'value': value, 'unit': 'frames/s', 'cores': 1, 'kind': 'oracle',
                              'sample': sample},
             'e2e': {'value': value, 'unit': 'frames/s', 'h2d_bytes_per_step': 0,
