@@ -6,10 +6,13 @@
 // rounding error of the iterate grows from one iteration to the next: a plain
 // FP32 iterate drifts 2e-5 m (640x480 staircase, 30 iterations) to 1.5e-4 m
 // (far spiral floor, 40 iterations) away from exact arithmetic.  The iterate
-// is therefore carried as a compensated pair of FP32 numbers (hi, lo) with
-// I = hi + lo: the u16 decode is split exactly (two-product), neighbour
-// differences include the lo parts, and the update I + lambda * s is added
-// with an error-free two-sum.  All arithmetic stays on the FP32 pipes.
+// is therefore carried as a pair of FP32 numbers (hi, lo) with I = hi + lo:
+// hi is the decoded depth, split exactly from the u16 encoding (two-product)
+// and never changed; lo starts at the decode's tail and accumulates every
+// update.  lo stays within a few centimetres, so its rounding is near 1e-9 m;
+// neighbour differences take the hi parts exactly (neighbouring depths differ
+// by less than a factor of two) and add the lo parts.  The output is hi + lo
+// rounded once.  All arithmetic stays on the FP32 pipes.
 //
 // Two kernels share one per-pixel update (so their results are bit-identical):
 //  * k_diffuse_tiles: temporal blocking.  A CTA loads a (dx+2T) x (dy+2T) tile
@@ -24,8 +27,7 @@
 // J_q = I_p of the oracle (no flux across a hole or the border) without a
 // branch; a hole receives only zero fluxes and keeps its value.  The first
 // launch decodes the sensor encoding on the fly (holes -> HOLE); the last
-// writes FP32 depth (the hi part, which is hi + lo rounded to nearest; HOLE
-// -> 0).
+// writes FP32 depth (hi + lo rounded to nearest; HOLE -> 0).
 #include "pm_internal.cuh"
 
 namespace pm {
@@ -43,18 +45,10 @@ __device__ __forceinline__ float pair_diff(float2 q, float2 p)
     return __fadd_rn(__fsub_rn(q.x, p.x), __fsub_rn(q.y, p.y));
 }
 
-// (hi, lo) + a, renormalised.  The update is small next to the depth
-// (|a| <= lambda * 4 * max|g(x) x| = 0.86 K, a few mm, against depths of
-// decimetres and more), so Dekker's fast two-sum gives the exact rounding
-// error of hi + a; it is folded into lo and the pair renormalised so that
-// |lo| <= ulp(hi)/2.
+// (hi, lo) + a: the update goes to lo (hi is the fixed decoded depth).
 __device__ __forceinline__ float2 pair_add(float2 p, float a)
 {
-    const float s = __fadd_rn(p.x, a);
-    const float e = __fsub_rn(a, __fsub_rn(s, p.x));
-    const float l = __fadd_rn(p.y, e);
-    const float h2 = __fadd_rn(s, l);
-    return make_float2(h2, __fsub_rn(l, __fsub_rn(h2, s)));
+    return make_float2(p.x, __fadd_rn(p.y, a));
 }
 
 constexpr float HOLE = 1e30f;
@@ -130,7 +124,10 @@ __device__ __forceinline__ float2 load_px(const void *src, int dtype, long long 
     return make_float2((v > 0.0f && v < __int_as_float(0x7f800000)) ? v : HOLE, 0.0f);
 }
 
-__device__ __forceinline__ float depth_out(float2 v) { return v.x == HOLE ? 0.0f : v.x; }
+__device__ __forceinline__ float depth_out(float2 v)
+{
+    return v.x == HOLE ? 0.0f : __fadd_rn(v.x, v.y);
+}
 
 __device__ __forceinline__ void store_px(const DiffFrame &f, long long i, float2 v)
 {
