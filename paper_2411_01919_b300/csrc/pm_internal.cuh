@@ -129,19 +129,6 @@ __device__ __forceinline__ bool hyp_plane(float3 a, float3 b, float3 c, float4 &
     return true;
 }
 
-// Two IEEE fused multiply-adds in one instruction (sm_100+ packed FP32): each
-// lane is exactly fmaf(a, b, c).
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
-{
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
-
 // Residual r = fma(nz, pz, fma(ny, py, fma(nx, px, d))); inlier iff
 // fma(r, r, -thr2) < 0 (the square is exact inside the fused operation).
 __device__ __forceinline__ bool is_inlier(float4 pl, float px, float py, float pz, float thr2)
