@@ -39,6 +39,7 @@ FP32_FLOP_PER_PAIR = 8          # 3 FMA residual + 1 FMA squared-threshold test
 # of hypotheses fixed, traffic grows with the candidate count, i.e. with pairs.
 SCORE_DRAM_BYTES_PER_PAIR = (152.80e6 + 3.58e6) / 9.73e9   # ncu, k_score round 0, 32 frames
 SEGMENT, BOX_TEST_FLOP = 32, 12
+N_SETS = 4                      # device copies of the batch the timed steps cycle through
 REGION_FLOP_PER_PAIR = 9     # 3 FMA residual, |r| x 2^32, 1 FMA inlier test
 SM_COUNT, FP32_LANES = 148, 128
 
@@ -364,11 +365,16 @@ def run_served(torch, pm, args, c2_frames, c2_dev):
     srv.close()
     srv = Server(p, budget_bytes=4 << 30, max_batch=16, n_lanes=2, max_w=640, max_h=480)
     h2 = [torch.from_numpy(f.encoded).pin_memory() for f in c2_frames]
-    c2 = [Request(i % 16, i, 0.0, h2[i % len(h2)], c2_frames[0].cam.intrinsics, frame_idx=i)
-          for i in range(640)]
-    srv.run(c2[:64], realtime=False)
-    cap2 = srv.run(c2, realtime=False)
-    out['capacity_640x480'] = summarize(cap2, srv.elapsed)
+    def c2_reqs():
+        return [Request(i % 16, i, 0.0, h2[i % len(h2)], c2_frames[0].cam.intrinsics,
+                        frame_idx=i) for i in range(1280)]
+    srv.run(c2_reqs()[:128], realtime=False)                                  # warm-up
+    runs = []
+    for _ in range(3):                   # a short run is noisy: the median of three
+        cap2 = srv.run(c2_reqs(), realtime=False)
+        runs.append(summarize(cap2, srv.elapsed))
+    runs.sort(key=lambda r: r['frames_per_s'])
+    out['capacity_640x480'] = dict(runs[1], runs_frames_per_s=[r['frames_per_s'] for r in runs])
     srv.close()
     return out
 
@@ -400,38 +406,78 @@ def run_ours(args):
     pipe.set_timing(2)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     s = torch.cuda.current_stream()
+    # Whole-job throughput: two pipelines (lanes) on their own streams take
+    # the steps in turn through the asynchronous batch API, so the host
+    # prepares and submits step k+1 while step k runs.  The steps cycle through
+    # N_SETS device copies of the batch (N_SETS x 39 MB > the 126 MB L2), so no
+    # step finds its input in L2.
+    pipe_b = pm.Pipeline(params, 640, 480, B)
+    if tuned:
+        pipe_b.set_tiling(*tuned['best'])
+    pipe_b.set_timing(2)
+    lanes = [(pipe, torch.cuda.Stream()), (pipe_b, torch.cuda.Stream())]
+    sets = [dframes] + [[d.clone() for d in dframes] for _ in range(N_SETS - 1)]
 
     def batch(step):
-        return [dict(depth=dframes[i], K=K, frame_idx=step * B + i) for i in range(B)]
+        src = sets[step % N_SETS]
+        return [dict(depth=src[i], K=K, frame_idx=step * B + i) for i in range(B)]
 
     for w in range(args.warmup):
-        pipe.process_batch(batch(w), use_graph=True)
+        for lp, ls in lanes:
+            with torch.cuda.stream(ls):
+                lp.process_batch(batch(w), use_graph=True, stream=ls)
     torch.cuda.synchronize()
     clocks = Clocks(local)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     step_ms, score_ms, score_pairs, eval_pairs, launches = [], 0.0, 0, 0, 0
-    torch.cuda.nvtx.range_push('timed')
-    for k in range(args.steps):
-        flush.fill_(float(k))                      # evict L2 between steps
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(s)
-        pipe.process_batch(batch(args.warmup + k), use_graph=True)
-        b.record(s)
-        b.synchronize()
-        step_ms.append(a.elapsed_time(b))
-        st = pipe.kernel_stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    done = [None, None]
+    t_sub = [0.0, 0.0]
+
+    def finish(li):
+        lp, _ = lanes[li]
+        nonlocal score_ms, score_pairs, eval_pairs, launches
+        done[li].synchronize()
+        lp.collect_batch()
+        step_ms.append(1e3 * (time.perf_counter() - t_sub[li]))
+        st = lp.kernel_stats()
         score_ms += st['score_ms']
         score_pairs += st['score_pairs']
         eval_pairs += st['evaluated_pairs']
         launches += st['launches']
+        done[li] = None
+
+    torch.cuda.nvtx.range_push('timed')
+    e0.record(s)
+    for _, ls in lanes:
+        ls.wait_event(e0)
+    for k in range(args.steps):
+        li = k % 2
+        lp, ls = lanes[li]
+        if done[li] is not None:
+            finish(li)
+        t_sub[li] = time.perf_counter()
+        with torch.cuda.stream(ls):
+            lp.submit_batch(batch(args.warmup + k), use_graph=True, stream=ls)
+        ev = torch.cuda.Event()
+        ev.record(ls)
+        done[li] = ev
+    for li in range(2):
+        if done[li] is not None:
+            s.wait_event(done[li])
+    e1.record(s)
+    for li in range(2):
+        if done[li] is not None:
+            finish(li)
+    e1.synchronize()
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    tot_ms = max_over_ranks(sum(step_ms), device=dev)
+    tot_ms = max_over_ranks(e0.elapsed_time(e1), device=dev)
     value = world * B * args.steps / (tot_ms * 1e-3)
 
     # plain per-frame path: pm_process_frame, synchronised per frame
@@ -457,27 +503,48 @@ def run_ours(args):
              'stage_ms_median': {k: statistics.median(x[k] for x in stage) for k in stage[0]}}
     pipe1.close()
 
-    # end to end: pinned host depth -> device, batch, planes back to host
+    # end to end: pinned host depth -> device, batch, planes back to host, the
+    # same two lanes in turn (a lane's copies run on its stream, so they
+    # overlap the other lane's batch)
     host = [torch.from_numpy(f.encoded).pin_memory() for f in frames]
-    dbuf = [torch.empty_like(d) for d in dframes]
-    e2e_ms = []
-    for k in range(max(2, args.steps // 2) + 1):
-        flush.fill_(float(k))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(s)
-        for i in range(B):
-            dbuf[i].copy_(host[i], non_blocking=True)
-        pipe.process_batch([dict(depth=dbuf[i], K=K, frame_idx=i) for i in range(B)],
-                           use_graph=True)
-        b.record(s)
-        b.synchronize()
-        if k > 0:
-            e2e_ms.append(a.elapsed_time(b))
+    dbuf = [[torch.empty_like(d) for d in dframes] for _ in lanes]
+    ne = max(4, args.steps // 2)
+    for lp, _ in lanes:
+        lp.set_timing(0)
+    pend = [None, None]
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    f0.record(s)
+    for _, ls in lanes:
+        ls.wait_event(f0)
+    for k in range(ne):
+        li = k % 2
+        lp, ls = lanes[li]
+        if pend[li] is not None:
+            pend[li].synchronize()
+            lp.collect_batch()
+        with torch.cuda.stream(ls):
+            for i in range(B):
+                dbuf[li][i].copy_(host[i], non_blocking=True)
+            lp.submit_batch([dict(depth=dbuf[li][i], K=K, frame_idx=i) for i in range(B)],
+                            use_graph=True, stream=ls)
+        ev = torch.cuda.Event()
+        ev.record(ls)
+        pend[li] = ev
+    for li in range(2):
+        if pend[li] is not None:
+            s.wait_event(pend[li])
+    f1.record(s)
+    for li, (lp, _) in enumerate(lanes):
+        if pend[li] is not None:
+            pend[li].synchronize()
+            lp.collect_batch()
+    f1.synchronize()
     h2d = sum(h.numel() * h.element_size() for h in host)
     d2h = B * (64 * 48 + 352)   # planes + per-frame state read back by the call
-    e2e = {'value': B / (statistics.mean(e2e_ms) * 1e-3), 'unit': 'frames/s',
+    e2e = {'value': B * ne / (f0.elapsed_time(f1) * 1e-3), 'unit': 'frames/s',
            'h2d_bytes_per_step': h2d, 'd2h_bytes_per_step': d2h,
-           'api': 'pm_process_batch after pinned-host copies'}
+           'api': 'pinned-host copies + pm_process_batch_async / pm_batch_collect, two lanes'}
 
     # roofline: the scoring kernel (FP32 ALU bound).  Executed work = the
     # pairs it evaluates (8 FLOP each) + one box test per hypothesis and
@@ -525,13 +592,18 @@ def run_ours(args):
             'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': tot_ms / args.steps,
             'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32',
             'data': 'synthetic',
-            'config': {'workload': WORKLOAD, 'batch_per_gpu': B, 'form': 'batched, CUDA graph',
-                       'l2': 'flushed between steps (256 MB write, untimed)',
+            'config': {'workload': WORKLOAD, 'batch_per_gpu': B,
+                       'form': 'batched, CUDA graph; two lanes take the steps in turn through '
+                               'the asynchronous batch API',
+                       'l2': 'steps cycle through %d device copies of the batch (%.0f MB > 126 MB '
+                             'L2)' % (N_SETS, N_SETS * sum(d.numel() * d.element_size()
+                                                           for d in dframes) / 1e6),
                        'parallelism': 'frames sharded across GPUs, no collective',
                        'diffusion_tiling': (dict(zip(('iters_per_launch', 'tile_w', 'tile_h'),
                                                      tuned['best'])) if tuned else 'library default')},
             'latency_ms': {'p50': percentile(step_ms, 50), 'p99': percentile(step_ms, 99),
-                           'note': 'a batched frame completes with its step'},
+                           'note': 'submit to collect of a step (two steps in flight); a batched '
+                                   'frame completes with its step'},
             'plain': plain, 'speedup_vs_plain': value / world / plain['value'],
             'served': served, 'regions': regions, 'sweep': sweep,
             'e2e': e2e, 'roofline': roof, 'diffusion_hbm': hbm, 'cpu_baseline': cpu,
@@ -541,6 +613,7 @@ def run_ours(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     pipe.close()
+    pipe_b.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
