@@ -406,16 +406,20 @@ def run_ours(args):
     pipe.set_timing(2)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     s = torch.cuda.current_stream()
-    # Whole-job throughput: two pipelines (lanes) on their own streams take
-    # the steps in turn through the asynchronous batch API, so the host
-    # prepares and submits step k+1 while step k runs.  The steps cycle through
+    # Whole-job throughput: --lanes pipelines on their own streams take the
+    # steps in turn through the asynchronous batch API, so the host prepares
+    # and submits the next steps while earlier ones run and their kernels
+    # share the GPU.  The steps cycle through
     # N_SETS device copies of the batch (N_SETS x 39 MB > the 126 MB L2), so no
     # step finds its input in L2.
-    pipe_b = pm.Pipeline(params, 640, 480, B)
-    if tuned:
-        pipe_b.set_tiling(*tuned['best'])
-    pipe_b.set_timing(2)
-    lanes = [(pipe, torch.cuda.Stream()), (pipe_b, torch.cuda.Stream())]
+    lanes = [(pipe, torch.cuda.Stream())]
+    for _ in range(args.lanes - 1):
+        extra = pm.Pipeline(params, 640, 480, B)
+        if tuned:
+            extra.set_tiling(*tuned['best'])
+        extra.set_timing(2)
+        lanes.append((extra, torch.cuda.Stream()))
+    NL = len(lanes)
     sets = [dframes] + [[d.clone() for d in dframes] for _ in range(N_SETS - 1)]
 
     def batch(step):
@@ -433,8 +437,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     step_ms, score_ms, score_pairs, eval_pairs, launches = [], 0.0, 0, 0, 0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    done = [None, None]
-    t_sub = [0.0, 0.0]
+    done = [None] * NL
+    t_sub = [0.0] * NL
 
     def finish(li):
         lp, _ = lanes[li]
@@ -454,7 +458,7 @@ def run_ours(args):
     for _, ls in lanes:
         ls.wait_event(e0)
     for k in range(args.steps):
-        li = k % 2
+        li = k % NL
         lp, ls = lanes[li]
         if done[li] is not None:
             finish(li)
@@ -464,11 +468,11 @@ def run_ours(args):
         ev = torch.cuda.Event()
         ev.record(ls)
         done[li] = ev
-    for li in range(2):
+    for li in range(NL):
         if done[li] is not None:
             s.wait_event(done[li])
     e1.record(s)
-    for li in range(2):
+    for li in range(NL):
         if done[li] is not None:
             finish(li)
     e1.synchronize()
@@ -504,21 +508,21 @@ def run_ours(args):
     pipe1.close()
 
     # end to end: pinned host depth -> device, batch, planes back to host, the
-    # same two lanes in turn (a lane's copies run on its stream, so they
-    # overlap the other lane's batch)
+    # same lanes in turn (a lane's copies run on its stream, so they overlap
+    # the other lanes' batches)
     host = [torch.from_numpy(f.encoded).pin_memory() for f in frames]
     dbuf = [[torch.empty_like(d) for d in dframes] for _ in lanes]
     ne = max(4, args.steps // 2)
     for lp, _ in lanes:
         lp.set_timing(0)
-    pend = [None, None]
+    pend = [None] * NL
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     f0.record(s)
     for _, ls in lanes:
         ls.wait_event(f0)
     for k in range(ne):
-        li = k % 2
+        li = k % NL
         lp, ls = lanes[li]
         if pend[li] is not None:
             pend[li].synchronize()
@@ -531,7 +535,7 @@ def run_ours(args):
         ev = torch.cuda.Event()
         ev.record(ls)
         pend[li] = ev
-    for li in range(2):
+    for li in range(NL):
         if pend[li] is not None:
             s.wait_event(pend[li])
     f1.record(s)
@@ -544,7 +548,7 @@ def run_ours(args):
     d2h = B * (64 * 48 + 352)   # planes + per-frame state read back by the call
     e2e = {'value': B * ne / (f0.elapsed_time(f1) * 1e-3), 'unit': 'frames/s',
            'h2d_bytes_per_step': h2d, 'd2h_bytes_per_step': d2h,
-           'api': 'pinned-host copies + pm_process_batch_async / pm_batch_collect, two lanes'}
+           'api': 'pinned-host copies + pm_process_batch_async / pm_batch_collect, %d lanes' % NL}
 
     # roofline: the scoring kernel (FP32 ALU bound).  Executed work = the
     # pairs it evaluates (8 FLOP each) + one box test per hypothesis and
@@ -593,8 +597,8 @@ def run_ours(args):
             'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32',
             'data': 'synthetic',
             'config': {'workload': WORKLOAD, 'batch_per_gpu': B,
-                       'form': 'batched, CUDA graph; two lanes take the steps in turn through '
-                               'the asynchronous batch API',
+                       'form': 'batched, CUDA graph; %d lanes take the steps in turn through '
+                               'the asynchronous batch API' % NL,
                        'l2': 'steps cycle through %d device copies of the batch (%.0f MB > 126 MB '
                              'L2)' % (N_SETS, N_SETS * sum(d.numel() * d.element_size()
                                                            for d in dframes) / 1e6),
@@ -602,8 +606,8 @@ def run_ours(args):
                        'diffusion_tiling': (dict(zip(('iters_per_launch', 'tile_w', 'tile_h'),
                                                      tuned['best'])) if tuned else 'library default')},
             'latency_ms': {'p50': percentile(step_ms, 50), 'p99': percentile(step_ms, 99),
-                           'note': 'submit to collect of a step (two steps in flight); a batched '
-                                   'frame completes with its step'},
+                           'note': 'submit to collect of a step (%d steps in flight); a batched '
+                                   'frame completes with its step' % NL},
             'plain': plain, 'speedup_vs_plain': value / world / plain['value'],
             'served': served, 'regions': regions, 'sweep': sweep,
             'e2e': e2e, 'roofline': roof, 'diffusion_hbm': hbm, 'cpu_baseline': cpu,
@@ -613,7 +617,8 @@ def run_ours(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     pipe.close()
-    pipe_b.close()
+    for lp, _ in lanes[1:]:
+        lp.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -631,6 +636,8 @@ def main():
     ap.add_argument('--skip-hbm', action='store_true')
     ap.add_argument('--skip-regions', action='store_true')
     ap.add_argument('--skip-sweep', action='store_true')
+    ap.add_argument('--lanes', type=int, default=3,
+                    help='pipelines taking the timed batches in turn (batches in flight)')
     ap.add_argument('--no-tune', action='store_true')
     ap.add_argument('--served-seconds', type=float, default=60.0)
     args = ap.parse_args()
