@@ -38,7 +38,7 @@ FP32_FLOP_PER_PAIR = 8          # 3 FMA residual + 1 FMA squared-threshold test
 # of 32 frames of this workload: 156.4 MB for 9.73e9 pairs.  With the number
 # of hypotheses fixed, traffic grows with the candidate count, i.e. with pairs.
 SCORE_DRAM_BYTES_PER_PAIR = (152.80e6 + 3.58e6) / 9.73e9   # ncu, k_score round 0, 32 frames
-SEGMENT, BOX_TEST_FLOP = 32, 12
+SEGMENT, BOX_TEST_FLOP = 32, 14   # box test: 6 FFMA + 2 FADD
 N_SETS = 4                      # device copies of the batch the timed steps cycle through
 REGION_FLOP_PER_PAIR = 9     # 3 FMA residual, |r| x 2^32, 1 FMA inlier test
 SM_COUNT, FP32_LANES = 148, 128
@@ -550,17 +550,19 @@ def run_ours(args):
            'h2d_bytes_per_step': h2d, 'd2h_bytes_per_step': d2h,
            'api': 'pinned-host copies + pm_process_batch_async / pm_batch_collect, %d lanes' % NL}
 
-    # roofline: the scoring kernel (FP32 ALU bound).  Executed work = the
-    # pairs it evaluates (8 FLOP each) + one box test per hypothesis and
-    # 32-candidate segment (12 FLOP); the pairs the box test skips are exact
-    # zeros and count only in the effective rate.
+    # roofline: the scoring kernel (FP32 ALU bound).  Algorithmic work = every
+    # hypothesis against every candidate, 8 FLOP per pair (3 FFMA for the
+    # residual, the test and the count).  Executed work = the pairs the kernel
+    # evaluates + one box test per hypothesis and 32-candidate segment
+    # (14 FLOP); a box test settles the other pairs of its segment exactly
+    # (all outside the threshold, or all inside).
     n_score = args.steps * MAXP
     clock_mhz = pk.get('sm_max_mhz', 2032.0)
     peak_tflops = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
     tests = score_pairs / SEGMENT
-    flop = eval_pairs * FP32_FLOP_PER_PAIR + tests * BOX_TEST_FLOP
-    ach = flop / (score_ms * 1e-3) / 1e12 if score_ms > 0 else 0.0
-    eff = score_pairs * FP32_FLOP_PER_PAIR / (score_ms * 1e-3) / 1e12 if score_ms > 0 else 0.0
+    flop_exec = eval_pairs * FP32_FLOP_PER_PAIR + tests * BOX_TEST_FLOP
+    ach = score_pairs * FP32_FLOP_PER_PAIR / (score_ms * 1e-3) / 1e12 if score_ms > 0 else 0.0
+    exe = flop_exec / (score_ms * 1e-3) / 1e12 if score_ms > 0 else 0.0
     roof = {'kernel': 'k_score', 'bound': 'alu', 'achieved': ach, 'peak': peak_tflops,
             'unit': 'TFLOP/s', 'frac': ach / peak_tflops,
             'traffic': (SCORE_DRAM_BYTES_PER_PAIR * score_pairs / n_score
@@ -570,13 +572,16 @@ def run_ours(args):
                             'hypothesis block',
             'peak_source': 'derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (%s peaks file)'
                            % (SM_COUNT, FP32_LANES, clock_mhz, pk_kind),
-            'work': '%d FLOP per evaluated hypothesis-candidate pair + %d FLOP per box test '
-                    '(hypothesis x %d-candidate segment); %.3e of %.3e pairs evaluated '
-                    '(%.1f%%) over %d launches'
-                    % (FP32_FLOP_PER_PAIR, BOX_TEST_FLOP, SEGMENT, eval_pairs, score_pairs,
-                       100.0 * eval_pairs / max(1, score_pairs), n_score),
-            'effective': {'achieved': eff, 'frac': eff / peak_tflops,
-                          'note': 'all H x M pairs x 8 FLOP / time, skipped pairs included'},
+            'work': 'algorithmic: %d FLOP per hypothesis-candidate pair, %.3e pairs over %d '
+                    'launches (H x M per frame and round)'
+                    % (FP32_FLOP_PER_PAIR, score_pairs, n_score),
+            'executed': {'achieved': exe, 'frac': exe / peak_tflops,
+                         'note': '%d FLOP per evaluated pair + %d FLOP per box test (hypothesis x '
+                                 '%d-candidate segment); %.3e of the pairs evaluated (%.1f%%), '
+                                 'the rest settled by the box test (segment proven free of '
+                                 'inliers, or all inliers)'
+                                 % (FP32_FLOP_PER_PAIR, BOX_TEST_FLOP, SEGMENT, eval_pairs,
+                                    100.0 * eval_pairs / max(1, score_pairs))},
             'kernel_ms_per_step': score_ms / args.steps,
             'share_of_step': (score_ms / args.steps) / (tot_ms / args.steps) if world == 1 else None}
 

@@ -353,6 +353,7 @@ RParams ransac_params(const pm_ctx *ctx)
     p.seed = ctx->rp.seed;
     p.cos_gate = (float)std::cos((double)ctx->rp.refit_normal_gate_deg * M_PI / 180.0);
     p.cull_thr = std::nextafter((float)(std::sqrt((double)p.thr2) * (1.0 + 0x1p-20)), INFINITY);
+    p.incl_thr = std::nextafter((float)(std::sqrt((double)p.thr2) * (1.0 - 0x1p-20)), 0.0f);
     return p;
 }
 

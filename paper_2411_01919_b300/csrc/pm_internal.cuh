@@ -95,7 +95,8 @@ struct RParams {
     int min_inliers;
     unsigned long long seed;
     float cos_gate;
-    float cull_thr;      // >= sqrt(thr2) (1 + 2^-20): threshold of the scoring box test
+    float cull_thr;      // >= sqrt(thr2) (1 + 2^-20): box test, no inlier beyond it
+    float incl_thr;      // <= sqrt(thr2) (1 - 2^-20): box test, every point inlier below it
 };
 
 // ---------------------------------------------------------------------------

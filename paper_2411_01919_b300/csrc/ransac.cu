@@ -401,7 +401,7 @@ __device__ void select_winner(const RFrame &F, const RParams &prm)
 }
 
 // ---------------------------------------------------------------------------
-// scoring with exact box culling.
+// scoring with exact box culling and inclusion.
 //
 // A work item is (frame, chunk of CHUNK candidates, block of HB hypotheses).
 // The chunk is cut into segments of SEG consecutive candidates (a few pixels
@@ -409,26 +409,39 @@ __device__ void select_winner(const RFrame &F, const RParams &prm)
 // axis-aligned box [c - e, c + e] that holds its points.  A hypothesis whose
 // plane stays farther than the threshold from the whole box, by a margin that
 // covers every rounding of the FP32 residual and of the test, has no inlier
-// in the segment: its count there is exactly 0 and the pair is not
-// evaluated.  The counts, and every decision taken from them, are the ones of
-// evaluating all pairs.
+// in the segment: its count there is exactly 0.  A hypothesis whose slab
+// holds the whole box, by the same margin, has every point of the segment as
+// an inlier: its count there is exactly the segment's size.  Neither kind of
+// pair is evaluated; the counts, and every decision taken from them, are the
+// ones of evaluating all pairs.
 //
-// The margin.  u = 2^-24.  The residual r~ = fma(nz,pz,fma(ny,py,fma(nx,px,d)))
-// is within 3.0000004 u B of n.p + d, B = |n|.|p| + |d| <= |n|.(|c| + e) + |d|.
-// A hypothesis is culled when, in FP32,
-//     |n.c + d|  >  |n|.g + w,   g = e + s (|c| + e),  w = thr' + s |d|,
-// with s = 2^-18 (64 u), thr' >= sqrt(thr2) (1 + 2^-20), and g, w rounded up.
-// Following the roundings through (each FP32 step of the test is off by at
-// most a few u), every point of the box then has |r~| > sqrt(thr2), so
-// fma(r~, r~, -thr2) >= 0: not an inlier.  A NaN anywhere keeps the pair.
+// The margin.  u = 2^-24, s = 2^-18 (64 u), T = sqrt(thr2) (real).  The
+// residual r~ = fma(nz,pz,fma(ny,py,fma(nx,px,d))) of a point p of the box is
+// within 3.0000004 u (|n|.|p| + |d|) of n.p + d, and |p_k| <= |c_k| + e_k.
+// The box test computes, each step rounded to nearest,
+//     t~ = fma(nz,cz,fma(ny,cy,fma(nx,cx,d))),
+//     A~ = fma(|nz|,gz,fma(|ny|,gy,fma(|nx|,gx,s|d|))),
+// with g_k = e_k + s (|c_k| + e_k) and s|d| rounded up.  t~ is within
+// 3.0000004 u (|n|.|c| + |d|) of n.c + d; the slack s in g and s|d| covers
+// both residual errors and the three roundings of A~ (all terms >= 0), so
+//     | |r~| - |t~| |  <=  |n|.e + 6.000001 u (|n|.(|c| + e) + |d|)  <=  A~
+// for every point of the box.  Rounding is monotone and the thresholds are
+// FP32 numbers, so
+//     fl(|t~| - A~) > thr_c   gives  |r~| > thr_c >= T:  r~ r~ - thr2 > 0;
+//     fl(|t~| + A~) < thr_i   gives  |r~| < thr_i <= T:  r~ r~ - thr2 < 0;
+// with thr_c >= T (1 + 2^-20) and thr_i <= T (1 - 2^-20) from the host.  A
+// degenerate hypothesis (n = 0, d = +inf) has t~ = inf, A~ = 0: culled.  A
+// NaN anywhere keeps the pair for evaluation.
 //
-// Per segment a warp tests all HB hypotheses (one per lane, ballot) into a
-// list of survivors, then scores the list up to four hypotheses per lane
-// against the segment's points (broadcast 16-byte loads from shared memory).  Per pair:
-// three residual FMAs, one FMA for r*r - thr2 and one integer add of its sign
-// bit, which is set iff it is negative (an exact zero rounds to +0): the
-// decision of is_inlier().  Counts go to shared memory, then once per work
-// item to global memory.
+// Per segment a warp tests all HB hypotheses (one per lane): included ones
+// add the segment's size to their shared-memory count, the rest that the
+// cull does not prove empty go to a list of survivors (ballot), which is
+// scored up to four hypotheses per lane against the segment's points
+// (broadcast 16-byte loads from shared memory).  Per pair: three residual
+// FMAs, one FMA for r*r - thr2 and one integer add of its sign bit, which is
+// set iff it is negative (an exact zero rounds to +0): the decision of
+// is_inlier().  Counts go to shared memory, then once per work item to
+// global memory.
 // ---------------------------------------------------------------------------
 constexpr int SEG = 32;
 constexpr int NSEG = CHUNK / SEG;
@@ -511,8 +524,8 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
     float4 *pts = sm;                  // [CHUNK] candidates of the chunk
     float4 *hpl = pts + CHUNK;         // [HB] planes (nx, ny, nz, d)
     float4 *box = hpl + HB;            // [NSEG][2] centre c; widened half-size g
-    float *hw = reinterpret_cast<float *>(box + 2 * NSEG);               // [HB] w
-    int *hcnt = reinterpret_cast<int *>(hw + HB);                        // [HB]
+    float *hsd = reinterpret_cast<float *>(box + 2 * NSEG);              // [HB] s |d|
+    int *hcnt = reinterpret_cast<int *>(hsd + HB);                       // [HB]
     unsigned short *lst = reinterpret_cast<unsigned short *>(hcnt + HB);  // [warps][HB]
     __shared__ int next_seg;
     __shared__ unsigned long long evaluated;
@@ -522,6 +535,7 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const float nthr2 = -prm.thr2;
+    const float cull_thr = prm.cull_thr, incl_thr = prm.incl_thr;
     unsigned short *my = lst + wid * HB;
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
         const int wi = it / per_chunk;
@@ -542,16 +556,16 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
             const int nh = min(HB, prm.H - h0);
             for (int k = threadIdx.x; k < HB; k += SCORE_THREADS) {
                 float4 pl = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
-                float w = -1.0f;                     // culls everywhere
+                float sd = 0.0f;                     // n = 0, d = inf: culled everywhere
                 if (k < nh) {
                     const float4 q = F.hyp[h0 + k];
                     if (fabsf(q.w) <= 3.0e38f) {     // degenerate planes carry d = +inf
                         pl = q;
-                        w = __fmaf_ru(CULL_SLACK, fabsf(q.w), prm.cull_thr);
+                        sd = __fmul_ru(CULL_SLACK, fabsf(q.w));
                     }
                 }
                 hpl[k] = pl;
-                hw[k] = w;
+                hsd[k] = sd;
                 hcnt[k] = 0;
             }
             if (threadIdx.x == 0) {
@@ -597,23 +611,27 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
                 if (sg >= nseg)
                     break;
                 const float4 bc = box[2 * sg], bg = box[2 * sg + 1];
+                const int sc = min(SEG, cnt - sg * SEG);
                 int len = 0;
                 for (int k = lane; k < nh + ((32 - (nh & 31)) & 31); k += 32) {
                     const float4 pl = hpl[k];
                     float t = __fmaf_rn(pl.x, bc.x, pl.w);
                     t = __fmaf_rn(pl.y, bc.y, t);
                     t = __fmaf_rn(pl.z, bc.z, t);
-                    float lim = __fmaf_rn(fabsf(pl.x), bg.x, hw[k]);
-                    lim = __fmaf_rn(fabsf(pl.y), bg.y, lim);
-                    lim = __fmaf_rn(fabsf(pl.z), bg.z, lim);
-                    const bool keep = !(fabsf(t) > lim);
+                    float a = __fmaf_rn(fabsf(pl.x), bg.x, hsd[k]);
+                    a = __fmaf_rn(fabsf(pl.y), bg.y, a);
+                    a = __fmaf_rn(fabsf(pl.z), bg.z, a);
+                    const float at = fabsf(t);
+                    const bool inc = __fadd_rn(at, a) < incl_thr;
+                    if (inc)
+                        atomicAdd(hcnt + k, sc);
+                    const bool keep = !inc && !(__fsub_rn(at, a) > cull_thr);
                     const unsigned m = __ballot_sync(0xffffffffu, keep);
                     if (keep)
                         my[len + __popc(m & lt)] = (unsigned short)k;
                     len += __popc(m);
                 }
                 __syncwarp();
-                const int sc = min(SEG, cnt - sg * SEG);
                 mine += (unsigned long long)len * (unsigned)sc;
                 if (sc == SEG)
                     score_list<true>(hpl, my, len, pts + sg * SEG, sc, nthr2, hcnt, lane);

@@ -306,6 +306,34 @@ def test_box_culling_keeps_threshold_inliers(z0, half_w):
     assert orc.band[0] > 0
 
 
+@pytest.mark.parametrize('z0,w,h', [(1.25, 61, 37), (7.0, 100, 41)])
+def test_box_inclusion_counts_whole_segments(z0, w, h):
+    """Every point on the plane z = z0, a candidate count that is not a
+    multiple of the 32-point segment: every hypothesis through three
+    non-collinear points is the plane itself, its slab holds every segment's
+    box, and the scoring kernel adds whole (and the ragged last) segments
+    without evaluating a pair.  Counts, winner and labels equal the oracle's."""
+    xs = np.linspace(-0.4, 0.4, w)
+    ys = np.linspace(-0.3, 0.3, h)
+    X, Y = np.meshgrid(xs, ys)
+    P = np.stack([X, Y, np.full((h, w), z0)]).astype(np.float32)
+    V = np.ones((h, w), dtype=np.uint8)
+    p = Params(iters=0, hypotheses=256, thr=0.01, max_planes=2, min_inliers=50, seed=9)
+    orc = oracle.ransac(P, None, V, p.hypotheses, p.thr, p.max_planes, p.min_inliers, p.seed,
+                        p.gate_deg, 0)
+    with Pipeline(p, w, h) as pipe:
+        pipe.set_timing(2)
+        g = pipe.ransac_planes(to_dev(P), None, to_dev(V), frame_idx=0)
+        lab = g.labels.cpu().numpy()
+        st = pipe.kernel_stats()
+    assert (w * h) % 32 != 0
+    assert np.array_equal(g.hyp_index, orc.hyp_index)
+    assert np.array_equal(g.n_inliers, orc.n_inliers) and g.n_inliers[0] == w * h
+    assert np.array_equal(lab, orc.labels)
+    assert st['score_pairs'] >= p.hypotheses * w * h
+    assert st['evaluated_pairs'] == 0
+
+
 # ---------------------------------------------------------------------------
 # the whole path
 # ---------------------------------------------------------------------------
