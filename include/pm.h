@@ -61,7 +61,7 @@ typedef struct {
  * lambda (Alg. 1's gamma) must lie in (0, 0.25] (stability of the explicit
  * scheme); K (Alg. 1's k) is in metres.  iters_per_launch is the temporal
  * blocking depth (iterations fused in one launch, 1..8); tile_w x tile_h is
- * the output tile of one CTA of the fused kernel (tile_w + 2*8 <= 96,
+ * the output tile of one CTA of the fused kernel (tile_w + 2*8 <= 144,
  * tile_h + 2*8 <= 64).  0 lets the library choose any of the three.  None of
  * them changes the result: every choice is bit-identical. */
 typedef struct {

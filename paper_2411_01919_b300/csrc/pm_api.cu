@@ -155,7 +155,7 @@ pm_status check_params(const pm_diffusion_params *dp, const pm_ransac_params *rp
         return fail(PM_ERR_ARG, "iters_per_launch must lie in [0, 8]");
     if (dp->tile_w < 0 || dp->tile_h < 0 || dp->tile_w + 2 * DT_MAX > TILE_MAX_DX ||
         dp->tile_h + 2 * DT_MAX > TILE_MAX_DY)
-        return fail(PM_ERR_ARG, "tile_w must lie in [0, 80] and tile_h in [0, 48]");
+        return fail(PM_ERR_ARG, "tile_w must lie in [0, 128] and tile_h in [0, 48]");
     if (rp->hypotheses < 1 || rp->hypotheses > MAX_HYP)
         return fail(PM_ERR_ARG, "hypotheses must lie in [1, 2048]");
     if (!(rp->thr_m > 0.0f) || !std::isfinite(rp->thr_m))

@@ -26,7 +26,7 @@ constexpr int PART_WORDS = 40;
 
 // Diffusion tiles (temporal blocking): output tile dx x dy chosen per launch
 // (at most TILE_MAX_DX x TILE_MAX_DY), halo T <= DT_MAX
-constexpr int TILE_MAX_DX = 96;
+constexpr int TILE_MAX_DX = 144;
 constexpr int TILE_MAX_DY = 64;
 constexpr int DT_MAX = 8;
 

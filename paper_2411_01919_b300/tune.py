@@ -18,8 +18,13 @@ from typing import Dict, List, Sequence, Tuple
 import torch
 
 # (iterations per launch, tile_w, tile_h)
+# The fused kernel computes, at iteration it of T, a region tile_w + 2 (T - it - 1)
+# columns wide in groups of 32 lanes; widths tile_w = 32 k - 2 (T - 1) fill every
+# group at the first iteration.
 CANDIDATES: List[Tuple[int, int, int]] = [
     (T, tw, th) for T in (4, 6, 8) for (tw, th) in ((48, 24), (64, 32), (80, 48), (64, 48))
+] + [
+    (T, 32 * k - 2 * (T - 1), th) for T in (4, 6) for k in (2, 3, 4) for th in (24, 32)
 ]
 
 

@@ -128,7 +128,8 @@ def test_temporal_blocking_is_bit_exact(mode):
     fr = frame('c2')
     outs = []
     for T, tw, th in ((1, 0, 0), (2, 0, 0), (3, 0, 0), (5, 0, 0), (8, 0, 0), (8, 80, 48),
-                      (8, 48, 24), (7, 17, 9), (4, 64, 1), (8, 1, 48), (6, 33, 40)):
+                      (8, 48, 24), (7, 17, 9), (4, 64, 1), (8, 1, 48), (6, 33, 40),
+                      (4, 122, 32), (8, 128, 48)):
         p = params('c2', mode=mode, iters_per_launch=T, tile_w=tw, tile_h=th)
         with Pipeline(p, fr.w, fr.h) as pipe:
             outs.append(pipe.diffuse(to_dev(fr.encoded)).cpu().numpy())
