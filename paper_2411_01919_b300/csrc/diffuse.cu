@@ -176,14 +176,64 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
     float2 *B = sm2 + SX * SY;
     const int lane = threadIdx.x, wy = threadIdx.y;
 
-    for (int y = wy; y < SY; y += 8) {
-        const int gy = ty0 - T + y;
-        for (int x = lane; x < SX; x += 32) {
-            const int gx = tx0 - T + x;
-            float2 v = make_float2(HOLE, 0.0f);
-            if (gx >= 0 && gx < f.w && gy >= 0 && gy < f.h)
-                v = load_px(f.src, f.src_dtype, f.src_pitch, gx, gy, f.scale);
-            A[y * SX + x] = v;
+    if (f.src_dtype == SRC_PAIR || f.src_dtype == PM_U16_MM) {
+        // the iterate of the previous launch, or the u16 encoding (decoded on
+        // the store): per warp two rows of 96 cells in flight before any
+        // shared-memory store
+        constexpr int G = 3;
+        const bool pair = f.src_dtype == SRC_PAIR;
+        const float2 hole = make_float2(HOLE, 0.0f);
+        for (int y0 = wy; y0 < SY; y0 += 16) {
+            for (int x0 = 0; x0 < SX; x0 += 32 * G) {
+                float2 v[2][G];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int y = y0 + 8 * r, gy = ty0 - T + y;
+                    const bool row_ok = y < SY && gy >= 0 && gy < f.h;
+                    const char *row = (const char *)f.src + (long long)(row_ok ? gy : 0) * f.src_pitch;
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const int x = x0 + lane + 32 * g, gx = tx0 - T + x;
+                        const bool ok = row_ok && x < SX && gx >= 0 && gx < f.w;
+                        if (pair) {
+                            v[r][g] = ok ? __ldg(reinterpret_cast<const float2 *>(row) + gx) : hole;
+                        } else {
+                            const unsigned short q =
+                                ok ? __ldg(reinterpret_cast<const unsigned short *>(row) + gx) : 0;
+                            v[r][g].x = __int_as_float((int)q);   // the raw code, decoded below
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int y = y0 + 8 * r;
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const int x = x0 + lane + 32 * g;
+                        if (y < SY && x < SX) {
+                            float2 w = v[r][g];
+                            if (!pair) {
+                                const int q = __float_as_int(w.x);
+                                const float qf = (float)q;
+                                const float h = __fmul_rn(qf, f.scale);
+                                w = q ? make_float2(h, __fmaf_rn(qf, f.scale, -h)) : hole;
+                            }
+                            A[y * SX + x] = w;
+                        }
+                    }
+                }
+            }
+        }
+    } else {
+        for (int y = wy; y < SY; y += 8) {
+            const int gy = ty0 - T + y;
+            for (int x = lane; x < SX; x += 32) {
+                const int gx = tx0 - T + x;
+                float2 v = make_float2(HOLE, 0.0f);
+                if (gx >= 0 && gx < f.w && gy >= 0 && gy < f.h)
+                    v = load_px(f.src, f.src_dtype, f.src_pitch, gx, gy, f.scale);
+                A[y * SX + x] = v;
+            }
         }
     }
     __syncthreads();
