@@ -146,9 +146,9 @@ __device__ __forceinline__ float2 pm4_combine(float2 Ip, float fN, float fS, flo
 }
 
 // Temporal blocking.  Block = 32 x 8 threads; tile = dx x dy output pixels
-// with a T-pixel halo, (dx + 2T) x (dy + 2T) float2 cells in shared memory,
-// two buffers.  Iteration it updates the region shrunk by it + 1 on every
-// side.  Each warp (one threadIdx.y) walks a band of rows top to bottom for
+// with a T-pixel halo, (dx + 2T) x (dy + 2T) cells in shared memory: the hi
+// parts once (they never change), the lo parts in two buffers (12 bytes per
+// cell).  Iteration it updates the region shrunk by it + 1 on every side.  Each warp (one threadIdx.y) walks a band of rows top to bottom for
 // its columns (lane, lane + 32, ...): the south link flux of a row is the
 // negated north link flux of the next row (exactly, see link_flux), so each
 // pixel evaluates three links (N reused) instead of four.
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
                                                        int n_frames, int T, int dx, int dy,
                                                        float lam, float c)
 {
-    extern __shared__ float2 sm2[];
+    extern __shared__ float sm1[];
     const int tile = blockIdx.x;
     int lo = 0, hi = n_frames - 1;
     while (lo < hi) {
@@ -171,9 +171,10 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
     const int tl = tile - f.tile_begin;
     const int tx0 = (tl % f.tiles_x) * dx;
     const int ty0 = (tl / f.tiles_x) * dy;
-    const int SX = dx + 2 * T, SY = dy + 2 * T;
-    float2 *A = sm2;
-    float2 *B = sm2 + SX * SY;
+    const int SX = dx + 2 * T, SY = dy + 2 * T, NC = SX * SY;
+    float *Hs = sm1;             // hi parts
+    float *A = sm1 + NC;         // lo parts read by this iteration
+    float *B = sm1 + 2 * NC;     // lo parts it writes
     const int lane = threadIdx.x, wy = threadIdx.y;
 
     if (f.src_dtype == SRC_PAIR || f.src_dtype == PM_U16_MM) {
@@ -218,7 +219,8 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
                                 const float h = __fmul_rn(qf, f.scale);
                                 w = q ? make_float2(h, __fmaf_rn(qf, f.scale, -h)) : hole;
                             }
-                            A[y * SX + x] = w;
+                            Hs[y * SX + x] = w.x;
+                            A[y * SX + x] = w.y;
                         }
                     }
                 }
@@ -232,7 +234,8 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
                 float2 v = make_float2(HOLE, 0.0f);
                 if (gx >= 0 && gx < f.w && gy >= 0 && gy < f.h)
                     v = load_px(f.src, f.src_dtype, f.src_pitch, gx, gy, f.scale);
-                A[y * SX + x] = v;
+                Hs[y * SX + x] = v.x;
+                A[y * SX + x] = v.y;
             }
         }
     }
@@ -253,18 +256,20 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
                 for (int g = 0; r0 + 32 * g < xe; ++g) {
                     const int x = r0 + lane + 32 * g;
                     const bool act = x < xe;
-                    const float2 *pa = A + y0 * SX + (act ? x : xe - 1);
-                    float2 *pb = B + y0 * SX + (act ? x : xe - 1);
-                    float2 cen = pa[0];
-                    float fN = link_flux(cen, pa[-SX], c);
-                    for (int y = y0; y < y1; ++y, pa += SX, pb += SX) {
-                        const float2 dn = pa[SX];
+                    const int k0 = y0 * SX + (act ? x : xe - 1);
+                    const float *ph = Hs + k0;
+                    const float *pa = A + k0;
+                    float *pb = B + k0;
+                    float2 cen = make_float2(ph[0], pa[0]);
+                    float fN = link_flux(cen, make_float2(ph[-SX], pa[-SX]), c);
+                    for (int y = y0; y < y1; ++y, ph += SX, pa += SX, pb += SX) {
+                        const float2 dn = make_float2(ph[SX], pa[SX]);
                         const float fS = link_flux(cen, dn, c);
-                        const float fW = link_flux(cen, pa[-1], c);
-                        const float fE = link_flux(cen, pa[1], c);
+                        const float fW = link_flux(cen, make_float2(ph[-1], pa[-1]), c);
+                        const float fE = link_flux(cen, make_float2(ph[1], pa[1]), c);
                         const float2 v = pm4_combine(cen, fN, fS, fW, fE, lam);
                         if (act)
-                            *pb = v;
+                            *pb = v.y;
                         fN = -fS;
                         cen = dn;
                     }
@@ -273,12 +278,16 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
                 for (int x = r0 + lane; x < SX - r0; x += 32)
                     for (int y = y0; y < y1; ++y) {
                         const int k = y * SX + x;
-                        B[k] = update_alg1(A[k], A[k - SX], A[k + SX], A[k - 1], A[k + 1], lam, c);
+                        const float2 v = update_alg1(
+                            make_float2(Hs[k], A[k]), make_float2(Hs[k - SX], A[k - SX]),
+                            make_float2(Hs[k + SX], A[k + SX]), make_float2(Hs[k - 1], A[k - 1]),
+                            make_float2(Hs[k + 1], A[k + 1]), lam, c);
+                        B[k] = v.y;
                     }
             }
         }
         __syncthreads();
-        float2 *t = A; A = B; B = t;
+        float *t = A; A = B; B = t;
     }
     for (int y = wy; y < dy; y += 8) {
         const int gy = ty0 + y;
@@ -286,8 +295,9 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
             break;
         for (int x = lane; x < dx; x += 32) {
             const int gx = tx0 + x;
+            const int k = (y + T) * SX + x + T;
             if (gx < f.w)
-                store_px(f, (long long)gy * f.w + gx, A[(y + T) * SX + x + T]);
+                store_px(f, (long long)gy * f.w + gx, make_float2(Hs[k], A[k]));
         }
     }
 }
@@ -435,7 +445,7 @@ static inline float conductance_scale(float K)
 
 size_t diffuse_tiles_smem(int T, int dx, int dy)
 {
-    return 2ull * (dx + 2 * T) * (dy + 2 * T) * sizeof(float2);
+    return 3ull * (dx + 2 * T) * (dy + 2 * T) * sizeof(float);
 }
 
 cudaError_t diffuse_init()
