@@ -363,7 +363,9 @@ def run_served(torch, pm, args, c2_frames, c2_dev):
                   realtime=False)
     out['capacity_mix'] = summarize(cap, srv.elapsed)
     srv.close()
-    srv = Server(p, budget_bytes=4 << 30, max_batch=16, n_lanes=2, max_w=640, max_h=480)
+    # 640x480 only: three lanes' scratch (1.1 GiB) fits the budget with room
+    # to spare (the mixed server, sized for 1280x720, keeps two: 2.3 GiB)
+    srv = Server(p, budget_bytes=4 << 30, max_batch=16, n_lanes=3, max_w=640, max_h=480)
     h2 = [torch.from_numpy(f.encoded).pin_memory() for f in c2_frames]
     def c2_reqs():
         return [Request(i % 16, i, 0.0, h2[i % len(h2)], c2_frames[0].cam.intrinsics,
@@ -399,7 +401,10 @@ def run_ours(args):
                        seed=0)
     pipe = pm.Pipeline(params, 640, 480, B)
     tuned = None
-    if not args.no_tune:
+    if args.tiling:
+        tuned = {'best': tuple(int(v) for v in args.tiling.split(','))}
+        pipe.set_tiling(*tuned['best'])
+    elif not args.no_tune:
         from paper_2411_01919_b300.tune import DiffusionTuner
         tuned = DiffusionTuner().tune(pipe, [dict(depth=dframes[i], K=frames[i].cam.intrinsics,
                                                   frame_idx=i) for i in range(B)])
@@ -644,6 +649,8 @@ def main():
     ap.add_argument('--lanes', type=int, default=3,
                     help='pipelines taking the timed batches in turn (batches in flight)')
     ap.add_argument('--no-tune', action='store_true')
+    ap.add_argument('--tiling', default='',
+                    help='diffusion tiling T,tile_w,tile_h instead of autotuning (e.g. 8,80,48)')
     ap.add_argument('--served-seconds', type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == 'ours':
