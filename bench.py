@@ -35,9 +35,9 @@ ITERS, HYP, MAXP, MINI, THR = 30, 1024, 12, 100, 0.01
 FP32_FLOP_PER_PAIR = 8          # 3 FMA residual + 1 FMA squared-threshold test
 # DRAM bytes (read + write) of the scoring kernel per hypothesis-point pair,
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on round 0
-# of 32 frames of this workload: 156.4 MB for 9.73e9 pairs.  With the number
+# of 32 frames of this workload: 155.9 MB for 9.73e9 pairs.  With the number
 # of hypotheses fixed, traffic grows with the candidate count, i.e. with pairs.
-SCORE_DRAM_BYTES_PER_PAIR = (152.80e6 + 3.58e6) / 9.73e9   # ncu, k_score round 0, 32 frames
+SCORE_DRAM_BYTES_PER_PAIR = (152.75e6 + 3.11e6) / 9.73e9   # ncu, k_score round 0, 32 frames
 SEGMENT, BOX_TEST_FLOP = 32, 14   # box test: 6 FFMA + 2 FADD
 N_SETS = 4                      # device copies of the batch the timed steps cycle through
 REGION_FLOP_PER_PAIR = 9     # 3 FMA residual, |r| x 2^32, 1 FMA inlier test

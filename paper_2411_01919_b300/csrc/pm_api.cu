@@ -372,13 +372,19 @@ pm_status enqueue_ransac(pm_ctx *ctx, RFrame *d_rframes, int n, long long total_
     const int hb = score_hyp_block(L.fine_score, L.prm.H);
     const long long score_items = total_chunks * (L.fine_score ? (L.prm.H + hb - 1) / hb : 1);
     const long long sb = (long long)ctx->sms * score_ctas_per_sm(L.fine_score, L.prm.H);
-    const long long cb = (long long)ctx->sms * 4;
+    // persistent grids of the resident CTAs (a CTA beyond them would start
+    // only when a resident one has finished all its work items)
+    const long long cb = (long long)ctx->sms * compact_ctas_per_sm();
+    const long long rb = (long long)ctx->sms * remove_ctas_per_sm();
     L.score_blocks = (int)(score_items < sb ? score_items : sb);
     L.chunk_blocks = (int)(total_chunks < cb ? total_chunks : cb);
+    L.remove_blocks = (int)(total_chunks < rb ? total_chunks : rb);
     if (L.score_blocks < 1)
         L.score_blocks = 1;
     if (L.chunk_blocks < 1)
         L.chunk_blocks = 1;
+    if (L.remove_blocks < 1)
+        L.remove_blocks = 1;
     if (!ctx->rstream) {
         PM_CK(cudaStreamCreateWithFlags(&ctx->rstream, cudaStreamNonBlocking));
         for (int i = 0; i < 2; ++i)

@@ -186,7 +186,8 @@ struct RansacLaunch {
     int max_total_chunks; // bound for persistent grids
     RParams prm;
     int score_blocks;     // persistent grid sizes
-    int chunk_blocks;
+    int chunk_blocks;     // grid of k_mark0 / k_compact (their resident CTAs, at most one per chunk)
+    int remove_blocks;    // grid of k_remove
     unsigned *d_counter;  // grid-completion counter of the compaction kernel
     bool fine_score;      // smaller hypothesis blocks, selection fused (small batches)
     cudaStream_t side;    // the refit's stream
@@ -238,9 +239,11 @@ struct SegLaunch {
 cudaError_t segment_regions(const SegLaunch &S, cudaStream_t s);
 
 cudaError_t ransac_init(const RansacLaunch &L, cudaStream_t s);
-cudaError_t score_init();                  // shared-memory opt-in and occupancy of k_score
+cudaError_t score_init();                  // shared-memory opt-in; occupancy of the RANSAC kernels
 int score_hyp_block(bool fine, int H);     // hypotheses per scoring work item
 int score_ctas_per_sm(bool fine, int H);
+int remove_ctas_per_sm();                  // resident CTAs per SM of k_remove
+int compact_ctas_per_sm();                 // ... of k_compact (and k_mark0)
 // ev_score: optional event pair recorded around the scoring launch.
 cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream_t s,
                          cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);

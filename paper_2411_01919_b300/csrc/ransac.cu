@@ -1064,6 +1064,7 @@ static cudaError_t score_attr(int *ctas)
 }
 
 static int g_score_ctas[3] = {1, 1, 1};   // CTAs per SM: <256,true>, <256,false>, <512,false>
+static int g_remove_ctas = 1, g_compact_ctas = 1;
 
 cudaError_t score_init()
 {
@@ -1072,8 +1073,16 @@ cudaError_t score_init()
         e = score_attr<256, false, true>(&g_score_ctas[1]);
     if (e == cudaSuccess)
         e = score_attr<512, false, true>(&g_score_ctas[2]);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_remove_ctas, k_remove,
+                                                          REMOVE_THREADS, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_compact_ctas, k_compact, 256, 0);
     return e;
 }
+
+int remove_ctas_per_sm() { return g_remove_ctas > 0 ? g_remove_ctas : 1; }
+int compact_ctas_per_sm() { return g_compact_ctas > 0 ? g_compact_ctas : 1; }
 
 int score_hyp_block(bool fine, int H) { return fine || H <= 256 ? 256 : 512; }
 
@@ -1115,7 +1124,7 @@ cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream
         record_event(ev_after, s);
     if (!fine)
         k_select<<<L.n, 1024, 0, s>>>(L.d_frames, p);
-    k_remove<<<L.chunk_blocks, REMOVE_THREADS, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
+    k_remove<<<L.remove_blocks, REMOVE_THREADS, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
     // the refit runs beside the compaction (and the next round's hypotheses
     // and scoring) on the side stream: nothing there reads its result
     if ((e = cudaEventRecord(L.ev_fork, s)) != cudaSuccess ||
