@@ -337,8 +337,9 @@ long long pm_scratch_bytes(int max_w, int max_h, int max_frames, int hypotheses,
  * events around every scoring launch (captured into graphs too);
  * pm_kernel_stats then returns the scoring kernels' summed device time (ms),
  * the hypothesis-point pairs they scored (H x candidates per round), the
- * pairs actually evaluated (the rest were proven inlier-free by the box
- * test) and their launch count.  In every
+ * pairs actually evaluated (a box test settled the rest exactly: its
+ * 32-candidate segment holds no inlier of the hypothesis, or only inliers)
+ * and their launch count.  In every
  * mode pm_kernel_stats returns in *launches the number of kernels the last
  * call launched.  Any output pointer may be NULL. */
 pm_status pm_set_timing(pm_ctx *ctx, int on);

@@ -2,7 +2,7 @@
 seeded inputs, plus form-equivalence (temporal blocking, batch vs single,
 graph vs stream launches, host vs device entry).
 
-Tolerances (spec bar, written here):
+Tolerances (the targets, written here):
   diffusion            <= 1e-5 m max abs (FP32 and FP16-storage paths alike)
   normals              <= 0.05 deg
   plane normal/offset  <= 0.1 deg / 1 mm
