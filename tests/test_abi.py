@@ -60,7 +60,7 @@ def _create(**kw):
                                 dict(ipl=9), dict(H=0), dict(H=4096), dict(thr=0.0),
                                 dict(mp=0), dict(mp=65), dict(mi=2), dict(stencil=3),
                                 dict(w=0), dict(frames=0), dict(frames=2000),
-                                dict(iters=-1), dict(tw=81), dict(th=49), dict(tw=-1)])
+                                dict(iters=-1), dict(tw=129), dict(th=49), dict(tw=-1)])
 def test_create_rejects_bad_parameters_before_touching_the_device(kw):
     st, h = _create(**kw)
     assert st == _ffi.PM_ERR_ARG
