@@ -336,7 +336,8 @@ def run_served(torch, pm, args, c2_frames, c2_dev):
     per frame), Poisson arrivals with a mean gap of 33 ms, continuous batching
     under a 4 GiB budget, real time for --served-seconds; then the capacity of
     the same loop with every request visible at once, on that stream mix and
-    on the 640x480 workload alone."""
+    on the 640x480 workload alone; and 16 cameras at 640x480 in real time for
+    a third of --served-seconds (at least 5 s)."""
     import synth
     from paper_2411_01919_b300.serve import Request, Server, poisson_arrivals, summarize
     n_streams, poses = 16, 4
@@ -371,6 +372,13 @@ def run_served(torch, pm, args, c2_frames, c2_dev):
         return [Request(i % 16, i, 0.0, h2[i % len(h2)], c2_frames[0].cam.intrinsics,
                         frame_idx=i) for i in range(1280)]
     srv.run(c2_reqs()[:128], realtime=False)                                  # warm-up
+    # the same 16 cameras at 640x480 in real time (Poisson, 30 Hz each)
+    rt_s = max(5.0, args.served_seconds / 3)
+    arr2 = poisson_arrivals(n_streams, rt_s, 1 / 30, seed=2)
+    rt2 = srv.run([Request(s, k, t, h2[(4 * s + k) % len(h2)], c2_frames[0].cam.intrinsics,
+                           frame_idx=k) for s, k, t in arr2], realtime=True)
+    out['realtime_640x480'] = dict(summarize(rt2, srv.elapsed), duration_s=rt_s,
+                                   offered=len(arr2))
     runs = []
     for _ in range(3):                   # a short run is noisy: the median of three
         cap2 = srv.run(c2_reqs(), realtime=False)
