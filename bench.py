@@ -353,7 +353,9 @@ def run_served(torch, pm, args, c2_frames, c2_dev):
     out = {'streams': n_streams, 'rate_per_stream_hz': 30, 'budget_bytes': 4 << 30,
            'resolutions': sorted({'%dx%d' % (f[0].w, f[0].h) for f in pool.values()}),
            'distinct_poses_per_stream': poses}
-    srv = Server(p, budget_bytes=4 << 30, max_batch=16, n_lanes=2)
+    # lanes sized for 1280x720: three of 10 frames hold 2.15 GiB of the 4 GiB
+    # budget (two of 16 frames: 2.29 GiB, and less capacity)
+    srv = Server(p, budget_bytes=4 << 30, max_batch=10, n_lanes=3)
     srv.run(make_reqs(poisson_arrivals(n_streams, 2.0, 1 / 30, seed=99)))   # warm-up
     arr = poisson_arrivals(n_streams, args.served_seconds, 1 / 30, seed=1)
     reqs = srv.run(make_reqs(arr), realtime=True)
@@ -364,8 +366,7 @@ def run_served(torch, pm, args, c2_frames, c2_dev):
                   realtime=False)
     out['capacity_mix'] = summarize(cap, srv.elapsed)
     srv.close()
-    # 640x480 only: three lanes' scratch (1.1 GiB) fits the budget with room
-    # to spare (the mixed server, sized for 1280x720, keeps two: 2.3 GiB)
+    # 640x480 only: three lanes of 16 frames hold 1.1 GiB
     srv = Server(p, budget_bytes=4 << 30, max_batch=16, n_lanes=3, max_w=640, max_h=480)
     h2 = [torch.from_numpy(f.encoded).pin_memory() for f in c2_frames]
     def c2_reqs():
