@@ -16,6 +16,8 @@
  * - "Device" pointers are CUDA device (or managed) memory on the current
  *   device; "host" pointers are ordinary CPU memory.  The caller owns every
  *   buffer it passes; the library owns only the scratch inside a pm_ctx.
+ *   Device buffers must be aligned to their element size (2 bytes for u16 /
+ *   f16 / int16, 4 for float / int32); a misaligned one returns PM_ERR_ARG.
  * - Every call is asynchronous on `stream` (a cudaStream_t passed as void*,
  *   NULL = the legacy default stream) unless it returns results in host
  *   memory, in which case it synchronises `stream` before returning.

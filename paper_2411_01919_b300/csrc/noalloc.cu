@@ -4,6 +4,7 @@
 // allocation; host code reaches the array through the address that
 // cudaGetSymbolAddress returns for the current device.
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 #include "pm_internal.cuh"
@@ -60,6 +61,8 @@ extern "C" pm_status pm_diffuse_noalloc(const void *depth, int dtype, int w, int
         return set_last_error(PM_ERR_ARG,
                               "image larger than PM_NOALLOC_MAX_PIXELS (524288 pixels)");
     const int es = dtype == PM_F32_M ? 4 : 2;
+    if (((uintptr_t)depth & (es - 1)) != 0 || ((uintptr_t)out & 3) != 0)
+        return set_last_error(PM_ERR_ARG, "depth or output pointer not aligned to its element size");
     if (pitch < w * es || pitch % es != 0)
         return set_last_error(PM_ERR_ARG, "pitch smaller than a row or not a multiple of the "
                                           "element size");

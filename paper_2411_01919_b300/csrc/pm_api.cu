@@ -1,6 +1,7 @@
 // pm_api.cu -- the C ABI of libpm (include/pm.h): contexts, argument checks,
 // scratch arena, launch orchestration, CUDA-graph capture of batches.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -173,6 +174,10 @@ pm_status check_params(const pm_diffusion_params *dp, const pm_ransac_params *rp
     return PM_OK;
 }
 
+// Whether a device pointer meets the alignment of its element type (a
+// misaligned element access would fault the kernel instead of failing here).
+bool misaligned(const void *p, size_t align) { return ((uintptr_t)p & (align - 1)) != 0; }
+
 pm_status check_frame(const pm_ctx *ctx, const void *depth, int dtype, int w, int h,
                       long long pitch, const pm_intrinsics *K)
 {
@@ -186,6 +191,8 @@ pm_status check_frame(const pm_ctx *ctx, const void *depth, int dtype, int w, in
         return fail(PM_ERR_ARG, "image larger than the context's max_w * max_h");
     if (pitch < (long long)w * elem_size(dtype) || pitch % elem_size(dtype) != 0)
         return fail(PM_ERR_ARG, "pitch smaller than a row or not a multiple of the element size");
+    if (misaligned(depth, elem_size(dtype)))
+        return fail(PM_ERR_ARG, "depth pointer not aligned to its element size");
     if (K && (!(K->fx > 0) || !(K->fy > 0) || !std::isfinite(K->fx) || !std::isfinite(K->fy) ||
               !std::isfinite(K->cx) || !std::isfinite(K->cy)))
         return fail(PM_ERR_ARG, "intrinsics must be finite with fx, fy > 0");
@@ -683,6 +690,8 @@ pm_status pm_diffuse(pm_ctx *ctx, const void *depth, int dtype, int w, int h, in
 {
     if (!ctx || !out)
         return fail(PM_ERR_ARG, "null context or output");
+    if (misaligned(out, 4))
+        return fail(PM_ERR_ARG, "output pointer not 4-byte aligned");
     pm_status st = check_frame(ctx, depth, dtype, w, h, pitch, nullptr);
     if (st != PM_OK)
         return st;
@@ -718,6 +727,8 @@ pm_status pm_normals(pm_ctx *ctx, const float *depth, int w, int h, const pm_int
 {
     if (!ctx || !K || !points || !normals || !valid)
         return fail(PM_ERR_ARG, "null argument");
+    if (misaligned(points, 4) || misaligned(normals, 4))
+        return fail(PM_ERR_ARG, "points / normals not 4-byte aligned");
     pm_status st = check_frame(ctx, depth, PM_F32_M, w, h, (long long)w * 4, K);
     if (st != PM_OK)
         return st;
@@ -735,6 +746,8 @@ pm_status pm_ransac_planes(pm_ctx *ctx, const float *points, const float *normal
         return fail(PM_ERR_ARG, "null argument");
     if (w < 1 || h < 1 || (long long)w * h > ctx->max_npx)
         return fail(PM_ERR_ARG, "image size out of range for this context");
+    if (misaligned(points, 4) || misaligned(normals, 4) || misaligned(labels, 2))
+        return fail(PM_ERR_ARG, "points / normals / labels not aligned to their element size");
     if (ctx->pending_n)
         return fail(PM_ERR_STATE, "an asynchronous batch is still pending on this context");
     cudaStream_t s = (cudaStream_t)stream;
@@ -781,6 +794,8 @@ pm_status pm_process_frame(pm_ctx *ctx, const void *depth, int dtype, int w, int
 {
     if (!ctx || !K || !planes || !n_planes || max_planes < 0)
         return fail(PM_ERR_ARG, "null argument");
+    if (misaligned(labels, 2))
+        return fail(PM_ERR_ARG, "labels not 2-byte aligned");
     pm_status st = check_frame(ctx, depth, dtype, w, h, pitch, K);
     if (st != PM_OK)
         return st;
@@ -839,6 +854,9 @@ static pm_status batch_jobs(pm_ctx *ctx, const pm_frame *frames, int n,
         pm_status st = check_frame(ctx, fr.depth, fr.dtype, fr.w, fr.h, fr.pitch, &fr.K);
         if (st != PM_OK)
             return fail(st, "frame " + std::to_string(f) + ": " + g_err);
+        if (misaligned(fr.labels, 2) || misaligned(fr.depth_out, 4))
+            return fail(PM_ERR_ARG, "frame " + std::to_string(f) +
+                                        ": labels / depth_out not aligned to their element size");
         const int it = fr.iters < 0 ? ctx->dp.iters : fr.iters;
         if (it > 100000)
             return fail(PM_ERR_ARG, "frame " + std::to_string(f) + ": iters out of range");
@@ -911,6 +929,8 @@ pm_status pm_ransac_regions(pm_ctx *ctx, const float *points, const unsigned cha
 {
     if (!ctx || !points || !valid || !regions || !out)
         return fail(PM_ERR_ARG, "null argument");
+    if (misaligned(points, 4) || misaligned(regions, 4))
+        return fail(PM_ERR_ARG, "points / regions not 4-byte aligned");
     if (w < 1 || h < 1 || (long long)w * h > ctx->max_npx)
         return fail(PM_ERR_ARG, "image size out of range for this context");
     if (n_regions < 1 || n_regions > 65535)
@@ -1028,6 +1048,8 @@ pm_status pm_canny(pm_ctx *ctx, const float *normals, const unsigned char *valid
 {
     if (!ctx || !normals || !valid || !edges)
         return fail(PM_ERR_ARG, "null argument");
+    if (misaligned(normals, 4))
+        return fail(PM_ERR_ARG, "normals not 4-byte aligned");
     if (w < 1 || h < 1 || (long long)w * h > ctx->max_npx)
         return fail(PM_ERR_ARG, "image size out of range for this context");
     if (low < 0 || high < low)
@@ -1060,6 +1082,8 @@ pm_status pm_segment(pm_ctx *ctx, const unsigned char *edges, const unsigned cha
 {
     if (!ctx || !edges || !valid || !labels || !n_regions)
         return fail(PM_ERR_ARG, "null argument");
+    if (misaligned(labels, 4))
+        return fail(PM_ERR_ARG, "labels not 4-byte aligned");
     if (w < 1 || h < 1 || (long long)w * h > ctx->max_npx)
         return fail(PM_ERR_ARG, "image size out of range for this context");
     if (gap < 0 || gap > 1 || min_pixels < 1)

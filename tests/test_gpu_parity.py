@@ -8,6 +8,7 @@ Tolerances (the targets, written here):
   plane normal/offset  <= 0.1 deg / 1 mm
   inlier labels        bit-exact (the inlier decision is FP32 on both sides)
 """
+import ctypes
 import functools
 
 import numpy as np
@@ -435,6 +436,30 @@ def test_argument_errors_raise():
             pipe.diffuse(torch.zeros((4, 4), dtype=torch.float64, device=DEV))
         with pytest.raises(PmError):
             pipe.process_batch([dict(depth=torch.zeros((4, 4), device=DEV), K=(0, 1, 0, 0))])
+
+
+def test_misaligned_device_pointers_are_rejected_before_launch():
+    """A device buffer not aligned to its element size is refused on the host
+    (PM_ERR_ARG) before any kernel could touch it."""
+    from paper_2411_01919_b300 import _ffi
+    buf = torch.zeros(32 * 32 + 4, dtype=torch.float32, device=DEV)
+    out = torch.zeros(32 * 32 + 4, dtype=torch.float32, device=DEV)
+    base, obase = buf.data_ptr(), out.data_ptr()
+    with Pipeline(Params(iters=2), 32, 32) as pipe:
+        lib, h = pipe.lib, pipe._h
+        assert lib.pm_diffuse(h, base + 2, _ffi.PM_F32_M, 32, 32, 128, obase, None) == _ffi.PM_ERR_ARG
+        assert lib.pm_diffuse(h, base + 1, _ffi.PM_U16_MM, 32, 32, 64, obase, None) == _ffi.PM_ERR_ARG
+        assert lib.pm_diffuse(h, base, _ffi.PM_F32_M, 32, 32, 128, obase + 2, None) == _ffi.PM_ERR_ARG
+        assert b'align' in lib.pm_last_error()
+        K = _ffi.Intrinsics(30.0, 30.0, 16.0, 16.0)
+        planes = (_ffi.Plane * 4)()
+        n = ctypes.c_int(0)
+        st = lib.pm_process_frame(h, base, _ffi.PM_F32_M, 32, 32, 128, ctypes.byref(K), 0, planes,
+                                  4, ctypes.byref(n), obase + 1, None)
+        assert st == _ffi.PM_ERR_ARG
+        # the aligned call goes through
+        assert lib.pm_diffuse(h, base, _ffi.PM_F32_M, 32, 32, 128, obase, None) == _ffi.PM_OK
+        torch.cuda.synchronize()
 
 
 def test_graph_replay_records_kernel_timing_events():
