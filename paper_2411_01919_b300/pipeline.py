@@ -41,6 +41,13 @@ class Params:
     depth_scale: float = 0.001
 
 
+# pm_plane as a numpy record (include/pm.h): the planes array a call fills is
+# read as one structured view instead of field by field
+_PLANE_DT = np.dtype([('n', '<f8', (3,)), ('d', '<f8'), ('n_inliers', '<i4'),
+                      ('n_refit', '<i4'), ('rms', '<f4'), ('hyp_index', '<i4')])
+assert _PLANE_DT.itemsize == ctypes.sizeof(_ffi.Plane)
+
+
 @dataclass
 class Planes:
     """Planes of one frame: rows (nx, ny, nz, d) with n . X + d = 0."""
@@ -53,10 +60,10 @@ class Planes:
 
     @staticmethod
     def from_c(arr, n, labels=None) -> 'Planes':
-        pl = np.array([[*arr[i].n, arr[i].d] for i in range(n)], dtype=np.float64).reshape(-1, 4)
-        g = lambda k, t: np.array([getattr(arr[i], k) for i in range(n)], dtype=t)
-        return Planes(pl, g('n_inliers', np.int64), g('n_refit', np.int64), g('rms', np.float64),
-                      g('hyp_index', np.int64), labels)
+        a = np.frombuffer(arr, dtype=_PLANE_DT, count=n)
+        pl = np.concatenate([a['n'], a['d'][:, None]], axis=1)
+        return Planes(pl, a['n_inliers'].astype(np.int64), a['n_refit'].astype(np.int64),
+                      a['rms'].astype(np.float64), a['hyp_index'].astype(np.int64), labels)
 
 
 @dataclass

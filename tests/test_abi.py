@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2411_01919_b300 as pm
@@ -89,3 +90,27 @@ def test_edge_and_region_calls_reject_a_null_context():
     assert lib.pm_canny(None, None, None, 64, 48, 60, 150, None, None) == _ffi.PM_ERR_ARG
     assert lib.pm_segment(None, None, None, 64, 48, 1, 200, None, ctypes.byref(n),
                           None) == _ffi.PM_ERR_ARG
+
+
+def test_plane_records_read_as_written():
+    """The binding reads the pm_plane array a call fills as one structured
+    view; every field must come back as the C struct holds it."""
+    from paper_2411_01919_b300.pipeline import Planes
+    rng = np.random.default_rng(3)
+    for n in (0, 1, 7, 12):
+        arr = (_ffi.Plane * 12)()
+        for i in range(12):
+            p = arr[i]
+            p.n[0], p.n[1], p.n[2] = rng.normal(size=3)
+            p.d = float(rng.normal())
+            p.n_inliers = int(rng.integers(0, 1 << 30))
+            p.n_refit = int(rng.integers(-5, 1 << 20))
+            p.rms = float(np.float32(rng.random()))
+            p.hyp_index = int(rng.integers(-1, 2048))
+        got = Planes.from_c(arr, n)
+        assert got.planes.shape == (n, 4) and got.planes.dtype == np.float64
+        for i in range(n):
+            p = arr[i]
+            assert list(got.planes[i]) == [p.n[0], p.n[1], p.n[2], p.d]
+            assert got.n_inliers[i] == p.n_inliers and got.n_refit[i] == p.n_refit
+            assert got.rms[i] == np.float32(p.rms) and got.hyp_index[i] == p.hyp_index
