@@ -243,6 +243,43 @@ def test_ransac_stage_bit_exact_labels(name):
     assert np.array_equal(lab, orc.labels)
 
 
+def test_ransac_to_the_plane_limit():
+    """64 sequential rounds (the plane limit) on a uniform random cloud, where
+    every round finds a plane through a few dozen points: labels, winners
+    and counts equal the oracle's in every round."""
+    rng = np.random.default_rng(7)
+    h, w = 40, 50
+    P = rng.uniform(-0.5, 0.5, (3, h, w)).astype(np.float32)
+    P[2] += 2.0
+    V = np.ones((h, w), dtype=np.uint8)
+    p = Params(iters=0, hypotheses=64, max_planes=64, min_inliers=3, seed=5)
+    orc = oracle.ransac(P, None, V, p.hypotheses, p.thr, p.max_planes, p.min_inliers, p.seed,
+                        p.gate_deg, 3)
+    assert len(orc.planes) == 64
+    with Pipeline(p, w, h) as pipe:
+        pipe.set_timing(2)
+        g = pipe.ransac_planes(to_dev(P), None, to_dev(V), frame_idx=3)
+        lab = g.labels.cpu().numpy()
+        st = pipe.kernel_stats()
+    assert np.array_equal(g.hyp_index, orc.hyp_index)
+    assert np.array_equal(g.n_inliers, orc.n_inliers)
+    assert np.array_equal(lab, orc.labels)
+    assert st['score_launches'] == 64 and st['score_pairs'] > 0
+
+
+def test_ransac_single_hypothesis_per_round():
+    fr = frame('c1')
+    P, N, V = ransac_inputs('c1')
+    p = Params(iters=0, hypotheses=1, max_planes=8, min_inliers=3, seed=5)
+    orc = oracle.ransac(P, N, V, p.hypotheses, p.thr, p.max_planes, p.min_inliers, p.seed,
+                        p.gate_deg, 3)
+    with Pipeline(p, fr.w, fr.h) as pipe:
+        g = pipe.ransac_planes(to_dev(P), to_dev(N), to_dev(V), frame_idx=3)
+        lab = g.labels.cpu().numpy()
+    compare_planes(g, orc)
+    assert np.array_equal(lab, orc.labels)
+
+
 def test_ransac_frame_index_changes_hypotheses():
     fr = frame('c1')
     P, N, V = ransac_inputs('c1')
