@@ -193,24 +193,34 @@ __device__ bool last_item_of_frame(int *counter, int items)
 // ---------------------------------------------------------------------------
 // round 0 candidate list: valid pixels in row-major order
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_mark0(RFrame *frames, int n, const int *chunk_base)
+constexpr int MARK_THREADS = 256;
+
+__global__ void __launch_bounds__(MARK_THREADS) k_mark0(RFrame *frames, int n,
+                                                        const int *chunk_base)
 {
-    __shared__ int wsum[8];
+    __shared__ int wsum[MARK_THREADS / 32];
+    constexpr int PER = CHUNK / MARK_THREADS;
     const int total = chunk_base[n];
     for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
         const int f = frame_of(chunk_base, n, wi);
         const RFrame &F = frames[f];
         const int c = wi - chunk_base[f];
         const int base = c * CHUNK;
+        // the thread's PER pixels loaded together, then marked
+        unsigned char vb[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int pix = base + threadIdx.x + u * MARK_THREADS;
+            vb[u] = pix < F.npx ? F.valid[pix] : 0;
+        }
         int kept = 0;
-        for (int j = threadIdx.x; j < CHUNK; j += blockDim.x) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int j = threadIdx.x + u * MARK_THREADS;
             const int pix = base + j;
-            bool keep = false;
-            if (pix < F.npx) {
-                keep = (F.valid[pix] & 1) != 0;
+            if (pix < F.npx)
                 F.labels[pix] = -1;
-            }
-            unsigned word = __ballot_sync(0xffffffffu, keep);
+            const unsigned word = __ballot_sync(0xffffffffu, (vb[u] & 1) != 0);
             if ((threadIdx.x & 31) == 0) {
                 F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)] = word;
                 kept += __popc(word);
@@ -221,7 +231,7 @@ __global__ void __launch_bounds__(256) k_mark0(RFrame *frames, int n, const int 
         __syncthreads();
         if (threadIdx.x == 0) {
             int s = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            for (int w = 0; w < MARK_THREADS / 32; ++w)
                 s += wsum[w];
             F.kept[c] = s;
         }
@@ -1038,7 +1048,7 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_refit(RFrame *frames, RParam
 cudaError_t ransac_init(const RansacLaunch &L, cudaStream_t s)
 {
     k_plan0<<<1, 1024, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, L.d_counter);
-    k_mark0<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base);
+    k_mark0<<<L.chunk_blocks, MARK_THREADS, 0, s>>>(L.d_frames, L.n, L.d_chunk_base);
     k_compact<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, 0, true, 0,
                                              L.prm.min_inliers, L.d_counter);
     return cudaGetLastError();
