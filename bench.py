@@ -181,6 +181,21 @@ def oracle_all_cores(frames):
                       'wall %.1f s (%.1f-%.1f s per frame)' % (n, wall, min(secs), max(secs))}
 
 
+def oracle_frame_stages(fr, frame_idx=0):
+    """The oracle's frame (the chain oracle.process_frame runs: decode,
+    diffusion, normals, RANSAC on the FP32 points), each stage timed."""
+    import oracle
+    t0 = time.perf_counter()
+    zs = oracle.diffuse(oracle.decode(fr.encoded, fr.dtype, 0.001), ITERS)
+    t1 = time.perf_counter()
+    P, N, V = oracle.normals(zs, fr.cam.intrinsics, 0)
+    t2 = time.perf_counter()
+    oracle.ransac(P.astype(np.float32), N.astype(np.float32), V, HYP, THR, MAXP, MINI, 0, 20.0,
+                  frame_idx)
+    t3 = time.perf_counter()
+    return t3 - t0, {'decode_diffuse_s': t1 - t0, 'normals_s': t2 - t1, 'ransac_s': t3 - t2}
+
+
 def run_reference(args):
     rank, _, world = env_rank()
     if rank != 0:
@@ -673,9 +688,9 @@ def run_ours(args):
 
     cpu = cpu_all = None
     if rank == 0 and not args.skip_cpu:
-        sec = oracle_frame_seconds(frames[0], 0)
+        sec, stages = oracle_frame_stages(frames[0], 0)
         cpu = {'value': 1.0 / sec, 'unit': 'frames/s', 'cores': 1, 'kind': 'oracle',
-               'host': host_cpu_model(),
+               'host': host_cpu_model(), 'stages_s': stages,
                'sample': '1 of the %d frames of a step, single-threaded C oracle (%.1f s)'
                          % (B, sec)}
         cpu_all = oracle_all_cores(frames)
