@@ -5,14 +5,15 @@
 //   k_hyp     : Philox4x64-10 -> three candidate indices -> FP32 plane (Alg. 2
 //               "select random subset of 3 points", "fit plane model")
 //   k_score   : every hypothesis against every candidate on FP32 CUDA cores
-//               (Alg. 2 inner parallel loop), skipping the pairs that a box
-//               test proves to hold no inlier; integer counters, one atomic
+//               (Alg. 2 inner parallel loop); a box test per 32-candidate
+//               segment settles the pairs it proves to hold no inlier or
+//               only inliers without evaluating them; integer counters, one atomic
 //               add per (work item, hypothesis).  For small batches the CTA
 //               that finishes a frame's last work item picks the frame's
 //               winner (maximum count, ties to the lowest index: an integer
 //               key); for large ones k_select does, one block per frame.
 //   k_remove  : labels of the winner's inliers, keep bitmask of the rest,
-//               compensated-FP32 moments of the inliers per group of chunks.
+//               compensated-FP32 moments of the inliers, one record per chunk.
 //   k_refit   : the group records reduced in compensated FP32 in a fixed
 //               order, the 3x3 eigenproblem solved in FP64 -> plane.  It runs
 //               on a side stream beside the compaction and the next round's
