@@ -177,7 +177,9 @@ pm_status pm_ransac_planes(pm_ctx *ctx, const float *points, const float *normal
  * sequence is captured once per frame shape and replayed as a CUDA graph
  * (on a context-owned stream ordered with the caller's when `stream` is the
  * legacy default stream); if `stream` is being captured by the caller, the
- * kernels are launched directly into that capture instead. */
+ * kernels are launched directly into that capture instead.  A context keeps
+ * the graphs of its 16 most recently captured shapes (frame or batch); a
+ * seventeenth shape evicts the oldest. */
 pm_status pm_process_frame(pm_ctx *ctx, const void *depth, int dtype, int w, int h, int pitch,
                            const pm_intrinsics *K, unsigned long long frame_idx,
                            pm_plane *planes, int max_planes, int *n_planes, short *labels,
