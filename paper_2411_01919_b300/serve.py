@@ -15,7 +15,12 @@ Admission is by memory: a request holds, while it is queued or on the GPU,
 the scratch bytes its frame size needs (pm_scratch_bytes for one frame) plus
 its input bytes; the sum over admitted requests stays within the budget
 (default 4 GiB) minus what the lanes and the per-stream buffers hold for good.
-A request not admitted within `max_wait_s` of its arrival is refused.
+A request not admitted within `max_wait_s` of its arrival is refused.  A
+request that cannot be served at all (a frame larger than the lanes, an
+unsupported depth type, intrinsics that are not finite with fx, fy > 0, a
+stream that changes its frame size) is refused at admission with the reason
+in `error`, and the loop goes on serving the others; a batch whose launch
+still fails marks only its own requests.
 
 Each frame's result is bit-identical to processing it alone with
 pm_process_frame (the batched kernels never mix frames), which the test suite
@@ -24,6 +29,7 @@ checks on a mixed stream load.
 from __future__ import annotations
 
 import collections
+import math
 import time
 from dataclasses import dataclass, field
 from typing import Dict, List, Optional, Sequence
@@ -31,7 +37,8 @@ from typing import Dict, List, Optional, Sequence
 import numpy as np
 import torch
 
-from .pipeline import Params, Pipeline, Planes, scratch_bytes
+from ._ffi import PmError
+from .pipeline import _DT, Params, Pipeline, Planes, scratch_bytes
 
 
 @dataclass
@@ -48,6 +55,7 @@ class Request:
     t_done: Optional[float] = None
     planes: Optional[Planes] = None
     refused: bool = False
+    error: Optional[str] = None  # why the request was refused as invalid, or its batch failed
 
 
 @dataclass
@@ -71,6 +79,7 @@ class Server:
         self.max_batch = max_batch
         self.max_wait_s = max_wait_s
         self.use_graph = use_graph
+        self.max_w, self.max_h = max_w, max_h
         self.lanes = [_Lane(Pipeline(params, max_w, max_h, max_batch), torch.cuda.Stream(), i)
                       for i in range(n_lanes)]
         self.static_bytes = n_lanes * scratch_bytes(max_w, max_h, max_batch, params.hypotheses,
@@ -90,6 +99,30 @@ class Server:
         return (scratch_bytes(w, h, 1, self.p.hypotheses, self.p.max_planes)
                 + r.depth.numel() * r.depth.element_size())
 
+    def invalid(self, r: Request) -> Optional[str]:
+        """Why a request cannot be served (None if it can): checked at
+        admission so that one malformed request is refused alone."""
+        d = r.depth
+        if not isinstance(d, torch.Tensor) or d.dim() != 2 or d.dtype not in _DT:
+            return 'depth must be a 2-D uint16 / float16 / float32 tensor'
+        h, w = d.shape
+        if not (1 <= w <= self.max_w and 1 <= h <= self.max_h):
+            return 'frame %dx%d outside 1x1 .. %dx%d' % (w, h, self.max_w, self.max_h)
+        if d.stride(1) != 1:
+            return 'depth rows must be contiguous'
+        try:
+            fx, fy, cx, cy = (float(x) for x in r.K)
+        except (TypeError, ValueError):
+            return 'intrinsics must be four numbers'
+        if not (fx > 0 and fy > 0 and all(math.isfinite(x) for x in (fx, fy, cx, cy))):
+            return 'intrinsics must be finite with fx, fy > 0'
+        if r.iters > 100000:
+            return 'iters out of range'
+        bufs = self.dev.get(r.stream)
+        if bufs is not None and (bufs[0].shape != d.shape or bufs[0].dtype != d.dtype):
+            return 'stream %d changed its frame size or dtype' % r.stream
+        return None
+
     def _room(self) -> int:
         return self.budget - self.static_bytes - self.stream_bytes - self.in_use
 
@@ -107,14 +140,23 @@ class Server:
     # -- the loop -----------------------------------------------------------
     def _launch(self, lane: _Lane, batch: List[Request]):
         frames = []
-        with torch.cuda.stream(lane.stream):
+        try:
+            with torch.cuda.stream(lane.stream):
+                for r in batch:
+                    buf = self._stream_buffers(r)[lane.index]
+                    buf.copy_(r.depth, non_blocking=True)
+                    frames.append(dict(depth=buf, K=r.K, frame_idx=r.frame_idx, iters=r.iters))
+                lane.pipe.submit_batch(frames, use_graph=self.use_graph, stream=lane.stream)
+                lane.event = torch.cuda.Event()
+                lane.event.record(lane.stream)
+        except (PmError, ValueError) as e:
+            # nothing was enqueued for the batch: its requests fail, the lane stays free
             for r in batch:
-                buf = self._stream_buffers(r)[lane.index]
-                buf.copy_(r.depth, non_blocking=True)
-                frames.append(dict(depth=buf, K=r.K, frame_idx=r.frame_idx, iters=r.iters))
-            lane.pipe.submit_batch(frames, use_graph=self.use_graph, stream=lane.stream)
-            lane.event = torch.cuda.Event()
-            lane.event.record(lane.stream)
+                r.refused = True
+                r.error = 'batch failed: %s' % e
+                self.in_use -= r.bytes
+            self.stats['failed_batches'] += 1
+            return
         lane.batch = batch
         self.stats['batches'] += 1
         self.stats['batched_frames'] += len(batch)
@@ -132,6 +174,13 @@ class Server:
     def _admit(self, waiting: collections.deque, admitted: collections.deque, now: float):
         while waiting:
             r = waiting[0]
+            why = self.invalid(r)
+            if why is not None:
+                waiting.popleft()
+                r.refused = True
+                r.error = why
+                self.stats['invalid'] += 1
+                continue
             if now - r.t_arrival > self.max_wait_s:
                 waiting.popleft()
                 r.refused = True
@@ -220,6 +269,7 @@ def summarize(reqs: Sequence[Request], elapsed: float) -> dict:
         return lat[min(len(lat) - 1, int(round(q / 100.0 * (len(lat) - 1))))]
 
     return {'frames': len(ok), 'refused': sum(r.refused for r in reqs),
+            'invalid': sum(r.error is not None for r in reqs),
             'frames_per_s': len(ok) / elapsed if elapsed > 0 else None,
             'p50_ms': pct(50), 'p99_ms': pct(99), 'max_ms': lat[-1] if lat else None,
             'elapsed_s': elapsed}

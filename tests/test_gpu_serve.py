@@ -68,6 +68,34 @@ def test_saturated_mix_batches_and_matches_alone():
         assert np.array_equal(r.planes.planes, ref[(r.stream, r.k)].planes)
 
 
+def test_malformed_requests_are_refused_alone():
+    """Requests that cannot be served -- bad intrinsics, a frame larger than
+    the lanes, a stream that changes its frame size -- are refused with a
+    reason at admission; every other request is served as it is alone."""
+    fr, host = pool()
+    reqs = make_reqs(fr, host, [(s, k, 0.0) for k in range(4) for s in range(4)], 2)
+    big = torch.zeros((8, 4000), dtype=torch.float32).pin_memory()
+    odd = torch.zeros((7, 9), dtype=torch.float32).pin_memory()
+    bad = [Request(0, 100, 0.0, host[0][0], (0.0, 0.0, 1.0, 1.0), frame_idx=100),
+           Request(9, 0, 0.0, big, fr[1][0].cam.intrinsics, frame_idx=0),
+           Request(1, 100, 0.0, odd, fr[1][0].cam.intrinsics, frame_idx=100)]
+    srv = Server(P, budget_bytes=4 << 30, max_batch=8, n_lanes=2, max_w=1280, max_h=720)
+    out = srv.run(reqs + bad, realtime=False)
+    srv.close()
+    assert srv.stats['invalid'] == 3
+    for r in bad:
+        assert r.refused and r.error and r.planes is None
+    assert 'intrinsics' in bad[0].error and 'outside' in bad[1].error
+    assert 'changed its frame size' in bad[2].error
+    good = [r for r in out if r.error is None]
+    assert len(good) == len(reqs) and all(r.planes is not None for r in good)
+    ref = alone(fr, good)
+    for r in good:
+        assert np.array_equal(r.planes.planes, ref[(r.stream, r.k)].planes)
+    s = summarize(out, srv.elapsed)
+    assert s['invalid'] == 3 and s['frames'] == len(reqs)
+
+
 def test_admission_is_bounded_by_the_memory_budget():
     fr, host = pool(2, 1)
     reqs = make_reqs(fr, host, [(s, k, 0.0) for k in range(3) for s in range(2)], 1)
