@@ -428,6 +428,25 @@ def test_batch_and_graph_equal_single_frames():
                 assert torch.equal(labs[i], singles[i].labels)
 
 
+def test_resume_in_a_fresh_context_is_bit_identical():
+    """The only state of a stream is (seed, frame index): a frame processed
+    again in a new context, after other frames went through the old one,
+    gives bit-identical planes and labels."""
+    fr = frame('c2')
+    p = params('c2')
+    d = to_dev(fr.encoded)
+    with Pipeline(p, fr.w, fr.h) as pipe:
+        a = pipe.process_frame(d, fr.cam.intrinsics, frame_idx=41)
+        la = a.labels.cpu().numpy()
+        for i in range(3):
+            pipe.process_frame(to_dev(frame('c2', i + 1).encoded), fr.cam.intrinsics, frame_idx=i)
+    with Pipeline(p, fr.w, fr.h) as pipe:
+        b = pipe.process_frame(d, fr.cam.intrinsics, frame_idx=41)
+        lb = b.labels.cpu().numpy()
+    assert np.array_equal(a.planes.view(np.uint64), b.planes.view(np.uint64))
+    assert np.array_equal(a.hyp_index, b.hyp_index) and np.array_equal(la, lb)
+
+
 def test_host_entry_equals_device_entry():
     fr = frame('c2')
     p = params('c2')
