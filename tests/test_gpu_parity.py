@@ -494,6 +494,20 @@ def test_argument_errors_raise():
             pipe.process_batch([dict(depth=torch.zeros((4, 4), device=DEV), K=(0, 1, 0, 0))])
 
 
+def test_scratch_allocation_failure_is_reported_and_recoverable():
+    """A context whose scratch cannot be allocated (about 22 TB) returns
+    PM_ERR_OOM -- an ordinary allocation failure, nothing launched -- and the
+    device stays usable for the next context."""
+    from paper_2411_01919_b300 import _ffi
+    with pytest.raises(PmError) as ei:
+        Pipeline(Params(iters=2), 16000, 16000, 1024)
+    assert ei.value.status == _ffi.PM_ERR_OOM
+    fr = frame('c1')
+    with Pipeline(params('c1'), fr.w, fr.h) as pipe:
+        r = pipe.process_frame(to_dev(fr.encoded), fr.cam.intrinsics)
+    assert len(r.planes) >= 1
+
+
 def test_misaligned_device_pointers_are_rejected_before_launch():
     """A device buffer not aligned to its element size is refused on the host
     (PM_ERR_ARG) before any kernel could touch it."""
