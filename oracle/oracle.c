@@ -417,7 +417,8 @@ static void draw_indices(uint64_t seed, uint64_t frame_idx, int round, int hyp, 
  *   stop without a plane if the winner has fewer than min_inliers inliers;
  *   label the winner's inliers with r;
  *   refit in FP64 by PCA over the inliers whose normal is valid and within
- *   gate_deg of the hypothesis normal (all inliers if fewer than 3 pass):
+ *   gate_deg of the hypothesis normal, decided in FP32 as |n . h| >= cos of
+ *   the gate angle (all inliers if fewer than 3 pass):
  *   n = eigenvector of the smallest covariance eigenvalue, d = -n . centroid,
  *   oriented towards the camera (d > 0).
  * Outputs: planes[max_planes], labels[w*h] (-1 = none), optional per-round
@@ -440,7 +441,11 @@ int or_ransac(const float *P, const float *N, const unsigned char *valid, int w,
         return -2;
     }
     float thr2 = thr * thr;
-    double cos_gate = cos(gate_deg * M_PI / 180.0);
+    /* the refit gate decides which inliers the refit uses (an integer set),
+     * so it is taken in FP32 with its operations spelled out, like the
+     * inlier test: cos of the gate angle rounded once to FP32, the dot
+     * product of the FP32 normals as fma(nz, hz, fma(ny, hy, nx * hx)) */
+    float cos_gate = (float)cos(gate_deg * M_PI / 180.0);
     for (long i = 0; i < n; ++i)
         labels[i] = -1;
     int n_planes = 0;
@@ -505,9 +510,8 @@ int or_ransac(const float *P, const float *N, const unsigned char *valid, int w,
                 n_in++;
                 int gated = 0;
                 if (N && (valid[i] & 2)) {
-                    double dot = (double)N[i] * pl[0] + (double)N[n + i] * pl[1] +
-                                 (double)N[2 * n + i] * pl[2];
-                    gated = fabs(dot) >= cos_gate;
+                    float dot = fmaf(N[2 * n + i], pl[2], fmaf(N[n + i], pl[1], N[i] * pl[0]));
+                    gated = fabsf(dot) >= cos_gate;
                 }
                 inl[m] = (unsigned char)(1 + gated);
                 n_gate += gated;

@@ -348,6 +348,41 @@ def test_ransac_recovers_single_analytic_plane(n, d):
     assert r.rms[0] < 1e-6
 
 
+def test_ransac_refit_gate_counts_the_normals_within_the_gate():
+    """The refit uses the inliers whose normal is valid and within the gate
+    angle of the hypothesis normal, in either orientation; with fewer than
+    three such inliers it uses them all.  A fronto-parallel plane (every
+    hypothesis normal is exactly (0, 0, +-1)) with per-pixel normals tilted by
+    known angles, none near the 20 degree boundary, fixes the count."""
+    f = synth.plane_frame(40, 30, 35.0, 35.0, 19.5, 14.5, (0.0, 0.0, 1.0), -2.0)
+    P, _, V = oracle.normals(f.depth, f.cam.intrinsics, 0)
+    V = V.copy()
+    h, w = V.shape
+    rng = np.random.default_rng(2)
+    angles = rng.choice([0.0, 7.0, 19.9, 19.99, 20.01, 20.2, 35.0, 89.0, 160.5, 175.0, 180.0],
+                        size=(h, w))
+    N = np.stack([np.zeros((h, w)), np.sin(np.radians(angles)), -np.cos(np.radians(angles))])
+    V |= 2
+    V[rng.random((h, w)) < 0.1] &= 1          # normal invalid: never gated
+    within = (np.minimum(angles, 180.0 - angles) < 20.0) & ((V & 2) > 0)
+    r = oracle.ransac(P.astype(np.float32), N.astype(np.float32), V, 16, 0.01, 1, 50, 3)
+    assert r.n_inliers[0] == h * w
+    assert r.n_refit[0] == int(within.sum())
+    assert abs(r.planes[0, 2] + 1.0) < 1e-12 and abs(r.planes[0, 3] - 2.0) < 1e-6
+    # fewer than three normals within the gate: the refit takes every inlier
+    a2 = np.full((h, w), 45.0)
+    a2[3, 5] = a2[7, 9] = 0.0
+    N2 = np.stack([np.zeros((h, w)), np.sin(np.radians(a2)), -np.cos(np.radians(a2))])
+    r = oracle.ransac(P.astype(np.float32), N2.astype(np.float32), V | 2, 16, 0.01, 1, 50, 3)
+    assert r.n_refit[0] == h * w
+    a2[11, 13] = 180.0                         # a third one, the other way round
+    N2 = np.stack([np.zeros((h, w)), np.sin(np.radians(a2)), -np.cos(np.radians(a2))])
+    r = oracle.ransac(P.astype(np.float32), N2.astype(np.float32), V | 2, 16, 0.01, 1, 50, 3)
+    assert r.n_refit[0] == 3
+    r = oracle.ransac(P.astype(np.float32), N.astype(np.float32), V & 1, 16, 0.01, 1, 50, 3)
+    assert r.n_refit[0] == h * w
+
+
 def test_ransac_recovers_noise_free_staircase():
     rng = np.random.Generator(np.random.PCG64(0))
     cam = synth.make_camera(160, 120, 120.0, 120.0, 80.0, 60.0, [0.0, 0.0, 1.0], 0.0, np.pi / 4)
