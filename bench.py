@@ -41,7 +41,7 @@ SCORE_DRAM_BYTES_PER_PAIR = (152.75e6 + 3.11e6) / 9.73e9   # ncu, k_score round 
 SEGMENT, BOX_TEST_FLOP = 32, 14   # box test: 6 FFMA + 2 FADD
 N_SETS = 4                      # device copies of the batch the timed steps cycle through
 REGION_FLOP_PER_PAIR = 9     # 3 FMA residual, |r| x 2^32, 1 FMA inlier test
-SM_COUNT, FP32_LANES = 148, 128
+FP32_LANES = 128              # FP32 lanes per SM (the derived peak printed beside the measured one)
 
 
 def env_rank():
@@ -68,7 +68,7 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile('w+', suffix='.csv', delete=False)
         try:
             self.p = subprocess.Popen(['nvidia-smi', '-i', str(index), '--query-gpu=' + self.Q,
-                                       '--format=csv,noheader,nounits', '-lms', '100'],
+                                       '--format=csv,noheader,nounits', '-lms', '50'],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -135,9 +135,7 @@ def diffusion_fused(pipe, B, batch, tuned):
             'tiling': list(tuned['best']) if tuned else 'library default',
             'ms_per_batch': ms, 'effective_gbs': eff,
             'note': 'effective: %d iterations x (4 B read + 4 B written) per pixel, which the '
-                    'tiles keep in shared memory; the kernel is FP32-issue bound (ncu: issue '
-                    '84%%, FMA pipe 45%%, XU pipe 19%%, profiles/k_diffuse_tiles_640x480_x32.md)'
-                    % ITERS}
+                    'tiles keep in shared memory; the kernel is FP32-issue bound' % ITERS}
 
 
 def _oracle_worker(job):
@@ -235,17 +233,26 @@ def percentile(xs, q):
     return xs[k]
 
 
-def diffusion_hbm(torch, pm, dev, pk, side=8192, reps=5):
-    """Diffusion with one iteration per launch (streaming kernel) on a side x
-    side FP32 image, 3 iterations: launch 1 reads FP32 depth and writes the
-    compensated (hi, lo) iterate, launch 2 reads and writes the iterate, launch 3
-    reads it and writes FP32 depth: 12 + 16 + 12 = 40 bytes per pixel.  The
-    working set (2 x 8 bytes per pixel at side 8192 = 1.07 GB) is >= 8x L2."""
-    p = pm.Params(iters=3, iters_per_launch=1)
+def diffusion_hbm(torch, pm, dev, pk, side=8192, iters=10, reps=5, dtype='u16'):
+    """Diffusion with one iteration per launch (the streaming kernel, the
+    HBM-bound form) on a side x side depth image in the sensor encoding,
+    `iters` launches.  Algorithmic bytes (the method's own traffic): per pixel
+    and iteration an FP32 iterate read and written (4 + 4 B), plus the first
+    read of the encoding (s = 2 B for u16): px (8 N + s).  Moved bytes (what
+    the kernels read and write): the first launch reads the encoding and
+    writes the lo parts of the compensated iterate (s + 4 B), every later one
+    reads the encoding and the lo parts and writes lo parts or, last, FP32
+    depth (s + 8 B): px (s + 4 + (N - 1)(s + 8)).  The working set (encoding,
+    two lo buffers, output: about 940 MB at 8192^2 u16) is >= 7x L2."""
+    s_in = 2 if dtype == 'u16' else 4
+    p = pm.Params(iters=iters, iters_per_launch=1)
     pipe = pm.Pipeline(p, side, side, 1)
     g = torch.Generator(device=dev).manual_seed(1)
-    z = 1.0 + 0.01 * torch.rand((side, side), generator=g, device=dev)
-    out = torch.empty_like(z)
+    zm = 1.0 + 2.0 * torch.rand((side, side), generator=g, device=dev)
+    zm[torch.rand((side, side), generator=g, device=dev) < 0.02] = 0.0
+    z = ((zm * 1000.0).round().to(torch.int32).to(torch.uint16) if dtype == 'u16'
+         else zm.to(torch.float32))
+    out = torch.empty((side, side), dtype=torch.float32, device=dev)
     s = torch.cuda.current_stream()
     for _ in range(2):
         pipe.diffuse(z, out)
@@ -259,15 +266,24 @@ def diffusion_hbm(torch, pm, dev, pk, side=8192, reps=5):
         ts.append(a.elapsed_time(b))
     pipe.close()
     ms = statistics.median(ts)
-    byts = 40.0 * side * side
-    gbs = byts / (ms * 1e-3) / 1e9
-    return {'kernel': 'k_diffuse_stream (1 iteration per launch, 3 launches)',
-            'image': '%dx%d' % (side, side), 'bytes_per_call': byts,
-            'bytes_per_pixel': '12 + 16 + 12 (FP32 in, float2 iterate, FP32 out)', 'ms': ms,
-            'achieved': gbs, 'peak': pk['hbm_gbs'], 'unit': 'GB/s', 'frac': gbs / pk['hbm_gbs']}
+    px = float(side) * side
+    alg = px * (8.0 * iters + s_in)
+    moved = px * (s_in + 4.0 + (iters - 1) * (s_in + 8.0))
+    gbs = alg / (ms * 1e-3) / 1e9
+    mgbs = moved / (ms * 1e-3) / 1e9
+    return {'kernel': 'k_diffuse_stream (1 iteration per launch, %d launches)' % iters,
+            'image': '%dx%d %s' % (side, side, dtype), 'iterations': iters,
+            'algorithmic_bytes_per_call': alg,
+            'algorithmic_bytes': 'px x (8 N + %d): FP32 iterate read + written per iteration, '
+                                 'encoding read once' % s_in,
+            'moved_bytes_per_call': moved,
+            'moved_bytes': 'px x (%d + (N - 1) x %d): the encoding re-read by every launch (the '
+                           'fixed hi parts), the 4-byte lo parts in and out' % (s_in + 4, s_in + 8),
+            'ms': ms, 'achieved': gbs, 'peak': pk['hbm_gbs'], 'unit': 'GB/s',
+            'frac': gbs / pk['hbm_gbs'], 'moved_gbs': mgbs, 'moved_frac': mgbs / pk['hbm_gbs']}
 
 
-def run_regions(torch, pm, pipe, frames, dframes, pk, n_frames=8, H=256, reps=3):
+def run_regions(torch, pm, pipe, frames, dframes, fp32_peak, n_frames=8, H=256, reps=3):
     """The step after the path, all on the GPU: Canny edges of the normal image,
     the regions they bound, and per-region RANSAC (one model per region) on
     640x480 staircase frames.  Points and normals come from the library's own
@@ -300,8 +316,7 @@ def run_regions(torch, pm, pipe, frames, dframes, pk, n_frames=8, H=256, reps=3)
         accepted += int(out.accepted.sum())
     med = statistics.median
     chain = med(t_edge) + med(t_seg) + med(t_rr)
-    clock_mhz = pk.get('sm_max_mhz', 2032.0)
-    peak = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
+    peak = fp32_peak
     tflops = pairs / n_frames * REGION_FLOP_PER_PAIR / (med(t_rr) * 1e-3) / 1e12
     return {'frames': n_frames, 'regions_per_frame': regions / n_frames,
             'accepted_per_frame': accepted / n_frames, 'hypotheses': H,
@@ -409,6 +424,162 @@ def run_sweep(torch, pm, pk, frames, dframes, flush):
     return out
 
 
+def _score_rate(torch, pm, pipe, batch, fp32_peak, step_ms):
+    """The scoring kernel of one graph-replayed batch: algorithmic work (every
+    hypothesis x candidate pair, 8 FLOP) and executed work (evaluated pairs +
+    box tests) over its summed launch time, against the measured FP32 peak."""
+    pipe.set_timing(2)
+    pipe.process_batch(batch, use_graph=True)
+    pipe.process_batch(batch, use_graph=True)
+    st = pipe.kernel_stats()
+    pipe.set_timing(0)
+    ms = st['score_ms']
+    pairs, ev = st['score_pairs'], st['evaluated_pairs']
+    ach = pairs * FP32_FLOP_PER_PAIR / (ms * 1e-3) / 1e12
+    exe = (ev * FP32_FLOP_PER_PAIR + pairs / SEGMENT * BOX_TEST_FLOP) / (ms * 1e-3) / 1e12
+    return {'kernel': 'k_score', 'achieved': ach, 'frac': ach / fp32_peak, 'executed': exe,
+            'executed_frac': exe / fp32_peak, 'evaluated_share': ev / max(1, pairs),
+            'kernel_ms_per_step': ms, 'share_of_step': ms / step_ms, 'unit': 'TFLOP/s',
+            'peak': fp32_peak}
+
+
+def run_forms(torch, pm, dev, fp32_peak, flush):
+    """The other two configurations the metric's family names, timed on their
+    own.  Precision form: 848x480 FP16 spiral staircase (12 steps of 20 deg,
+    rise 0.17 m), 40 diffusion iterations, 2048 hypotheses x up to 16 planes;
+    16 frames per graph-replayed, autotuned batch, and the plain per-frame
+    path.  Batched form: 64 frames of resolutions drawn from {320x240,
+    640x480, 848x480, 1280x720}, straight or spiral staircases, FP16 depth,
+    20-40 iterations per frame, one graph-replayed autotuned batch per step.
+    Each reports frames/s and the scoring kernel's FP32 rates; one precision
+    frame's outputs are kept for the per-stage comparison with the oracle."""
+    import synth
+    from paper_2411_01919_b300.tune import DiffusionTuner
+    s = torch.cuda.current_stream()
+    workers = min(16, os.cpu_count() or 1)
+
+    def time_batch(pipe, batch, reps=10):
+        for _ in range(3):
+            pipe.process_batch(batch, use_graph=True)
+        ms = []
+        for k in range(reps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            pipe.process_batch(batch, use_graph=True)
+            b.record(s)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    out = {}
+    # precision form
+    n3 = 16
+    f3 = synth.render_many('frame_c3', [(sd,) for sd in range(n3)], workers)
+    d3 = [torch.from_numpy(f.encoded).to(dev) for f in f3]
+    p3 = pm.Params(iters=40, hypotheses=2048, max_planes=16, min_inliers=100, seed=5)
+    b3 = [dict(depth=d3[i], K=f.cam.intrinsics, frame_idx=i) for i, f in enumerate(f3)]
+    with pm.Pipeline(p3, 848, 480, n3) as pipe:
+        tuned = DiffusionTuner().tune(pipe, b3)
+        ms = time_batch(pipe, b3)
+        score = _score_rate(torch, pm, pipe, b3, fp32_peak, ms)
+        # one frame's outputs for the per-stage comparison with the oracle
+        z = torch.empty((480, 848), dtype=torch.float32, device=dev)
+        lab = torch.empty((480, 848), dtype=torch.int16, device=dev)
+        one = [dict(depth=d3[1], K=f3[1].cam.intrinsics, frame_idx=1, depth_out=z, labels=lab)]
+        pl = pipe.process_batch(one, use_graph=False)[0]
+        P, N, V = pipe.frame_geometry(0, 848, 480)
+        sample = dict(frame=f3[1], params=p3, frame_idx=1, depth=z.cpu().numpy(),
+                      P=P.cpu().numpy(), N=N.cpu().numpy(), V=V.cpu().numpy(), planes=pl,
+                      labels=lab.cpu().numpy())
+    with pm.Pipeline(p3, 848, 480, 1) as pipe:
+        for i in range(3):
+            pipe.process_frame(d3[i], f3[i].cam.intrinsics, frame_idx=i, labels=False)
+        lat = []
+        for i in range(n3):
+            t0 = time.perf_counter()
+            pipe.process_frame(d3[i], f3[i].cam.intrinsics, frame_idx=i, labels=False)
+            lat.append(1e3 * (time.perf_counter() - t0))
+        pipe.set_timing(1)
+        st = []
+        for i in range(6):
+            pipe.process_frame(d3[i], f3[i].cam.intrinsics, frame_idx=i, labels=False)
+            st.append(pipe.stage_times())
+    out['precision_848x480_fp16'] = {
+        'batched': {'frames': n3, 'frames_per_s': n3 / (ms * 1e-3), 'ms_per_step': ms,
+                    'tiling': list(tuned['best']), 'score': score},
+        'plain': {'frames_per_s': len(lat) / (sum(lat) * 1e-3), 'p50_ms': percentile(lat, 50),
+                  'p99_ms': percentile(lat, 99),
+                  'stage_ms_median': {k: statistics.median(x[k] for x in st) for k in st[0]}},
+        'config': '848x480 FP16 spiral, 40 iterations, 2048 hypotheses x 16 planes, 1 cm'}
+    out['c3_sample'] = sample
+    # batched form, mixed resolutions
+    f4 = synth.render_many('frame_c4', [(11, i) for i in range(64)], workers)
+    d4 = [torch.from_numpy(f.encoded).to(dev) for f in f4]
+    p4 = pm.Params(iters=30, hypotheses=HYP, max_planes=MAXP, min_inliers=MINI, seed=2)
+    b4 = [dict(depth=d4[i], K=f.cam.intrinsics, frame_idx=i, iters=f.meta['iters'])
+          for i, f in enumerate(f4)]
+    with pm.Pipeline(p4, 1280, 720, 64) as pipe:
+        tuned4 = DiffusionTuner().tune(pipe, b4)
+        ms4 = time_batch(pipe, b4)
+        score4 = _score_rate(torch, pm, pipe, b4, fp32_peak, ms4)
+    res = {}
+    for f in f4:
+        k = '%dx%d' % (f.w, f.h)
+        res[k] = res.get(k, 0) + 1
+    out['batched_mixed_64'] = {
+        'frames': 64, 'frames_per_s': 64 / (ms4 * 1e-3), 'ms_per_step': ms4,
+        'megapixels_per_s': sum(f.w * f.h for f in f4) / (ms4 * 1e-3) / 1e6,
+        'resolutions': res, 'iters': [min(f.meta['iters'] for f in f4),
+                                      max(f.meta['iters'] for f in f4)],
+        'tiling': list(tuned4['best']), 'score': score4,
+        'config': '64 mixed-resolution FP16 frames, 20-40 iterations, 1024 hypotheses x 12 planes'}
+    return out
+
+
+def c3_stage_errors(sample):
+    """The precision form's errors against the FP64 oracle, stage by stage on
+    one frame, each oracle stage fed the GPU's output of the stage before:
+    diffusion (max |z - z_oracle|), points, normals (max angle), and per plane
+    the winner, inlier and refit counts, labels, and the plane's angle and
+    offset."""
+    import oracle
+    fr, p = sample['frame'], sample['params']
+    f32 = lambda x: float(np.float32(x))
+    t0 = time.perf_counter()
+    z = oracle.diffuse(oracle.decode(fr.encoded, fr.dtype, f32(p.depth_scale)), p.iters,
+                       f32(p.lam), f32(p.K), p.mode)
+    dg = sample['depth'].astype(np.float64)
+    Po, No, Vo = oracle.normals(dg, fr.cam.intrinsics, p.stencil)
+    V = sample['V']
+    ok = (V & 2) > 0
+    cosang = np.clip(np.abs(np.sum(sample['N'][:, ok].astype(np.float64) * No[:, ok], axis=0)),
+                     0.0, 1.0)
+    r = oracle.ransac(sample['P'], sample['N'], V, p.hypotheses, p.thr, p.max_planes,
+                      p.min_inliers, p.seed, p.gate_deg, sample['frame_idx'])
+    g = sample['planes']
+    n = min(len(g.planes), len(r.planes))
+    angs = [float(np.degrees(np.arccos(min(1.0, abs(float(g.planes[k, :3] @ r.planes[k, :3]))))))
+            for k in range(n)]
+    offs = [float(abs(g.planes[k, 3] - r.planes[k, 3])) for k in range(n)]
+    return {'frame': 'seed 1 of the precision form (848x480 FP16)',
+            'diffusion_max_abs_m': float(np.abs(dg - z).max()),
+            'diffusion_bar_m': 5e-4,
+            'points_max_abs_m': float(np.abs(sample['P'].astype(np.float64) - Po).max()),
+            'validity_bits_equal': bool(np.array_equal(V, Vo)),
+            'normals_max_deg': float(np.degrees(np.arccos(cosang)).max()) if ok.any() else 0.0,
+            'planes': {'gpu': len(g.planes), 'oracle': len(r.planes),
+                       'winners_equal': bool(np.array_equal(g.hyp_index, r.hyp_index)),
+                       'inlier_counts_equal': bool(np.array_equal(g.n_inliers, r.n_inliers)),
+                       'refit_counts_equal': bool(np.array_equal(g.n_refit, r.n_refit)),
+                       'labels_equal': bool(np.array_equal(sample['labels'], r.labels)),
+                       'max_angle_deg': max(angs) if angs else None,
+                       'max_offset_m': max(offs) if offs else None,
+                       'near_threshold_band': [int(b) for b in r.band]},
+            'oracle_s': time.perf_counter() - t0,
+            'method': 'each oracle stage on the GPU output of the stage before (teacher forcing)'}
+
+
 def run_served(torch, pm, args, c2_frames, c2_dev):
     """The served form: 16 simulated cameras (fixed resolution each from
     424x240 / 640x480 / 848x480 / 1280x720, staircases, camera advancing 5 cm
@@ -480,6 +651,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device('cuda', local)
     pk, pk_kind = peaks()
+    meas = pm.measure_peaks()           # FFMA and ex2 throughput of this device, its SM count
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     B = args.batch
     from paper_2411_01919_b300.shard import max_over_ranks, rank_frame_seeds
     frames = [__import__('synth').frame_c2(sd) for sd in rank_frame_seeds(rank, world, B)]
@@ -602,17 +775,24 @@ def run_ours(args):
              'stage_ms_median': {k: statistics.median(x[k] for x in stage) for k in stage[0]}}
     pipe1.close()
 
-    # end to end: pinned host depth -> device, batch, planes back to host, the
-    # same lanes in turn (a lane's copies run on its stream, so they overlap
-    # the other lanes' batches)
-    # one contiguous pinned batch, one copy per step into the lane's buffer
-    host = torch.from_numpy(np.stack([f.encoded for f in frames])).pin_memory()
-    dbuf = [torch.empty(host.shape, dtype=host.dtype, device=dev) for _ in lanes]
+    # end to end through the C ABI with host buffers: every step hands the
+    # batch's depth in pinned host memory to pm_process_batch_host_async, which
+    # copies each frame to the device on the lane's stream and enqueues the
+    # path; the planes come back to the host with pm_batch_collect.  The same
+    # lanes take the steps in turn, so one lane's copies overlap the others'
+    # batches.
+    host = [torch.from_numpy(f.encoded).pin_memory() for f in frames]
     ne = args.steps
     for lp, _ in lanes:
         lp.set_timing(0)
     pend = [None] * NL
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hb = [dict(depth=host[i], K=K, frame_idx=i) for i in range(B)]
+    for lp, ls in lanes:                       # warm-up of the host entry's graphs
+        with torch.cuda.stream(ls):
+            lp.submit_batch_host(hb, use_graph=True, stream=ls)
+        ls.synchronize()
+        lp.collect_batch()
     torch.cuda.synchronize()
     f0.record(s)
     for _, ls in lanes:
@@ -624,9 +804,7 @@ def run_ours(args):
             pend[li].synchronize()
             lp.collect_batch()
         with torch.cuda.stream(ls):
-            dbuf[li].copy_(host, non_blocking=True)
-            lp.submit_batch([dict(depth=dbuf[li][i], K=K, frame_idx=i) for i in range(B)],
-                            use_graph=True, stream=ls)
+            lp.submit_batch_host(hb, use_graph=True, stream=ls)
         ev = torch.cuda.Event()
         ev.record(ls)
         pend[li] = ev
@@ -639,12 +817,25 @@ def run_ours(args):
             pend[li].synchronize()
             lp.collect_batch()
     f1.synchronize()
-    h2d = host.numel() * host.element_size()
+    h2d = sum(h.numel() * h.element_size() for h in host)
     d2h = B * (64 * 48 + 352)   # planes + per-frame state read back by the call
     e2e = {'value': B * ne / (f0.elapsed_time(f1) * 1e-3), 'unit': 'frames/s',
            'h2d_bytes_per_step': h2d, 'd2h_bytes_per_step': d2h,
-           'api': 'one pinned-host copy of the batch + pm_process_batch_async / pm_batch_collect per '
-                  'step, %d lanes' % NL}
+           'api': 'pm_process_batch_host_async (pinned host depth, copied by the call) + '
+                  'pm_batch_collect per step, %d lanes' % NL}
+    # the plain frame end to end: pm_process_frame_host, host depth in, planes out
+    pipe1 = pm.Pipeline(params, 640, 480, 1)
+    for i in range(3):
+        pipe1.process_frame_host(frames[i].encoded, K, frame_idx=i)
+    lat_h = []
+    for i in range(n_plain):
+        t0 = time.perf_counter()
+        pipe1.process_frame_host(frames[i].encoded, K, frame_idx=i)
+        lat_h.append(1e3 * (time.perf_counter() - t0))
+    pipe1.close()
+    plain['e2e'] = {'value': len(lat_h) / (sum(lat_h) * 1e-3), 'unit': 'frames/s',
+                    'p50_ms': percentile(lat_h, 50), 'p99_ms': percentile(lat_h, 99),
+                    'api': 'pm_process_frame_host (host depth in, planes out), synchronised'}
 
     # roofline: the scoring kernel (FP32 ALU bound).  Algorithmic work = every
     # hypothesis against every candidate, 8 FLOP per pair (3 FFMA for the
@@ -654,7 +845,8 @@ def run_ours(args):
     # (all outside the threshold, or all inside).
     n_score = args.steps * MAXP
     clock_mhz = pk.get('sm_max_mhz', 2032.0)
-    peak_tflops = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
+    derived_tflops = sm_count * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
+    peak_tflops = meas['fp32_tflops']
     tests = score_pairs / SEGMENT
     flop_exec = eval_pairs * FP32_FLOP_PER_PAIR + tests * BOX_TEST_FLOP
     ach = score_pairs * FP32_FLOP_PER_PAIR / (score_ms * 1e-3) / 1e12 if score_ms > 0 else 0.0
@@ -666,8 +858,10 @@ def run_ours(args):
             'traffic_note': 'bytes per launch, scaled from an ncu capture of round 0 of 32 frames '
                             'by pairs scored; algorithmic bytes are 16 B per candidate per '
                             'hypothesis block',
-            'peak_source': 'derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (%s peaks file)'
-                           % (SM_COUNT, FP32_LANES, clock_mhz, pk_kind),
+            'peak_source': 'measured: pm_measure_peaks, an FFMA-only kernel on all %d SMs timed '
+                           'with CUDA events (derived %d SMs x %d lanes x 2 FLOP x %.0f MHz = '
+                           '%.1f TFLOP/s)' % (meas['sm_count'], sm_count, FP32_LANES, clock_mhz,
+                                              derived_tflops),
             'work': 'algorithmic: %d FLOP per hypothesis-candidate pair, %.3e pairs over %d '
                     'launches (H x M per frame and round)'
                     % (FP32_FLOP_PER_PAIR, score_pairs, n_score),
@@ -682,18 +876,30 @@ def run_ours(args):
             'share_of_step': (score_ms / args.steps) / (tot_ms / args.steps) if world == 1 else None}
 
     hbm = diffusion_hbm(torch, pm, dev, pk) if not args.skip_hbm else None
-    regions = run_regions(torch, pm, pipe, frames, dframes, pk) if not args.skip_regions else None
+    hbm_f32 = (diffusion_hbm(torch, pm, dev, pk, dtype='f32', reps=3)
+               if not args.skip_hbm else None)
+    regions = (run_regions(torch, pm, pipe, frames, dframes, peak_tflops)
+               if not args.skip_regions else None)
+    forms = run_forms(torch, pm, dev, peak_tflops, flush) if not args.skip_forms else None
     sweep = run_sweep(torch, pm, pk, frames, dframes, flush) if not args.skip_sweep else None
     served = run_served(torch, pm, args, frames, dframes) if args.served_seconds > 0 else None
 
     cpu = cpu_all = None
     if rank == 0 and not args.skip_cpu:
-        sec, stages = oracle_frame_stages(frames[0], 0)
+        runs = [oracle_frame_stages(frames[i], i) for i in range(args.cpu_frames)]
+        secs = [r[0] for r in runs]
+        sec = statistics.median(secs)
+        stages = {k: statistics.median(r[1][k] for r in runs) for k in runs[0][1]}
         cpu = {'value': 1.0 / sec, 'unit': 'frames/s', 'cores': 1, 'kind': 'oracle',
-               'host': host_cpu_model(), 'stages_s': stages,
-               'sample': '1 of the %d frames of a step, single-threaded C oracle (%.1f s)'
-                         % (B, sec)}
+               'host': host_cpu_model(), 'stages_s_median': stages,
+               'sample': 'median of %d of the %d frames of a step, single-threaded C oracle '
+                         '(%.1f-%.1f s per frame)' % (len(secs), B, min(secs), max(secs))}
         cpu_all = oracle_all_cores(frames)
+        if forms is not None and forms.get('c3_sample') is not None:
+            forms['precision_848x480_fp16']['errors_vs_oracle'] = c3_stage_errors(
+                forms['c3_sample'])
+    if forms is not None:
+        forms.pop('c3_sample', None)
 
     line = {'metric': METRIC, 'value': value, 'unit': 'frames/s', 'n_gpus': world,
             'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': tot_ms / args.steps,
@@ -712,8 +918,13 @@ def run_ours(args):
                            'note': 'submit to collect of a step (%d steps in flight); a batched '
                                    'frame completes with its step' % NL},
             'plain': plain, 'speedup_vs_plain': value / world / plain['value'],
+            'served_capacity_vs_plain': (served['capacity_640x480']['frames_per_s'] / plain['value']
+                                         if served else None),
             'served': served, 'regions': regions, 'sweep': sweep,
-            'e2e': e2e, 'roofline': roof, 'diffusion_hbm': hbm, 'diffusion_fused': fused,
+            'e2e': e2e, 'roofline': roof, 'diffusion_hbm': hbm, 'diffusion_hbm_f32': hbm_f32,
+            'diffusion_fused': fused, 'forms': forms,
+            'measured_peaks': dict(meas, how='pm_measure_peaks: FFMA-only and ex2-only kernels on '
+                                             'every SM, CUDA events, device clocks as found'),
             'cpu_baseline': cpu, 'cpu_baseline_all_cores': cpu_all,
             'gpu_launches': launches, 'clocks': clk,
             'paper_context': '>30 Hz whole pipeline; 7.5 ms/frame; <15 ms at 640x480 with 10 '
@@ -725,6 +936,46 @@ def run_ours(args):
         lp.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_case(args):
+    """One small workload for a profiler capture (no JSON line): the kernel
+    named by --case on the given image / batch, `--steps` calls after
+    `--warmup` calls.
+      stream-u16 / stream-f32: 8192 x 8192 depth, 4 iterations, one per launch
+      tiles-640x480x64: the fused diffusion of the 64-frame 640x480 batch
+      path-640x480x32: the whole path over 32 frames of the 640x480 workload"""
+    import torch
+    import paper_2411_01919_b300 as pm
+    import synth
+    dev = torch.device('cuda', 0)
+    torch.cuda.set_device(0)
+    if args.case.startswith('stream-'):
+        side = 8192
+        g = torch.Generator(device=dev).manual_seed(1)
+        zm = 1.0 + 2.0 * torch.rand((side, side), generator=g, device=dev)
+        zm[torch.rand((side, side), generator=g, device=dev) < 0.02] = 0.0
+        z = ((zm * 1000.0).round().to(torch.int32).to(torch.uint16) if args.case == 'stream-u16'
+             else zm.to(torch.float32))
+        out = torch.empty((side, side), dtype=torch.float32, device=dev)
+        with pm.Pipeline(pm.Params(iters=4, iters_per_launch=1), side, side, 1) as pipe:
+            for _ in range(args.warmup + args.steps):
+                pipe.diffuse(z, out)
+            torch.cuda.synchronize()
+        return 0
+    n = 64 if args.case == 'tiles-640x480x64' else 32
+    frames = [synth.frame_c2(sd) for sd in range(n)]
+    d = [torch.from_numpy(f.encoded).to(dev) for f in frames]
+    K = frames[0].cam.intrinsics
+    p = pm.Params(iters=ITERS, hypotheses=HYP, thr=THR, max_planes=MAXP, min_inliers=MINI, seed=0)
+    with pm.Pipeline(p, 640, 480, n) as pipe:
+        if args.tiling:
+            pipe.set_tiling(*(int(v) for v in args.tiling.split(',')))
+        batch = [dict(depth=d[i], K=K, frame_idx=i) for i in range(n)]
+        for _ in range(args.warmup + args.steps):
+            pipe.process_batch(batch, use_graph=False)
+        torch.cuda.synchronize()
     return 0
 
 
@@ -740,16 +991,25 @@ def main():
     ap.add_argument('--skip-hbm', action='store_true')
     ap.add_argument('--skip-regions', action='store_true')
     ap.add_argument('--skip-sweep', action='store_true')
+    ap.add_argument('--skip-forms', action='store_true')
+    ap.add_argument('--cpu-frames', type=int, default=5,
+                    help='frames of the single-core oracle baseline (the median is reported)')
     ap.add_argument('--lanes', type=int, default=3,
                     help='pipelines taking the timed batches in turn (batches in flight)')
     ap.add_argument('--no-tune', action='store_true')
     ap.add_argument('--tiling', default='',
                     help='diffusion tiling T,tile_w,tile_h instead of autotuning (e.g. 8,80,48)')
     ap.add_argument('--served-seconds', type=float, default=60.0)
+    ap.add_argument('--case', default='',
+                    choices=['', 'stream-u16', 'stream-f32', 'tiles-640x480x64',
+                             'path-640x480x32'],
+                    help='run one small workload for a profiler capture instead of the benchmark')
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == 'ours':
         print('note: raising --warmup to 3 (timing rule)', file=sys.stderr)
         args.warmup = 3
+    if args.case:
+        return run_case(args)
     if args.impl == 'reference':
         return run_reference(args)
     return run_ours(args)

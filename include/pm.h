@@ -85,7 +85,10 @@ typedef struct {
  * refit_normal_gate_deg of the hypothesis normal, and repeats on the points
  * not yet labelled.  It stops after max_planes planes or when the best
  * hypothesis has fewer than min_inliers inliers (min_inliers >= 3).
- * hypotheses must lie in [1, 2048]; max_planes in [1, 64]. */
+ * hypotheses must lie in [1, 2048]; max_planes in [1, 64].  The gate test
+ * is |n_p . n_h| >= cos(gate) in FP32 (n_p the pixel's normal, n_h the
+ * hypothesis normal).  Alg. 2's own selection rule (minimum total distance)
+ * and 0.9 acceptance ratio are per polygon and belong to pm_ransac_regions. */
 typedef struct {
     int hypotheses;
     float thr_m;
@@ -136,9 +139,14 @@ typedef struct {
 typedef struct pm_ctx pm_ctx;
 
 /* Create a context on the current CUDA device whose scratch holds up to
- * `max_frames` frames of at most max_w x max_h pixels each.  The parameters
- * are copied.  Returns PM_ERR_ARG for out-of-range parameters, PM_ERR_OOM if
- * the scratch cannot be allocated.  *out is set only on success. */
+ * `max_frames` frames of at most max_w x max_h pixels each, plus the scratch
+ * of the edge and region passes (pm_canny, pm_segment) for one such image and
+ * of per-region RANSAC (pm_ransac_regions) for up to 256 regions at
+ * rp->hypotheses hypotheses: all of it is allocated here, so no later call
+ * allocates device memory except pm_ransac_regions beyond those 256 regions
+ * (pm_scratch_bytes gives the total).  The parameters are copied.  Returns
+ * PM_ERR_ARG for out-of-range parameters, PM_ERR_OOM if the scratch cannot be
+ * allocated.  *out is set only on success. */
 pm_status pm_create(const pm_diffusion_params *dp, const pm_ransac_params *rp,
                     const pm_misc_params *mp, int max_w, int max_h, int max_frames,
                     pm_ctx **out);
@@ -209,6 +217,29 @@ pm_status pm_process_batch_async(pm_ctx *ctx, const pm_frame *frames, int n, int
                                  void *stream);
 pm_status pm_batch_collect(pm_ctx *ctx, pm_plane *planes, int *n_planes, int n);
 
+/* As pm_process_batch_async, with every frame's depth in HOST memory (pinned
+ * memory makes the copies asynchronous; pageable memory is copied before the
+ * call returns): the call copies frame f into the context's input staging on
+ * `stream` and enqueues the batch after the copies.  labels and depth_out
+ * are device pointers or NULL as in pm_frame.  Pinned host buffers must stay
+ * unchanged until the batch completes; collect with pm_batch_collect. */
+pm_status pm_process_batch_host_async(pm_ctx *ctx, const pm_frame *frames, int n, int use_graph,
+                                      void *stream);
+
+/* What the RANSAC stage (Alg. 2) of the context's last whole-path call
+ * (pm_process_frame, pm_process_frame_host, pm_process_batch,
+ * pm_process_batch_async or pm_process_batch_host_async) consumed for frame `frame` of its batch: the
+ * back-projected points and unit normals of Eq. 2 (device float SoA
+ * [3][h*w] each) and the validity bytes (device uint8 [h*w]; bits as in
+ * pm_normals), w x h being that frame's size.  It lets a caller check each
+ * stage of the path on the previous stage's own output.  Any output may be
+ * NULL.  Device-to-device copies, asynchronous on `stream`; the data stays
+ * valid until the next whole-path call on the context.  PM_ERR_ARG if the
+ * last whole-path call had no such frame, PM_ERR_STATE while an asynchronous
+ * batch is pending (collect it first). */
+pm_status pm_frame_geometry(pm_ctx *ctx, int frame, float *points, float *normals,
+                            unsigned char *valid, void *stream);
+
 /* Per-region RANSAC in the literal form of Alg. 2 (Sec. III-D): one plane
  * model per region (e.g. a polygon of the paper's contour step).  For region r
  * (regions[p] == r, device int32 [h*w]; values outside [0, n_regions) and
@@ -225,7 +256,13 @@ pm_status pm_batch_collect(pm_ctx *ctx, pm_plane *planes, int *n_planes, int n);
  * out: host [n_regions] (n, d: the winning FP32 hypothesis plane, not refit;
  * hyp_index = -1 when the region has fewer than 3 points or no usable
  * hypothesis).  n_regions in [1, 65535] and n_regions * hypotheses <= 2^22.
- * Uses the context's seed and threshold; synchronises `stream`. */
+ * Uses the context's seed and threshold; synchronises `stream`.  The scratch
+ * pm_create allocated covers 256 regions at the context's hypothesis count; a
+ * larger call grows it (a device allocation), except while `stream` is being
+ * captured, when it returns PM_ERR_STATE: make one call of that size first.
+ * This is where the literal selection rule of Alg. 2 (minimum total
+ * distance) and its 0.9 inlier-ratio acceptance live; the whole-frame form
+ * (pm_ransac_planes) takes the winner by inlier count. */
 typedef struct {
     double n[3];
     double d;
@@ -351,24 +388,40 @@ pm_status pm_stage_times(pm_ctx *ctx, float ms[3]);
 pm_status pm_kernel_stats(pm_ctx *ctx, float *score_ms, long long *score_pairs,
                           long long *evaluated_pairs, int *score_launches, long long *launches);
 
+/* Measured throughput of the two CUDA-core pipes the path's kernels run on,
+ * the denominators of their roofline fractions: *fp32_tflops, FP32 fused
+ * multiply-adds at 2 FLOP each (the inlier test of Eq. 3 is three FMAs and
+ * one squared-threshold FMA per point), and *ex2_tops, the special-function
+ * unit's ex2 (the conductance exp(-(x/K)^2) of Eq. 1); *sm_count, the
+ * device's multiprocessors.  Each is timed with CUDA events on a kernel that
+ * issues only that instruction, in independent chains, on every SM at full
+ * occupancy (about 0.15 s in all, synchronising `stream`), at whatever
+ * clocks the device runs; no device setting is read or changed.  Any output
+ * may be NULL. */
+pm_status pm_measure_peaks(double *fp32_tflops, double *ex2_tops, int *sm_count, void *stream);
+
 /* Allocation-free diffusion.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc, e.g. a hard real-time
  * control loop (cudaMalloc and cudaFree can synchronise the whole device and
  * take unbounded time) or a plug-in running inside a host framework whose own
  * allocator owns the device memory.  It needs no pm_ctx and allocates nothing:
  * the caller passes the input and the output, and the library keeps the
- * compensated iterate in a fixed array of device memory that every GPU which
- * loads libpm holds until the process exits (2 x PM_NOALLOC_MAX_PIXELS x 8
+ * iterate (the lo parts of the compensated depth; the hi parts are decoded
+ * from the input) in a fixed array of device memory that every GPU which
+ * loads libpm holds until the process exits (2 x PM_NOALLOC_MAX_PIXELS x 4
  * bytes = 8 MiB).  Same arguments and result as pm_diffuse with
  * iters_per_launch = 1 (dp->iters_per_launch is ignored); w * h above
  * PM_NOALLOC_MAX_PIXELS returns PM_ERR_ARG.  The first call on a device looks
  * up the array's device address (with that device current); make that first
- * call before any stream capture.  All calls share the one array: calls whose
+ * call before any stream capture.  The address is kept per device and CUDA
+ * context: after cudaDeviceReset (or anything else that replaces the
+ * device's context) the next call looks it up again, so that call, too,
+ * belongs before any capture.  All calls share the one array: calls whose
  * GPU work overlaps (on different streams, or from different host threads
  * without ordering) race and corrupt each other's results.  Every pixel of
  * the array that a call reads was written earlier in the same call, so no
  * state carries over from one call to the next. */
-#define PM_NOALLOC_MAX_PIXELS (1 << 19)
+#define PM_NOALLOC_MAX_PIXELS (1 << 20)
 pm_status pm_diffuse_noalloc(const void *depth, int dtype, int w, int h, int pitch,
                              const pm_diffusion_params *dp, float depth_scale, float *out,
                              void *stream);

@@ -11,7 +11,7 @@ PM_OK, PM_ERR_ARG, PM_ERR_OOM, PM_ERR_CUDA, PM_ERR_TIMEOUT, PM_ERR_STATE = range
 STATUS = {0: 'PM_OK', 1: 'PM_ERR_ARG', 2: 'PM_ERR_OOM', 3: 'PM_ERR_CUDA', 4: 'PM_ERR_TIMEOUT',
           5: 'PM_ERR_STATE'}
 PM_U16_MM, PM_F16_M, PM_F32_M = 0, 1, 2
-PM_NOALLOC_MAX_PIXELS = 1 << 19
+PM_NOALLOC_MAX_PIXELS = 1 << 20
 
 
 class Intrinsics(ctypes.Structure):
@@ -74,10 +74,12 @@ class Frame(ctypes.Structure):
 
 EXPORTS = ['pm_create', 'pm_destroy', 'pm_diffuse', 'pm_normals', 'pm_ransac_planes',
            'pm_process_frame', 'pm_process_frame_host', 'pm_process_batch',
-           'pm_process_batch_async', 'pm_batch_collect', 'pm_scratch_bytes', 'pm_set_timing',
+           'pm_process_batch_async', 'pm_process_batch_host_async', 'pm_batch_collect',
+           'pm_frame_geometry',
+           'pm_scratch_bytes', 'pm_set_timing',
            'pm_stage_times', 'pm_kernel_stats', 'pm_ransac_regions', 'pm_canny', 'pm_segment',
            'pm_map_create', 'pm_map_destroy', 'pm_map_integrate', 'pm_map_size',
-           'pm_map_polygon', 'pm_map_drift', 'pm_diffuse_noalloc',
+           'pm_map_polygon', 'pm_map_drift', 'pm_diffuse_noalloc', 'pm_measure_peaks',
            'pm_set_tiling', 'pm_last_error']
 
 _lib = None
@@ -111,7 +113,9 @@ def load(path: str = LIB_PATH):
                                    vp], i),
         'pm_process_batch': ([vp, P(Frame), i, P(Plane), P(i), i, vp], i),
         'pm_process_batch_async': ([vp, P(Frame), i, i, vp], i),
+        'pm_process_batch_host_async': ([vp, P(Frame), i, i, vp], i),
         'pm_batch_collect': ([vp, P(Plane), P(i), i], i),
+        'pm_frame_geometry': ([vp, i, vp, vp, vp, vp], i),
         'pm_scratch_bytes': ([i, i, i, i, i], ctypes.c_longlong),
         'pm_set_timing': ([vp, i], i),
         'pm_stage_times': ([vp, P(ctypes.c_float)], i),
@@ -127,6 +131,7 @@ def load(path: str = LIB_PATH):
         'pm_map_polygon': ([vp, i, P(ctypes.c_double), P(ctypes.c_double), P(i), vp, i, P(i)], i),
         'pm_map_drift': ([vp, P(ctypes.c_double), P(ctypes.c_double)], i),
         'pm_diffuse_noalloc': ([vp, i, i, i, i, P(DiffusionParams), ctypes.c_float, vp, vp], i),
+        'pm_measure_peaks': ([P(ctypes.c_double), P(ctypes.c_double), P(i), vp], i),
         'pm_set_tiling': ([vp, i, i, i], i),
         'pm_last_error': ([], ctypes.c_char_p),
     }

@@ -8,7 +8,7 @@ CSRC = os.path.join(HERE, 'csrc')
 LIB = os.path.join(HERE, 'libpm.so')
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 SOURCES = ['pm_api.cu', 'diffuse.cu', 'normals.cu', 'ransac.cu', 'regions.cu', 'canny.cu',
-           'noalloc.cu', 'map.cpp']
+           'noalloc.cu', 'peak.cu', 'map.cpp']
 
 
 def _nvcc():

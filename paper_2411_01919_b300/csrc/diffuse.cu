@@ -14,6 +14,11 @@
 // by less than a factor of two) and add the lo parts.  The output is hi + lo
 // rounded once.  All arithmetic stays on the FP32 pipes.
 //
+// Because hi is the decoded input, a launch decodes it again from the sensor
+// encoding (2 bytes per pixel for u16 / f16, 4 for f32) and only the 4-byte lo
+// parts pass from one launch to the next: a middle launch of a u16 frame
+// moves 2 + 4 bytes in and 4 out per pixel.
+//
 // Two kernels share one per-pixel update (so their results are bit-identical):
 //  * k_diffuse_tiles: temporal blocking.  A CTA loads a (dx+2T) x (dy+2T) tile
 //    with a T-pixel halo into shared memory, runs T Jacobi iterations there on
@@ -21,13 +26,12 @@
 //    frame of a batch form one grid (a frame table maps tile -> frame).
 //  * k_diffuse_stream: one iteration per launch over one frame, one pass over
 //    HBM.
-// Holes and pixels outside the image hold the sentinel HOLE = 1e30 in the
-// iterate: across a link to it the difference x is about 1e30, x*x overflows
-// to +inf, 2^(x*x*c) is exactly +0 and so is the flux g(x) x -- the ghost rule
+// Holes and pixels outside the image hold the sentinel HOLE = 1e30 as hi:
+// across a link to it the difference x is about 1e30, x*x overflows to +inf,
+// 2^(x*x*c) is exactly +0 and so is the flux g(x) x -- the ghost rule
 // J_q = I_p of the oracle (no flux across a hole or the border) without a
-// branch; a hole receives only zero fluxes and keeps its value.  The first
-// launch decodes the sensor encoding on the fly (holes -> HOLE); the last
-// writes FP32 depth (hi + lo rounded to nearest; HOLE -> 0).
+// branch; a hole receives only zero fluxes and keeps its value.  The last
+// launch writes FP32 depth (hi + lo rounded to nearest; HOLE -> 0).
 #include "pm_internal.cuh"
 
 namespace pm {
@@ -64,13 +68,12 @@ __device__ __forceinline__ float link_flux(float2 Ip, float2 Iq, float c)
     return __fmul_rn(g, x);
 }
 
-// mode 0 (PM4): I' = I + lambda * (((f_N + f_S) + f_W) + f_E)
-__device__ __forceinline__ float2 update_pm4(float2 Ip, float2 In, float2 Is, float2 Iw,
-                                             float2 Ie, float lam, float c)
+// PM4 update from the four link fluxes: I' = I + lambda * (((f_N + f_S) + f_W)
+// + f_E) (a HOLE pixel receives only zero fluxes and keeps its value).
+__device__ __forceinline__ float2 pm4_combine(float2 Ip, float fN, float fS, float fW, float fE,
+                                              float lam)
 {
-    const float s = __fadd_rn(__fadd_rn(__fadd_rn(link_flux(Ip, In, c), link_flux(Ip, Is, c)),
-                                        link_flux(Ip, Iw, c)), link_flux(Ip, Ie, c));
-    return pair_add(Ip, __fmul_rn(lam, s));
+    return pair_add(Ip, __fmul_rn(lam, __fadd_rn(__fadd_rn(__fadd_rn(fN, fS), fW), fE)));
 }
 
 // mode 1 (ALG1): c_p from the central-difference gradient of the ghosted
@@ -91,37 +94,42 @@ __device__ __forceinline__ float2 update_alg1(float2 Ip, float2 In, float2 Is, f
     return pair_add(Ip, __fmul_rn(__fmul_rn(lam, cp), lap));
 }
 
-template <int MODE>
-__device__ __forceinline__ float2 update(float2 Ip, float2 In, float2 Is, float2 Iw, float2 Ie,
-                                         float lam, float c)
+// ---------------------------------------------------------------------------
+// the sensor encoding: each pixel read as a 32-bit container (the u16 code,
+// the f16 bits or the f32 bits); a pixel outside the image reads as 0, which
+// decodes to a hole in every encoding
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned load_raw(const DiffFrame &f, int x, int y)
 {
-    return MODE == 0 ? update_pm4(Ip, In, Is, Iw, Ie, lam, c)
-                     : update_alg1(Ip, In, Is, Iw, Ie, lam, c);
+    const char *row = (const char *)f.src + (long long)y * f.src_pitch;
+    if (f.src_dtype == PM_F32_M)
+        return __float_as_uint(__ldg(reinterpret_cast<const float *>(row) + x));
+    return __ldg(reinterpret_cast<const unsigned short *>(row) + x);
 }
 
-// Source pixel -> compensated metres; holes (0, negative, non-finite) -> HOLE.
-// u16: q * scale split exactly (q has at most 16 significant bits, so the
-// product fits in 40 bits and the fused multiply-add returns its exact tail).
-__device__ __forceinline__ float2 load_px(const void *src, int dtype, long long pitch, int x,
-                                          int y, float scale)
+// Raw container -> (hi, decode tail); holes (0, negative, non-finite) ->
+// (HOLE, 0).  u16: q * scale split exactly (q has at most 16 significant
+// bits, so the product fits in 40 bits and the fused multiply-add returns its
+// exact tail).
+template <int DT>
+__device__ __forceinline__ float2 decode(unsigned r, float scale)
 {
-    const char *row = (const char *)src + (long long)y * pitch;
-    float v;
-    if (dtype == SRC_PAIR) {
-        return __ldg((const float2 *)row + x);
-    } else if (dtype == PM_U16_MM) {
-        const unsigned short q = __ldg((const unsigned short *)row + x);
-        if (!q)
+    if (DT == PM_U16_MM) {
+        if (!r)
             return make_float2(HOLE, 0.0f);
-        const float qf = (float)q;
+        const float qf = (float)r;
         const float hi = __fmul_rn(qf, scale);
         return make_float2(hi, __fmaf_rn(qf, scale, -hi));
-    } else if (dtype == PM_F16_M) {
-        v = __half2float(__ldg((const __half *)row + x));
-    } else {
-        v = __ldg((const float *)row + x);
     }
+    const float v = DT == PM_F16_M ? __half2float(__ushort_as_half((unsigned short)r))
+                                   : __uint_as_float(r);
     return make_float2((v > 0.0f && v < __int_as_float(0x7f800000)) ? v : HOLE, 0.0f);
+}
+
+__device__ __forceinline__ float2 decode_rt(unsigned r, int dt, float scale)
+{
+    return dt == PM_U16_MM ? decode<PM_U16_MM>(r, scale)
+         : dt == PM_F16_M ? decode<PM_F16_M>(r, scale) : decode<PM_F32_M>(r, scale);
 }
 
 __device__ __forceinline__ float depth_out(float2 v)
@@ -129,29 +137,18 @@ __device__ __forceinline__ float depth_out(float2 v)
     return v.x == HOLE ? 0.0f : __fadd_rn(v.x, v.y);
 }
 
-__device__ __forceinline__ void store_px(const DiffFrame &f, long long i, float2 v)
-{
-    if (f.dst_pair)
-        reinterpret_cast<float2 *>(f.dst)[i] = v;
-    else
-        reinterpret_cast<float *>(f.dst)[i] = depth_out(v);
-}
+// ---------------------------------------------------------------------------
+// temporal blocking
+// ---------------------------------------------------------------------------
 
-// PM4 update from the four link fluxes, in the order of update_pm4 (a HOLE
-// pixel receives only zero fluxes and keeps its value).
-__device__ __forceinline__ float2 pm4_combine(float2 Ip, float fN, float fS, float fW, float fE,
-                                              float lam)
-{
-    return pair_add(Ip, __fmul_rn(lam, __fadd_rn(__fadd_rn(__fadd_rn(fN, fS), fW), fE)));
-}
-
-// Temporal blocking.  Block = 32 x 8 threads; tile = dx x dy output pixels
-// with a T-pixel halo, (dx + 2T) x (dy + 2T) cells in shared memory: the hi
-// parts once (they never change), the lo parts in two buffers (12 bytes per
-// cell).  Iteration it updates the region shrunk by it + 1 on every side.  Each warp (one threadIdx.y) walks a band of rows top to bottom for
-// its columns (lane, lane + 32, ...): the south link flux of a row is the
-// negated north link flux of the next row (exactly, see link_flux), so each
-// pixel evaluates three links (N reused) instead of four.
+// Block = 32 x 8 threads; tile = dx x dy output pixels with a T-pixel halo,
+// (dx + 2T) x (dy + 2T) cells in shared memory: the hi parts once (they never
+// change), the lo parts in two buffers (12 bytes per cell).  Iteration it
+// updates the region shrunk by it + 1 on every side.  Each warp (one
+// threadIdx.y) walks a band of rows top to bottom for its columns (lane,
+// lane + 32, ...): the south link flux of a row is the negated north link flux
+// of the next row (exactly, see link_flux), so each pixel evaluates three
+// links (N reused) instead of four.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restrict__ frames,
                                                        int n_frames, int T, int dx, int dy,
@@ -177,32 +174,25 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
     float *B = sm1 + 2 * NC;     // lo parts it writes
     const int lane = threadIdx.x, wy = threadIdx.y;
 
-    if (f.src_dtype == SRC_PAIR || f.src_dtype == PM_U16_MM) {
-        // the iterate of the previous launch, or the u16 encoding (decoded on
-        // the store): per warp two rows of 96 cells in flight before any
-        // shared-memory store
+    // the tile with its halo: per warp two rows of 96 cells (encoding and lo
+    // parts) in flight before any shared-memory store
+    {
         constexpr int G = 3;
-        const bool pair = f.src_dtype == SRC_PAIR;
-        const float2 hole = make_float2(HOLE, 0.0f);
+        const bool has_lo = f.lo_in != nullptr;
         for (int y0 = wy; y0 < SY; y0 += 16) {
             for (int x0 = 0; x0 < SX; x0 += 32 * G) {
-                float2 v[2][G];
+                unsigned rv[2][G];
+                float lv[2][G];
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
                     const int y = y0 + 8 * r, gy = ty0 - T + y;
                     const bool row_ok = y < SY && gy >= 0 && gy < f.h;
-                    const char *row = (const char *)f.src + (long long)(row_ok ? gy : 0) * f.src_pitch;
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
                         const int x = x0 + lane + 32 * g, gx = tx0 - T + x;
                         const bool ok = row_ok && x < SX && gx >= 0 && gx < f.w;
-                        if (pair) {
-                            v[r][g] = ok ? __ldg(reinterpret_cast<const float2 *>(row) + gx) : hole;
-                        } else {
-                            const unsigned short q =
-                                ok ? __ldg(reinterpret_cast<const unsigned short *>(row) + gx) : 0;
-                            v[r][g].x = __int_as_float((int)q);   // the raw code, decoded below
-                        }
+                        rv[r][g] = ok ? load_raw(f, gx, gy) : 0u;
+                        lv[r][g] = ok && has_lo ? __ldg(f.lo_in + (long long)gy * f.w + gx) : 0.0f;
                     }
                 }
 #pragma unroll
@@ -212,30 +202,12 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
                     for (int g = 0; g < G; ++g) {
                         const int x = x0 + lane + 32 * g;
                         if (y < SY && x < SX) {
-                            float2 w = v[r][g];
-                            if (!pair) {
-                                const int q = __float_as_int(w.x);
-                                const float qf = (float)q;
-                                const float h = __fmul_rn(qf, f.scale);
-                                w = q ? make_float2(h, __fmaf_rn(qf, f.scale, -h)) : hole;
-                            }
-                            Hs[y * SX + x] = w.x;
-                            A[y * SX + x] = w.y;
+                            const float2 v = decode_rt(rv[r][g], f.src_dtype, f.scale);
+                            Hs[y * SX + x] = v.x;
+                            A[y * SX + x] = has_lo ? lv[r][g] : v.y;
                         }
                     }
                 }
-            }
-        }
-    } else {
-        for (int y = wy; y < SY; y += 8) {
-            const int gy = ty0 - T + y;
-            for (int x = lane; x < SX; x += 32) {
-                const int gx = tx0 - T + x;
-                float2 v = make_float2(HOLE, 0.0f);
-                if (gx >= 0 && gx < f.w && gy >= 0 && gy < f.h)
-                    v = load_px(f.src, f.src_dtype, f.src_pitch, gx, gy, f.scale);
-                Hs[y * SX + x] = v.x;
-                A[y * SX + x] = v.y;
             }
         }
     }
@@ -297,143 +269,448 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
             const int gx = tx0 + x;
             const int k = (y + T) * SX + x + T;
             if (gx < f.w)
-                store_px(f, (long long)gy * f.w + gx, make_float2(Hs[k], A[k]));
+                f.dst[(long long)gy * f.w + gx] =
+                    f.dst_lo ? A[k] : depth_out(make_float2(Hs[k], A[k]));
         }
     }
 }
 
-// Source pixel of a launch whose encoding SRC is known at compile time.
-template <int SRC>
-__device__ __forceinline__ float2 load_src(const DiffFrame &f, int x, int y)
+// ---------------------------------------------------------------------------
+// temporal blocking in registers (mode PM4)
+// ---------------------------------------------------------------------------
+
+// Packed pairs of FP32 values: one 64-bit register pair, low word first.  The
+// sm_100-family f32x2 instructions round each half exactly as the scalar
+// instruction does, so a packed update is bit-identical to two scalar ones.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float a, float b)
 {
-    const char *row = (const char *)f.src + (long long)y * f.src_pitch;
-    if (SRC == SRC_PAIR)
-        return __ldg((const float2 *)row + x);
-    return load_px(f.src, SRC, f.src_pitch, x, y, f.scale);
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 unpk(f2 v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ float lo_of(f2 v) { return unpk(v).x; }
+__device__ __forceinline__ float hi_of(f2 v) { return unpk(v).y; }
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 neg2(f2 a) { return a ^ 0x8000000080000000ull; }
+// a b rounded once, for a product that feeds an addition: computed as
+// fma(a, b, -0), which equals the rounded product exactly (an exact product
+// plus -0 is itself) and leaves no separate multiply for the compiler to fuse
+// into the addition that follows (one rounding instead of two).
+__device__ __forceinline__ f2 mulr2(f2 a, f2 b)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(0x8000000080000000ull));
+    return r;
 }
 
-// Two horizontally adjacent pixels (x even) in one access where the row
-// pitch and the base pointer allow it: 16 bytes for the float2 iterate, 8 for
-// FP32.
-template <int SRC>
-__device__ __forceinline__ void load_src2(const DiffFrame &f, int x, int y, bool vec, float2 &a,
-                                          float2 &b)
+// Two link fluxes at once, each exactly link_flux(p, q) of its half:
+// x = (hi_q - hi_p) + (lo_q - lo_p), g = 2^(x x c), flux g x.
+__device__ __forceinline__ f2 link_flux2(f2 ph, f2 pl, f2 qh, f2 ql, f2 c2)
 {
-    const char *row = (const char *)f.src + (long long)y * f.src_pitch;
-    if (SRC == SRC_PAIR && vec) {
-        const float4 v = __ldg((const float4 *)row + (x >> 1));
-        a = make_float2(v.x, v.y);
-        b = make_float2(v.z, v.w);
-        return;
-    }
-    if (SRC == PM_F32_M && vec) {
-        const float2 v = __ldg((const float2 *)row + (x >> 1));
-        const float inf = __int_as_float(0x7f800000);
-        a = make_float2((v.x > 0.0f && v.x < inf) ? v.x : HOLE, 0.0f);
-        b = make_float2((v.y > 0.0f && v.y < inf) ? v.y : HOLE, 0.0f);
-        return;
-    }
-    a = load_src<SRC>(f, x, y);
-    b = load_src<SRC>(f, x + 1, y);
+    const f2 x = add2(sub2(qh, ph), sub2(ql, pl));
+    const f2 t = mul2(mul2(x, x), c2);
+    return mulr2(pk(ex2_approx(lo_of(t)), ex2_approx(hi_of(t))), x);
 }
 
-// One iteration over one frame, one pass over HBM.  Block = 32 x 8 threads;
-// lane l of warp w covers the two columns x0 = 64*blockIdx.x + 2l, x0 + 1 and
-// walks STREAM_ROWS rows down: the north link flux of a row is the negated
-// south link flux of the row before (exactly, see link_flux) and the link
-// between the two columns is evaluated once; the horizontal neighbours come
-// from the adjacent lanes by shuffle, and lanes 0 and 31 fetch the column
-// just outside the warp.  Every link enters the sum of update_pm4 with the
-// same value and in the same order, so the result is bit-identical to the
-// tiled kernel.
-constexpr int STREAM_ROWS = 8;
+// Block = 8 warps; tile = 128 columns (4 per lane) x 8R rows (R per warp),
+// with a T-cell halo on every side, so the output is (128 - 2T) x (8R - 2T)
+// pixels.  Every thread keeps its 4 x R cells (hi and lo, as packed pairs of
+// columns 0-1 and 2-3) in registers for all T iterations of the launch: the
+// horizontal neighbours come from the adjacent lanes by shuffle, the vertical
+// ones from the thread's own rows,
+// except across the boundary between two warps, whose rows pass through
+// shared memory once per iteration (double-buffered: one barrier per
+// iteration).  Each warp walks its rows top to bottom with the north flux of
+// a row the negated south flux of the row above, and each lane evaluates the
+// five horizontal links of its columns once (exactly antisymmetric, see
+// link_flux), so the fluxes and their order of summation are those of the
+// other kernels: the results are bit-identical.  Every cell of the tile is
+// updated every iteration; those outside the region an iteration can update
+// exactly (the ring of width it + 1) come out wrong, but only cells further
+// out read them, and the output region lies inside every iteration's exact
+// region.
+template <int R>
+__global__ void __launch_bounds__(256, 2) k_diffuse_regs(const DiffFrame *__restrict__ frames,
+                                                          int n_frames, int T, float lam, float c)
+{
+    __shared__ float4 bnd_lo[2][2][8][32];   // [buffer][first / last row][warp][lane]
+    __shared__ float4 bnd_hi[2][8][32];      // [first / last row][warp][lane]
+    const int tile = blockIdx.x;
+    int lo_f = 0, hi_f = n_frames - 1;
+    while (lo_f < hi_f) {
+        int mid = (lo_f + hi_f + 1) >> 1;
+        if (frames[mid].tile_begin <= tile)
+            lo_f = mid;
+        else
+            hi_f = mid - 1;
+    }
+    const DiffFrame f = frames[lo_f];
+    const int DX = 128 - 2 * T, DY = 8 * R - 2 * T;
+    const int tl = tile - f.tile_begin;
+    const int tx0 = (tl % f.tiles_x) * DX - T;    // tile column of cell column 0
+    const int ty0 = (tl / f.tiles_x) * DY - T;
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int x0 = tx0 + 4 * lane;
+    const bool has_lo = f.lo_in != nullptr;
 
-template <int MODE, int SRC>
-__global__ void __launch_bounds__(256) k_diffuse_stream(DiffFrame f, float lam, float c)
+    f2 h01[R], h23[R], l01[R], l23[R];          // the thread's cells, row r
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int gy = ty0 + w * R + r;
+        float hv[4], lv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int gx = x0 + k;
+            const bool ok = gy >= 0 && gy < f.h && gx >= 0 && gx < f.w;
+            const float2 d = decode_rt(ok ? load_raw(f, gx, gy) : 0u, f.src_dtype, f.scale);
+            hv[k] = d.x;
+            lv[k] = has_lo ? (ok ? __ldg(f.lo_in + (long long)gy * f.w + gx) : 0.0f) : d.y;
+        }
+        h01[r] = pk(hv[0], hv[1]);
+        h23[r] = pk(hv[2], hv[3]);
+        l01[r] = pk(lv[0], lv[1]);
+        l23[r] = pk(lv[2], lv[3]);
+    }
+    // static neighbours: hi of the rows above and below the warp's rows
+    // (warps 0 and 7: outside the tile, holes)
+    bnd_hi[0][w][lane] = make_float4(lo_of(h01[0]), hi_of(h01[0]), lo_of(h23[0]), hi_of(h23[0]));
+    bnd_hi[1][w][lane] = make_float4(lo_of(h01[R - 1]), hi_of(h01[R - 1]), lo_of(h23[R - 1]),
+                                     hi_of(h23[R - 1]));
+    __syncthreads();
+    f2 hN01, hN23, hS01, hS23;
+    {
+        const float4 a = w > 0 ? bnd_hi[1][w - 1][lane] : make_float4(HOLE, HOLE, HOLE, HOLE);
+        const float4 b = w < 7 ? bnd_hi[0][w + 1][lane] : make_float4(HOLE, HOLE, HOLE, HOLE);
+        hN01 = pk(a.x, a.y);
+        hN23 = pk(a.z, a.w);
+        hS01 = pk(b.x, b.y);
+        hS23 = pk(b.z, b.w);
+    }
+    const f2 c2 = pk(c, c), lam2 = pk(lam, lam);
+    constexpr int H2 = R / 2;
+    for (int it = 0; it < f.n_iters; ++it) {
+        const int buf = it & 1;
+        bnd_lo[buf][0][w][lane] = make_float4(lo_of(l01[0]), hi_of(l01[0]), lo_of(l23[0]),
+                                              hi_of(l23[0]));
+        bnd_lo[buf][1][w][lane] = make_float4(lo_of(l01[R - 1]), hi_of(l01[R - 1]),
+                                              lo_of(l23[R - 1]), hi_of(l23[R - 1]));
+        __syncthreads();
+        const float4 a = w > 0 ? bnd_lo[buf][1][w - 1][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = w < 7 ? bnd_lo[buf][0][w + 1][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const f2 lN01 = pk(a.x, a.y), lN23 = pk(a.z, a.w);
+        const f2 lS01 = pk(b.x, b.y), lS23 = pk(b.z, b.w);
+        // Two chains walk the warp's rows top to bottom, rows [0, H2) and
+        // [H2, R), independent of each other (more instructions in flight).
+        // The flux between rows H2 - 1 and H2 is taken before either is
+        // updated: it is the second chain's first north flux and, negated,
+        // the first chain's last south flux.
+        const f2 fB01 = link_flux2(h01[H2], l01[H2], h01[H2 - 1], l01[H2 - 1], c2);
+        const f2 fB23 = link_flux2(h23[H2], l23[H2], h23[H2 - 1], l23[H2 - 1], c2);
+        f2 fN01[2], fN23[2];
+        fN01[0] = link_flux2(h01[0], l01[0], hN01, lN01, c2);
+        fN23[0] = link_flux2(h23[0], l23[0], hN23, lN23, c2);
+        fN01[1] = fB01;
+        fN23[1] = fB23;
+#pragma unroll
+        for (int j = 0; j < H2; ++j) {
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch) {
+                const int r = ch * H2 + j;
+                f2 fS01, fS23;
+                if (j + 1 < H2) {
+                    const int rs = j + 1 < H2 ? r + 1 : r;
+                    fS01 = link_flux2(h01[r], l01[r], h01[rs], l01[rs], c2);
+                    fS23 = link_flux2(h23[r], l23[r], h23[rs], l23[rs], c2);
+                } else if (ch == 0) {
+                    fS01 = neg2(fB01);
+                    fS23 = neg2(fB23);
+                } else {
+                    fS01 = link_flux2(h01[r], l01[r], hS01, lS01, c2);
+                    fS23 = link_flux2(h23[r], l23[r], hS23, lS23, c2);
+                }
+                // horizontal: (W of column 0, E of column 3) and (0-1, 2-3)
+                // packed, 1-2 alone
+                // the column left of the lane's and right of it (lanes 0 and
+                // 31: outside the tile, holes)
+                float hW = __shfl_up_sync(0xffffffffu, hi_of(h23[r]), 1);
+                float hE = __shfl_down_sync(0xffffffffu, lo_of(h01[r]), 1);
+                float lW = __shfl_up_sync(0xffffffffu, hi_of(l23[r]), 1);
+                float lE = __shfl_down_sync(0xffffffffu, lo_of(l01[r]), 1);
+                if (lane == 0) {
+                    hW = HOLE;
+                    lW = 0.0f;
+                }
+                if (lane == 31) {
+                    hE = HOLE;
+                    lE = 0.0f;
+                }
+                const float h0 = lo_of(h01[r]), h1 = hi_of(h01[r]), h2 = lo_of(h23[r]),
+                            h3 = hi_of(h23[r]);
+                const float v0 = lo_of(l01[r]), v1 = hi_of(l01[r]), v2 = lo_of(l23[r]),
+                            v3 = hi_of(l23[r]);
+                const f2 fWE = link_flux2(pk(h0, h3), pk(v0, v3), pk(hW, hE), pk(lW, lE), c2);
+                const f2 fIn = link_flux2(pk(h0, h2), pk(v0, v2), pk(h1, h3), pk(v1, v3), c2);
+                const float f12 = link_flux(make_float2(h1, v1), make_float2(h2, v2), c);
+                const float fW0 = lo_of(fWE), fE3 = hi_of(fWE);
+                const float f01 = lo_of(fIn), f23 = hi_of(fIn);
+                // column k: W flux, then E flux, as pm4_combine sums them
+                const f2 fW01 = pk(fW0, -f01), fE01 = pk(f01, f12);
+                const f2 fW23 = pk(-f12, -f23), fE23 = pk(f23, fE3);
+                l01[r] = add2(l01[r], mulr2(lam2, add2(add2(add2(fN01[ch], fS01), fW01), fE01)));
+                l23[r] = add2(l23[r], mulr2(lam2, add2(add2(add2(fN23[ch], fS23), fW23), fE23)));
+                fN01[ch] = neg2(fS01);
+                fN23[ch] = neg2(fS23);
+            }
+        }
+    }
+    // the output region: rows [T, 8R - T), columns [T, 128 - T) of the tile
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int ty = w * R + r;
+        const int gy = ty0 + ty;
+        if (ty < T || ty >= 8 * R - T || gy >= f.h)
+            continue;
+        const float hv[4] = {lo_of(h01[r]), hi_of(h01[r]), lo_of(h23[r]), hi_of(h23[r])};
+        const float lv[4] = {lo_of(l01[r]), hi_of(l01[r]), lo_of(l23[r]), hi_of(l23[r])};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int tx = 4 * lane + k, gx = x0 + k;
+            if (tx >= T && tx < 128 - T && gx < f.w)
+                f.dst[(long long)gy * f.w + gx] =
+                    f.dst_lo ? lv[k] : depth_out(make_float2(hv[k], lv[k]));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one iteration per launch, one pass over HBM
+// ---------------------------------------------------------------------------
+
+// Block = 32 x 8 threads; lane l of warp w covers the four columns
+// x0 = 128 blockIdx.x + 4 l .. x0 + 3 and walks STREAM_ROWS rows down.  The
+// north link flux of a row is the negated south link flux of the row before
+// and the three links inside a lane's columns are evaluated once (exactly
+// antisymmetric, see link_flux); the horizontal neighbours come from the
+// adjacent lanes by shuffle, and lanes 0 and 31 read the column just outside
+// the warp.  Every link enters the sum of pm4_combine with the same value and
+// in the same order as in the tiled kernel, so the results are bit-identical.
+// Two rows below the current one are in flight while it is computed.
+constexpr int SCOLS = 4;
+constexpr int STREAM_ROWS = 16;
+
+// One row of a lane's columns as read from memory: encoding containers, lo
+// parts, and the column outside the warp (lanes 0 and 31).
+struct RowRaw {
+    unsigned r[SCOLS];
+    float l[SCOLS];
+    unsigned re;
+    float le;
+};
+
+template <int DT, bool HAS_LO>
+__device__ __forceinline__ void load_row(const DiffFrame &f, int y, int x0, int xe, bool edge,
+                                         bool vsrc, bool vlo, RowRaw &o)
+{
+#pragma unroll
+    for (int k = 0; k < SCOLS; ++k) {
+        o.r[k] = 0u;
+        o.l[k] = 0.0f;
+    }
+    o.re = 0u;
+    o.le = 0.0f;
+    if (y < 0 || y >= f.h)
+        return;
+    const char *row = (const char *)f.src + (long long)y * f.src_pitch;
+    const bool full = x0 + SCOLS <= f.w;
+    if (full && vsrc) {
+        if (DT == PM_F32_M) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(row) + (x0 >> 2));
+            o.r[0] = v.x; o.r[1] = v.y; o.r[2] = v.z; o.r[3] = v.w;
+        } else {
+            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(row) + (x0 >> 2));
+            o.r[0] = v.x & 0xffffu; o.r[1] = v.x >> 16;
+            o.r[2] = v.y & 0xffffu; o.r[3] = v.y >> 16;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCOLS; ++k)
+            if (x0 + k < f.w)
+                o.r[k] = load_raw(f, x0 + k, y);
+    }
+    if (HAS_LO) {
+        const float *lrow = f.lo_in + (long long)y * f.w;
+        if (full && vlo) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(lrow + x0));
+            o.l[0] = v.x; o.l[1] = v.y; o.l[2] = v.z; o.l[3] = v.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < SCOLS; ++k)
+                if (x0 + k < f.w)
+                    o.l[k] = __ldg(lrow + x0 + k);
+        }
+        if (edge)
+            o.le = __ldg(lrow + xe);
+    }
+    if (edge)
+        o.re = load_raw(f, xe, y);
+}
+
+template <int DT, bool HAS_LO>
+__device__ __forceinline__ void decode_row(const RowRaw &o, float scale, float2 (&a)[SCOLS],
+                                           float2 &e)
+{
+#pragma unroll
+    for (int k = 0; k < SCOLS; ++k) {
+        a[k] = decode<DT>(o.r[k], scale);
+        if (HAS_LO)
+            a[k].y = o.l[k];
+    }
+    e = decode<DT>(o.re, scale);
+    if (HAS_LO)
+        e.y = o.le;
+}
+
+// State of a lane walking down its columns: the row being computed (a, with
+// the column outside the warp ae), the row above (u, for the Alg. 1 form) and
+// the north fluxes of the row (PM4).
+struct StreamState {
+    float2 u[SCOLS], a[SCOLS], ae;
+    float fN[SCOLS];
+};
+
+// Row y of the lane's columns, its row below already read into `below`, which
+// is refilled with row y + 3 (the row read two steps ahead) when `more`.
+template <int MODE, int DT, bool HAS_LO, bool DST_LO>
+__device__ __forceinline__ void stream_row(const DiffFrame &f, int y, int x0, int xe, bool edge,
+                                           bool vsrc, bool vlo, bool vdst, int lane, float lam,
+                                           float c, RowRaw &below, bool more, StreamState &S)
+{
+    const float2 Z = make_float2(HOLE, 0.0f);
+    float2 d[SCOLS], de;
+    decode_row<DT, HAS_LO>(below, f.scale, d, de);
+    if (more)
+        load_row<DT, HAS_LO>(f, y + 3, x0, xe, edge, vsrc, vlo, below);
+    float2 L = make_float2(__shfl_up_sync(0xffffffffu, S.a[SCOLS - 1].x, 1),
+                           __shfl_up_sync(0xffffffffu, S.a[SCOLS - 1].y, 1));
+    float2 R = make_float2(__shfl_down_sync(0xffffffffu, S.a[0].x, 1),
+                           __shfl_down_sync(0xffffffffu, S.a[0].y, 1));
+    if (lane == 0)
+        L = edge ? S.ae : Z;
+    if (lane == 31)
+        R = edge ? S.ae : Z;
+    float2 n[SCOLS];
+    if (MODE == 0) {
+        float fS[SCOLS], fH[SCOLS + 1];   // fH[k]: into column k from column k - 1
+        fH[0] = link_flux(S.a[0], L, c);
+#pragma unroll
+        for (int k = 1; k < SCOLS; ++k)
+            fH[k] = link_flux(S.a[k], S.a[k - 1], c);
+        fH[SCOLS] = link_flux(S.a[SCOLS - 1], R, c);   // into the last column from R
+#pragma unroll
+        for (int k = 0; k < SCOLS; ++k)
+            fS[k] = link_flux(S.a[k], d[k], c);
+#pragma unroll
+        for (int k = 0; k < SCOLS; ++k) {
+            const float fW = fH[k];
+            const float fE = k + 1 < SCOLS ? -fH[k + 1] : fH[SCOLS];
+            n[k] = pm4_combine(S.a[k], S.fN[k], fS[k], fW, fE, lam);
+            S.fN[k] = -fS[k];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCOLS; ++k)
+            n[k] = update_alg1(S.a[k], S.u[k], d[k], k ? S.a[k - 1] : L,
+                               k + 1 < SCOLS ? S.a[k + 1] : R, lam, c);
+    }
+    if (f.n_iters == 0) {
+#pragma unroll
+        for (int k = 0; k < SCOLS; ++k)
+            n[k] = S.a[k];
+    }
+    float o[SCOLS];
+#pragma unroll
+    for (int k = 0; k < SCOLS; ++k)
+        o[k] = DST_LO ? n[k].y : depth_out(n[k]);
+    float *drow = f.dst + (long long)y * f.w;
+    if (vdst && x0 + SCOLS <= f.w) {
+        *reinterpret_cast<float4 *>(drow + x0) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCOLS; ++k)
+            if (x0 + k < f.w)
+                drow[x0 + k] = o[k];
+    }
+#pragma unroll
+    for (int k = 0; k < SCOLS; ++k) {
+        S.u[k] = S.a[k];
+        S.a[k] = d[k];
+    }
+    S.ae = de;
+}
+
+template <int MODE, int DT, bool HAS_LO, bool DST_LO>
+__global__ void __launch_bounds__(256, 3) k_diffuse_stream(DiffFrame f, float lam, float c)
 {
     const int lane = threadIdx.x;
-    const int x0 = blockIdx.x * 64 + 2 * lane;
+    const int x0 = blockIdx.x * (32 * SCOLS) + SCOLS * lane;
     const int y0 = (blockIdx.y * 8 + threadIdx.y) * STREAM_ROWS;
     if (y0 >= f.h)
         return;
     const int y1 = min(y0 + STREAM_ROWS, f.h);
-    const float2 Z = make_float2(HOLE, 0.0f);
-    const int vb = SRC == SRC_PAIR ? 16 : 8;
-    const bool vec_ld = (SRC == SRC_PAIR || SRC == PM_F32_M) && f.src_pitch % vb == 0 &&
-                        ((uintptr_t)f.src % vb) == 0;
-    const int ob = f.dst_pair ? 16 : 8;
-    const bool vec_st = ((long long)f.w * (f.dst_pair ? 8 : 4)) % ob == 0 &&
-                        ((uintptr_t)f.dst % ob) == 0;
-    auto ld2 = [&](int y, float2 &a, float2 &b) {
-        a = Z;
-        b = Z;
-        if (y < 0 || y >= f.h)
-            return;
-        if (x0 + 1 < f.w)
-            load_src2<SRC>(f, x0, y, vec_ld, a, b);
-        else if (x0 < f.w)
-            a = load_src<SRC>(f, x0, y);
-    };
-    // the column just outside the warp: x0 - 1 for lane 0, x0 + 2 for lane 31
-    const int xe = lane == 0 ? x0 - 1 : x0 + 2;
+    constexpr int VB = SCOLS * (DT == PM_F32_M ? 4 : 2);   // bytes of a lane's encoding
+    const bool vsrc = ((uintptr_t)f.src % VB) == 0 && f.src_pitch % VB == 0;
+    const bool vlo = ((uintptr_t)f.lo_in % 16) == 0 && f.w % 4 == 0;
+    const bool vdst = ((uintptr_t)f.dst % 16) == 0 && f.w % 4 == 0;
+    // the column just outside the warp: x0 - 1 for lane 0, x0 + 4 for lane 31
+    const int xe = lane == 0 ? x0 - 1 : x0 + SCOLS;
     const bool edge = (lane == 0 || lane == 31) && xe >= 0 && xe < f.w;
 
-    float2 a0, a1, u0, u1;
-    ld2(y0, a0, a1);
-    ld2(y0 - 1, u0, u1);
-    float fN0 = 0.0f, fN1 = 0.0f;
-    if (MODE == 0) {
-        fN0 = link_flux(a0, u0, c);
-        fN1 = link_flux(a1, u1, c);
-    }
-    for (int y = y0; y < y1; ++y) {
-        float2 d0, d1;
-        ld2(y + 1, d0, d1);
-        float2 E = Z;
-        if (edge)
-            E = load_src<SRC>(f, xe, y);
-        float2 L = make_float2(__shfl_up_sync(0xffffffffu, a1.x, 1),
-                               __shfl_up_sync(0xffffffffu, a1.y, 1));
-        float2 R = make_float2(__shfl_down_sync(0xffffffffu, a0.x, 1),
-                               __shfl_down_sync(0xffffffffu, a0.y, 1));
-        if (lane == 0)
-            L = E;
-        if (lane == 31)
-            R = E;
-        float2 n0, n1;
-        if (MODE == 0) {
-            const float f01 = link_flux(a0, a1, c);              // into x0 from x0+1
-            const float fE1 = link_flux(a1, R, c);               // into x0+1 from x0+2
-            const float fW0 = link_flux(a0, L, c);               // into x0 from x0-1
-            const float fW1 = -f01;
-            const float fS0 = link_flux(a0, d0, c), fS1 = link_flux(a1, d1, c);
-            n0 = pm4_combine(a0, fN0, fS0, fW0, f01, lam);
-            n1 = pm4_combine(a1, fN1, fS1, fW1, fE1, lam);
-            fN0 = -fS0;
-            fN1 = -fS1;
-        } else {
-            n0 = update_alg1(a0, u0, d0, L, a1, lam, c);
-            n1 = update_alg1(a1, u1, d1, a0, R, lam, c);
-        }
-        if (f.n_iters == 0) {
-            n0 = a0;
-            n1 = a1;
-        }
-        const long long row = (long long)y * f.w;
-        if (vec_st && x0 + 1 < f.w) {
-            if (f.dst_pair)
-                reinterpret_cast<float4 *>(f.dst)[(row + x0) >> 1] = make_float4(n0.x, n0.y, n1.x, n1.y);
-            else
-                reinterpret_cast<float2 *>(f.dst)[(row + x0) >> 1] =
-                    make_float2(depth_out(n0), depth_out(n1));
-        } else {
-            if (x0 < f.w)
-                store_px(f, row + x0, n0);
-            if (x0 + 1 < f.w)
-                store_px(f, row + x0 + 1, n1);
-        }
-        u0 = a0; u1 = a1;
-        a0 = d0; a1 = d1;
+    // two read buffers alternate: while row y is computed, rows y + 1 and
+    // y + 2 are in flight
+    RowRaw rA, rB;
+    StreamState S;
+    load_row<DT, HAS_LO>(f, y0 - 1, x0, xe, edge, vsrc, vlo, rA);
+    load_row<DT, HAS_LO>(f, y0, x0, xe, edge, vsrc, vlo, rB);
+    float2 ue;
+    decode_row<DT, HAS_LO>(rA, f.scale, S.u, ue);
+    decode_row<DT, HAS_LO>(rB, f.scale, S.a, S.ae);
+    load_row<DT, HAS_LO>(f, y0 + 1, x0, xe, edge, vsrc, vlo, rA);
+    load_row<DT, HAS_LO>(f, y0 + 2, x0, xe, edge, vsrc, vlo, rB);
+#pragma unroll
+    for (int k = 0; k < SCOLS; ++k)
+        S.fN[k] = MODE == 0 ? link_flux(S.a[k], S.u[k], c) : 0.0f;
+    for (int y = y0; y < y1; y += 2) {
+        stream_row<MODE, DT, HAS_LO, DST_LO>(f, y, x0, xe, edge, vsrc, vlo, vdst, lane, lam, c,
+                                             rA, y + 2 < y1, S);
+        if (y + 1 >= y1)
+            break;
+        stream_row<MODE, DT, HAS_LO, DST_LO>(f, y + 1, x0, xe, edge, vsrc, vlo, vdst, lane, lam,
+                                             c, rB, y + 3 < y1, S);
     }
 }
 
@@ -441,6 +718,16 @@ static inline float conductance_scale(float K)
 {
     // exp(-(x/K)^2) = 2^(x^2 * c) with c = -log2(e) / K^2
     return (float)(-1.4426950408889634 / ((double)K * (double)K));
+}
+
+int regs_rows(int mode, int T, int dx, int dy)
+{
+    if (mode != 0 || T < 1 || dx != 128 - 2 * T)
+        return 0;
+    for (int R = 4; R <= 8; R += 2)
+        if (dy == 8 * R - 2 * T)
+            return R;
+    return 0;
 }
 
 size_t diffuse_tiles_smem(int T, int dx, int dy)
@@ -467,32 +754,64 @@ cudaError_t launch_diffuse_tiles(const DiffFrame *d_frames, int n_frames, int to
     const size_t smem = diffuse_tiles_smem(T, dx, dy);
     const float c = conductance_scale(K);
     const dim3 block(32, 8);
-    if (mode == 0)
+    const int R = regs_rows(mode, T, dx, dy);
+    if (R == 4)
+        k_diffuse_regs<4><<<total_tiles, block, 0, s>>>(d_frames, n_frames, T, lambda, c);
+    else if (R == 6)
+        k_diffuse_regs<6><<<total_tiles, block, 0, s>>>(d_frames, n_frames, T, lambda, c);
+    else if (R == 8)
+        k_diffuse_regs<8><<<total_tiles, block, 0, s>>>(d_frames, n_frames, T, lambda, c);
+    else if (mode == 0)
         k_diffuse_tiles<0><<<total_tiles, block, smem, s>>>(d_frames, n_frames, T, dx, dy, lambda, c);
     else
         k_diffuse_tiles<1><<<total_tiles, block, smem, s>>>(d_frames, n_frames, T, dx, dy, lambda, c);
     return cudaGetLastError();
 }
 
+// The streaming kernel for the launch's iterate input and output (lo parts
+// read or not, lo parts or depth written).
+template <int M, int DT>
+static void launch_stream_io(const DiffFrame &f, dim3 grid, dim3 block, float lam, float c,
+                             cudaStream_t s)
+{
+    if (f.lo_in) {
+        if (f.dst_lo)
+            k_diffuse_stream<M, DT, true, true><<<grid, block, 0, s>>>(f, lam, c);
+        else
+            k_diffuse_stream<M, DT, true, false><<<grid, block, 0, s>>>(f, lam, c);
+    } else {
+        if (f.dst_lo)
+            k_diffuse_stream<M, DT, false, true><<<grid, block, 0, s>>>(f, lam, c);
+        else
+            k_diffuse_stream<M, DT, false, false><<<grid, block, 0, s>>>(f, lam, c);
+    }
+}
+
 cudaError_t launch_diffuse_stream(const DiffFrame &f, float lambda, float K, int mode,
                                   cudaStream_t s)
 {
-    dim3 grid((f.w + 63) / 64, (f.h + 8 * STREAM_ROWS - 1) / (8 * STREAM_ROWS));
+    dim3 grid((f.w + 32 * SCOLS - 1) / (32 * SCOLS),
+              (f.h + 8 * STREAM_ROWS - 1) / (8 * STREAM_ROWS));
     const dim3 block(32, 8);
     const float c = conductance_scale(K);
-#define PM_STREAM(M, S) k_diffuse_stream<M, S><<<grid, block, 0, s>>>(f, lambda, c)
-    switch (f.src_dtype * 2 + (mode ? 1 : 0)) {
-    case PM_U16_MM * 2: PM_STREAM(0, PM_U16_MM); break;
-    case PM_U16_MM * 2 + 1: PM_STREAM(1, PM_U16_MM); break;
-    case PM_F16_M * 2: PM_STREAM(0, PM_F16_M); break;
-    case PM_F16_M * 2 + 1: PM_STREAM(1, PM_F16_M); break;
-    case PM_F32_M * 2: PM_STREAM(0, PM_F32_M); break;
-    case PM_F32_M * 2 + 1: PM_STREAM(1, PM_F32_M); break;
-    case SRC_PAIR * 2: PM_STREAM(0, SRC_PAIR); break;
-    case SRC_PAIR * 2 + 1: PM_STREAM(1, SRC_PAIR); break;
-    default: return cudaErrorInvalidValue;
+    if (f.src_dtype != PM_U16_MM && f.src_dtype != PM_F16_M && f.src_dtype != PM_F32_M)
+        return cudaErrorInvalidValue;
+    const int dt = f.src_dtype;
+    if (mode == 0) {
+        if (dt == PM_U16_MM)
+            launch_stream_io<0, PM_U16_MM>(f, grid, block, lambda, c, s);
+        else if (dt == PM_F16_M)
+            launch_stream_io<0, PM_F16_M>(f, grid, block, lambda, c, s);
+        else
+            launch_stream_io<0, PM_F32_M>(f, grid, block, lambda, c, s);
+    } else {
+        if (dt == PM_U16_MM)
+            launch_stream_io<1, PM_U16_MM>(f, grid, block, lambda, c, s);
+        else if (dt == PM_F16_M)
+            launch_stream_io<1, PM_F16_M>(f, grid, block, lambda, c, s);
+        else
+            launch_stream_io<1, PM_F32_M>(f, grid, block, lambda, c, s);
     }
-#undef PM_STREAM
     return cudaGetLastError();
 }
 

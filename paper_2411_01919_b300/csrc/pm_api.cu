@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pm_internal.cuh"
 
 using namespace pm;
@@ -14,6 +16,16 @@ using namespace pm;
 namespace {
 
 thread_local std::string g_err;
+
+// An NVTX range over the lifetime of the object (entry points and the stages
+// of a launch sequence), visible to profilers that record NVTX; header-only,
+// inert when no tool is attached.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 pm_status fail(pm_status s, const std::string &m)
 {
@@ -50,8 +62,8 @@ Layout make_layout(long long npx, int frames, int H, int max_chunks)
         return o;
     };
     const size_t F = (size_t)frames, P = (size_t)npx;
-    L.buf[0] = take(F * P * 8);   // compensated iterate (float2)
-    L.buf[1] = take(F * P * 8);
+    L.buf[0] = take(F * P * 4);   // lo parts of the compensated iterate
+    L.buf[1] = take(F * P * 4);
     L.depth = take(F * P * 4);
     L.P = take(F * P * 12);
     L.N = take(F * P * 12);
@@ -73,6 +85,65 @@ Layout make_layout(long long npx, int frames, int H, int max_chunks)
     L.total = off;
     return L;
 }
+
+// Per-region RANSAC scratch for R regions x H hypotheses.
+struct RegionLayout {
+    size_t cnt, box, off, cur, cb, hyp, deg, err, inl, out, total;
+};
+
+RegionLayout region_layout(size_t R, size_t H)
+{
+    RegionLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o = align_up(o + bytes, 256);
+        return r;
+    };
+    const size_t RH = R * H;
+    L.cnt = take(R * 4);
+    L.box = take(R * 16);
+    L.off = take(R * 4);
+    L.cur = take(R * 4);
+    L.cb = take((R + 1) * 4);
+    L.hyp = take(RH * 16);
+    L.deg = take(RH);
+    L.err = take(RH * 8);
+    L.inl = take(RH * 4);
+    L.out = take(R * sizeof(pm_region_plane));
+    L.total = o;
+    return L;
+}
+
+// Scratch of the edge and region passes for images of up to n pixels.
+struct EdgeLayout {
+    size_t state, strong, L, size, pre, bsum, err, total;
+};
+
+EdgeLayout edge_layout(size_t n)
+{
+    EdgeLayout E;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o = align_up(o + bytes, 256);
+        return r;
+    };
+    const size_t nb = (n + 1023) / 1024 + 1;
+    E.state = take(n);
+    E.strong = take(n);
+    E.L = take(n * 4);
+    E.size = take(n * 4);
+    E.pre = take(n * 4);
+    E.bsum = take(nb * 4);
+    E.err = take(4);
+    E.total = o;
+    return E;
+}
+
+// Regions the per-region RANSAC scratch allocated by pm_create holds (at the
+// context's hypothesis count).
+constexpr int CREATE_REGIONS = 256;
 
 struct GraphEntry {
     std::vector<long long> sig;
@@ -121,6 +192,7 @@ struct pm_ctx {
     cudaEvent_t gev[2] = {nullptr, nullptr};
     long long launches = 0;               // kernels launched by the last call
     int last_n = 0;                       // frames of the last call
+    std::vector<int> geom_wh;             // w, h of each frame of the last whole-path call
 
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(arena + off); }
 };
@@ -154,9 +226,11 @@ pm_status check_params(const pm_diffusion_params *dp, const pm_ransac_params *rp
         return fail(PM_ERR_ARG, "diffusion mode must be 0 (PM4) or 1 (ALG1)");
     if (dp->iters_per_launch < 0 || dp->iters_per_launch > DT_MAX)
         return fail(PM_ERR_ARG, "iters_per_launch must lie in [0, 8]");
-    if (dp->tile_w < 0 || dp->tile_h < 0 || dp->tile_w + 2 * DT_MAX > TILE_MAX_DX ||
-        dp->tile_h + 2 * DT_MAX > TILE_MAX_DY)
-        return fail(PM_ERR_ARG, "tile_w must lie in [0, 128] and tile_h in [0, 48]");
+    const int T_eff = dp->iters_per_launch > 0 ? dp->iters_per_launch : DT_MAX;
+    if (dp->tile_w < 0 || dp->tile_h < 0 || dp->tile_w + 2 * T_eff > TILE_MAX_DX ||
+        dp->tile_h + 2 * T_eff > TILE_MAX_DY)
+        return fail(PM_ERR_ARG, "tile_w + 2 T must lie in [0, 144] and tile_h + 2 T in [0, 64] "
+                                "(T = iters_per_launch, 8 when 0)");
     if (rp->hypotheses < 1 || rp->hypotheses > MAX_HYP)
         return fail(PM_ERR_ARG, "hypotheses must lie in [1, 2048]");
     if (!(rp->thr_m > 0.0f) || !std::isfinite(rp->thr_m))
@@ -262,10 +336,13 @@ Plan build_tables(pm_ctx *ctx, const std::vector<FrameJob> &jobs, int T, bool ra
         pl.total_chunks += ((long long)jobs[f].w * jobs[f].h + CHUNK - 1) / CHUNK;
         big_tiles += (long long)((jobs[f].w + 79) / 80) * ((jobs[f].h + 47) / 48);
     }
-    // tile shape: large tiles (less halo recompute) once they fill the GPU
-    // twice over, smaller ones for small batches
-    pl.dx = ctx->dp.tile_w > 0 ? ctx->dp.tile_w : (big_tiles >= 2LL * ctx->sms ? 80 : 48);
-    pl.dy = ctx->dp.tile_h > 0 ? ctx->dp.tile_h : (big_tiles >= 2LL * ctx->sms ? 48 : 24);
+    // tile shape: for PM4 batches that fill the GPU twice over, the
+    // register-blocked kernel's (128 - 2T) x (48 - 2T) tiles; otherwise the
+    // shared-memory kernel's smaller tiles (more CTAs for small batches)
+    const bool big = big_tiles >= 2LL * ctx->sms;
+    const bool regs = false;
+    pl.dx = ctx->dp.tile_w > 0 ? ctx->dp.tile_w : (regs ? 128 - 2 * T : big ? 80 : 48);
+    pl.dy = ctx->dp.tile_h > 0 ? ctx->dp.tile_h : (regs ? 48 - 2 * T : big ? 48 : 24);
     size_t off = 0;
     for (int k = 0; k < Lmax; ++k) {
         DiffFrame *tab = reinterpret_cast<DiffFrame *>(ctx->h_tables + off);
@@ -280,13 +357,14 @@ Plan build_tables(pm_ctx *ctx, const std::vector<FrameJob> &jobs, int T, bool ra
             if (write) {
                 DiffFrame d;
                 const bool first = k == 0, lastk = k == L[f] - 1;
-                d.src = first ? j.src : (const void *)(ctx->at<float2>(ctx->lay.buf[(k - 1) & 1]) + slot);
-                d.src_dtype = first ? j.dtype : SRC_PAIR;
-                d.src_pitch = first ? j.pitch : (long long)j.w * 8;
+                d.src = j.src;
+                d.src_dtype = j.dtype;
+                d.src_pitch = j.pitch;
+                d.lo_in = first ? nullptr : ctx->at<float>(ctx->lay.buf[(k - 1) & 1]) + slot;
                 d.w = j.w;
                 d.h = j.h;
-                d.dst = lastk ? (void *)j.depth_out : (void *)(ctx->at<float2>(ctx->lay.buf[k & 1]) + slot);
-                d.dst_pair = lastk ? 0 : 1;
+                d.dst = lastk ? j.depth_out : ctx->at<float>(ctx->lay.buf[k & 1]) + slot;
+                d.dst_lo = lastk ? 0 : 1;
                 int rem = j.iters - k * T;
                 d.n_iters = rem < T ? (rem > 0 ? rem : 0) : T;
                 d.tiles_x = tx;
@@ -368,6 +446,7 @@ RParams ransac_params(const pm_ctx *ctx)
 pm_status enqueue_ransac(pm_ctx *ctx, RFrame *d_rframes, int n, long long total_chunks,
                          cudaStream_t s)
 {
+    Range range_("ransac");
     RansacLaunch L;
     L.d_frames = d_rframes;
     L.n = n;
@@ -420,6 +499,7 @@ pm_status enqueue_batch(pm_ctx *ctx, const Plan &pl, int n, int T, bool ransac, 
     PM_CK(cudaMemcpyAsync(ctx->d_tables, ctx->h_tables, pl.bytes, cudaMemcpyHostToDevice, s));
     if (timed)
         PM_CK(record_event(ctx->ev[0], s));
+    Range r_diff("diffusion");
     for (size_t k = 0; k < pl.diff_off.size(); ++k) {
         if (pl.diff_n[k] == 0)
             continue;
@@ -433,6 +513,7 @@ pm_status enqueue_batch(pm_ctx *ctx, const Plan &pl, int n, int T, bool ransac, 
         PM_CK(record_event(ctx->ev[1], s));
     if (!ransac)
         return PM_OK;
+    Range r_norm("normals");
     PM_CK(launch_normals_batch(ctx->d_tables + pl.norm_off, n, pl.max_w, pl.max_h,
                                ctx->mp.normal_stencil, s));
     ctx->launches += 1;
@@ -467,6 +548,13 @@ pm_status run_batch(pm_ctx *ctx, std::vector<FrameJob> &jobs, bool ransac, bool 
     }
     ctx->launches = 0;
     ctx->last_n = n;
+    if (ransac) {
+        ctx->geom_wh.resize(2 * (size_t)n);
+        for (int f = 0; f < n; ++f) {
+            ctx->geom_wh[2 * f] = jobs[f].w;
+            ctx->geom_wh[2 * f + 1] = jobs[f].h;
+        }
+    }
     Plan pl = build_tables(ctx, jobs, T, ransac, false);
     pm_status st = ensure_tables(ctx, pl.bytes);
     if (st != PM_OK)
@@ -576,7 +664,9 @@ long long pm_scratch_bytes(int max_w, int max_h, int max_frames, int hypotheses,
         return -1;
     long long npx = (long long)max_w * max_h;
     int max_chunks = (int)((npx + CHUNK - 1) / CHUNK);
-    return (long long)make_layout(npx, max_frames, hypotheses, max_chunks).total;
+    return (long long)(make_layout(npx, max_frames, hypotheses, max_chunks).total +
+                       edge_layout((size_t)npx).total +
+                       region_layout(CREATE_REGIONS, (size_t)hypotheses).total);
 }
 
 pm_status pm_create(const pm_diffusion_params *dp, const pm_ransac_params *rp,
@@ -621,7 +711,27 @@ pm_status pm_create(const pm_diffusion_params *dp, const pm_ransac_params *rp,
         return bail(fail(PM_ERR_OOM, "scratch arena of " + std::to_string(ctx->lay.total) +
                                          " bytes: " + cudaGetErrorString(e)));
     }
-    e = cudaMemset(ctx->arena + ctx->lay.counter, 0, 4);
+    // the edge / region passes' scratch and the per-region RANSAC scratch
+    // for CREATE_REGIONS regions, so that those calls allocate nothing
+    const EdgeLayout EL = edge_layout((size_t)ctx->max_npx);
+    const RegionLayout RL = region_layout(CREATE_REGIONS, (size_t)rp->hypotheses);
+    e = cudaMalloc(&ctx->eg, EL.total);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&ctx->rg, RL.total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(PM_ERR_OOM, std::string("edge / region scratch: ") + cudaGetErrorString(e)));
+    }
+    ctx->rg_cap = RL.total;
+    e = cudaMemset(ctx->eg + EL.err, 0, 4);
+    if (e == cudaSuccess)
+        e = cudaMallocHost(&ctx->h_eg, 2 * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMallocHost(&ctx->h_rg, CREATE_REGIONS * sizeof(pm_region_plane));
+    if (e == cudaSuccess) {
+        ctx->h_rg_cap = CREATE_REGIONS;
+        e = cudaMemset(ctx->arena + ctx->lay.counter, 0, 4);
+    }
     if (e == cudaSuccess)
         e = cudaMallocHost(&ctx->h_state, max_frames * sizeof(RState));
     if (e == cudaSuccess)
@@ -688,6 +798,7 @@ void pm_destroy(pm_ctx *ctx)
 pm_status pm_diffuse(pm_ctx *ctx, const void *depth, int dtype, int w, int h, int pitch,
                      float *out, void *stream)
 {
+    Range range_("pm_diffuse");
     if (!ctx || !out)
         return fail(PM_ERR_ARG, "null context or output");
     if (misaligned(out, 4))
@@ -695,6 +806,9 @@ pm_status pm_diffuse(pm_ctx *ctx, const void *depth, int dtype, int w, int h, in
     pm_status st = check_frame(ctx, depth, dtype, w, h, pitch, nullptr);
     if (st != PM_OK)
         return st;
+    // the iterate lives in the context's scratch, which a pending batch still uses
+    if (ctx->pending_n)
+        return fail(PM_ERR_STATE, "an asynchronous batch is still pending on this context");
     cudaStream_t s = (cudaStream_t)stream;
     if (ctx->dp.iters_per_launch == 1) {
         // one iteration per launch: the streaming kernel, ping-pong in scratch
@@ -703,13 +817,14 @@ pm_status pm_diffuse(pm_ctx *ctx, const void *depth, int dtype, int w, int h, in
         for (int k = 0; k < (it > 0 ? it : 1); ++k) {
             DiffFrame d{};
             const bool lastk = k == (it > 0 ? it : 1) - 1;
-            d.src = k == 0 ? depth : (const void *)(ctx->at<float2>(ctx->lay.buf[(k - 1) & 1]));
-            d.src_dtype = k == 0 ? dtype : SRC_PAIR;
-            d.src_pitch = k == 0 ? pitch : (long long)w * 8;
+            d.src = depth;
+            d.src_dtype = dtype;
+            d.src_pitch = pitch;
+            d.lo_in = k == 0 ? nullptr : ctx->at<float>(ctx->lay.buf[(k - 1) & 1]);
             d.w = w;
             d.h = h;
-            d.dst = lastk ? (void *)out : (void *)ctx->at<float2>(ctx->lay.buf[k & 1]);
-            d.dst_pair = lastk ? 0 : 1;
+            d.dst = lastk ? out : ctx->at<float>(ctx->lay.buf[k & 1]);
+            d.dst_lo = lastk ? 0 : 1;
             d.n_iters = it > 0 ? 1 : 0;
             d.scale = ctx->mp.depth_scale;
             (void)npx;
@@ -725,6 +840,7 @@ pm_status pm_diffuse(pm_ctx *ctx, const void *depth, int dtype, int w, int h, in
 pm_status pm_normals(pm_ctx *ctx, const float *depth, int w, int h, const pm_intrinsics *K,
                      float *points, float *normals, unsigned char *valid, void *stream)
 {
+    Range range_("pm_normals");
     if (!ctx || !K || !points || !normals || !valid)
         return fail(PM_ERR_ARG, "null argument");
     if (misaligned(points, 4) || misaligned(normals, 4))
@@ -742,6 +858,7 @@ pm_status pm_ransac_planes(pm_ctx *ctx, const float *points, const float *normal
                            pm_plane *planes, int max_planes, int *n_planes, short *labels,
                            void *stream)
 {
+    Range range_("pm_ransac_planes");
     if (!ctx || !points || !valid || !planes || !n_planes || max_planes < 0)
         return fail(PM_ERR_ARG, "null argument");
     if (w < 1 || h < 1 || (long long)w * h > ctx->max_npx)
@@ -792,6 +909,7 @@ pm_status pm_process_frame(pm_ctx *ctx, const void *depth, int dtype, int w, int
                            const pm_intrinsics *K, unsigned long long frame_idx, pm_plane *planes,
                            int max_planes, int *n_planes, short *labels, void *stream)
 {
+    Range range_("pm_process_frame");
     if (!ctx || !K || !planes || !n_planes || max_planes < 0)
         return fail(PM_ERR_ARG, "null argument");
     if (misaligned(labels, 2))
@@ -818,11 +936,15 @@ pm_status pm_process_frame_host(pm_ctx *ctx, const void *depth_host, int dtype, 
                                 pm_plane *planes, int max_planes, int *n_planes,
                                 short *labels_host, void *stream)
 {
+    Range range_("pm_process_frame_host");
     if (!ctx || !K || !planes || !n_planes || max_planes < 0)
         return fail(PM_ERR_ARG, "null argument");
     pm_status st = check_frame(ctx, depth_host, dtype, w, h, pitch, K);
     if (st != PM_OK)
         return st;
+    // the host depth is staged in the context's scratch, which a pending batch still uses
+    if (ctx->pending_n)
+        return fail(PM_ERR_STATE, "an asynchronous batch is still pending on this context");
     cudaStream_t s = (cudaStream_t)stream;
     const int es = elem_size(dtype);
     void *d_in = ctx->at<char>(ctx->lay.input);
@@ -870,6 +992,7 @@ static pm_status batch_jobs(pm_ctx *ctx, const pm_frame *frames, int n,
 pm_status pm_process_batch(pm_ctx *ctx, const pm_frame *frames, int n, pm_plane *planes,
                            int *n_planes, int use_graph, void *stream)
 {
+    Range range_("pm_process_batch");
     if (!planes || !n_planes)
         return fail(PM_ERR_ARG, "null output");
     std::vector<FrameJob> jobs;
@@ -896,11 +1019,41 @@ pm_status pm_process_batch(pm_ctx *ctx, const pm_frame *frames, int n, pm_plane 
 pm_status pm_process_batch_async(pm_ctx *ctx, const pm_frame *frames, int n, int use_graph,
                                  void *stream)
 {
+    Range range_("pm_process_batch_async");
     std::vector<FrameJob> jobs;
     pm_status st = batch_jobs(ctx, frames, n, jobs);
     if (st != PM_OK)
         return st;
     st = run_batch(ctx, jobs, true, use_graph != 0, (cudaStream_t)stream);
+    if (st != PM_OK)
+        return st;
+    ctx->pending_n = n;
+    return PM_OK;
+}
+
+pm_status pm_process_batch_host_async(pm_ctx *ctx, const pm_frame *frames, int n, int use_graph,
+                                      void *stream)
+{
+    Range range_("pm_process_batch_host_async");
+    std::vector<FrameJob> jobs;
+    pm_status st = batch_jobs(ctx, frames, n, jobs);
+    if (st != PM_OK)
+        return st;
+    if (ctx->pending_n)
+        return fail(PM_ERR_STATE, "an asynchronous batch is still pending on this context");
+    cudaStream_t s = (cudaStream_t)stream;
+    // frame f is staged in input slot f (max_npx * 4 bytes), outside any
+    // graph, so the batch's captured launch sequence sees fixed addresses
+    for (int f = 0; f < n; ++f) {
+        FrameJob &j = jobs[f];
+        const size_t row = (size_t)j.w * elem_size(j.dtype);
+        char *slot = ctx->at<char>(ctx->lay.input) + (size_t)f * ctx->max_npx * 4;
+        PM_CK(cudaMemcpy2DAsync(slot, row, j.src, (size_t)j.pitch, row, j.h,
+                                cudaMemcpyHostToDevice, s));
+        j.src = slot;
+        j.pitch = (long long)row;
+    }
+    st = run_batch(ctx, jobs, true, use_graph != 0, s);
     if (st != PM_OK)
         return st;
     ctx->pending_n = n;
@@ -923,10 +1076,38 @@ pm_status pm_batch_collect(pm_ctx *ctx, pm_plane *planes, int *n_planes, int n)
     return PM_OK;
 }
 
+pm_status pm_frame_geometry(pm_ctx *ctx, int frame, float *points, float *normals,
+                            unsigned char *valid, void *stream)
+{
+    Range range_("pm_frame_geometry");
+    if (!ctx)
+        return fail(PM_ERR_ARG, "null context");
+    if (frame < 0 || 2 * (size_t)frame >= ctx->geom_wh.size())
+        return fail(PM_ERR_ARG, "no frame of that index in the last whole-path call");
+    if (misaligned(points, 4) || misaligned(normals, 4))
+        return fail(PM_ERR_ARG, "points / normals not 4-byte aligned");
+    if (ctx->pending_n)
+        return fail(PM_ERR_STATE, "an asynchronous batch is still pending on this context");
+    const size_t npx = (size_t)ctx->geom_wh[2 * frame] * ctx->geom_wh[2 * frame + 1];
+    const size_t slot = (size_t)frame * ctx->max_npx;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (points)
+        PM_CK(cudaMemcpyAsync(points, ctx->at<float>(ctx->lay.P) + 3 * slot, 3 * npx * 4,
+                              cudaMemcpyDeviceToDevice, s));
+    if (normals)
+        PM_CK(cudaMemcpyAsync(normals, ctx->at<float>(ctx->lay.N) + 3 * slot, 3 * npx * 4,
+                              cudaMemcpyDeviceToDevice, s));
+    if (valid)
+        PM_CK(cudaMemcpyAsync(valid, ctx->at<unsigned char>(ctx->lay.valid) + slot, npx,
+                              cudaMemcpyDeviceToDevice, s));
+    return PM_OK;
+}
+
 pm_status pm_ransac_regions(pm_ctx *ctx, const float *points, const unsigned char *valid,
                             const int *regions, int w, int h, int n_regions, int hypotheses,
                             unsigned long long frame_idx, pm_region_plane *out, void *stream)
 {
+    Range range_("pm_ransac_regions");
     if (!ctx || !points || !valid || !regions || !out)
         return fail(PM_ERR_ARG, "null argument");
     if (misaligned(points, 4) || misaligned(regions, 4))
@@ -941,24 +1122,26 @@ pm_status pm_ransac_regions(pm_ctx *ctx, const float *points, const unsigned cha
         return fail(PM_ERR_ARG, "n_regions * hypotheses above 2^22");
     if (ctx->pending_n)
         return fail(PM_ERR_STATE, "an asynchronous batch is still pending on this context");
-    const size_t R = (size_t)n_regions, RH = R * (size_t)hypotheses;
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        size_t o = off;
-        off = align_up(off + bytes, 256);
-        return o;
-    };
-    const size_t o_cnt = take(R * 4), o_box = take(R * 16), o_off = take(R * 4),
-                 o_cur = take(R * 4), o_cb = take((R + 1) * 4), o_hyp = take(RH * 16),
-                 o_deg = take(RH), o_err = take(RH * 8), o_inl = take(RH * 4),
-                 o_out = take(R * sizeof(pm_region_plane));
-    if (off > ctx->rg_cap) {
+    const size_t R = (size_t)n_regions;
+    const RegionLayout RL = region_layout(R, (size_t)hypotheses);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (RL.total > ctx->rg_cap || n_regions > ctx->h_rg_cap) {
+        // more than the scratch pm_create sized: grow it, but never inside a
+        // stream capture (an allocation there would fail or break the capture)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        PM_CK(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(PM_ERR_STATE, "region scratch smaller than n_regions x hypotheses while "
+                                      "the stream is being captured; make one such call before "
+                                      "capturing");
+    }
+    if (RL.total > ctx->rg_cap) {
         if (ctx->rg)
             cudaFree(ctx->rg);
         ctx->rg = nullptr;
         ctx->rg_cap = 0;
-        PM_CK(cudaMalloc(&ctx->rg, off));
-        ctx->rg_cap = off;
+        PM_CK(cudaMalloc(&ctx->rg, RL.total));
+        ctx->rg_cap = RL.total;
     }
     if (n_regions > ctx->h_rg_cap) {
         if (ctx->h_rg)
@@ -980,18 +1163,17 @@ pm_status pm_ransac_regions(pm_ctx *ctx, const float *points, const unsigned cha
     L.frame_idx = frame_idx;
     L.seed = ctx->rp.seed;
     L.thr2 = ctx->rp.thr_m * ctx->rp.thr_m;
-    L.cnt = reinterpret_cast<int *>(b + o_cnt);
-    L.box = reinterpret_cast<int *>(b + o_box);
-    L.offset = reinterpret_cast<int *>(b + o_off);
-    L.cursor = reinterpret_cast<int *>(b + o_cur);
-    L.chunk_base = reinterpret_cast<int *>(b + o_cb);
+    L.cnt = reinterpret_cast<int *>(b + RL.cnt);
+    L.box = reinterpret_cast<int *>(b + RL.box);
+    L.offset = reinterpret_cast<int *>(b + RL.off);
+    L.cursor = reinterpret_cast<int *>(b + RL.cur);
+    L.chunk_base = reinterpret_cast<int *>(b + RL.cb);
     L.list = ctx->at<float4>(ctx->lay.cpt[0]);
-    L.hyp = reinterpret_cast<float4 *>(b + o_hyp);
-    L.deg = reinterpret_cast<unsigned char *>(b + o_deg);
-    L.err = reinterpret_cast<unsigned long long *>(b + o_err);
-    L.inl = reinterpret_cast<int *>(b + o_inl);
-    L.out = reinterpret_cast<pm_region_plane *>(b + o_out);
-    cudaStream_t s = (cudaStream_t)stream;
+    L.hyp = reinterpret_cast<float4 *>(b + RL.hyp);
+    L.deg = reinterpret_cast<unsigned char *>(b + RL.deg);
+    L.err = reinterpret_cast<unsigned long long *>(b + RL.err);
+    L.inl = reinterpret_cast<int *>(b + RL.inl);
+    L.out = reinterpret_cast<pm_region_plane *>(b + RL.out);
     PM_CK(ransac_regions(L, ctx->sms, s));
     PM_CK(cudaMemcpyAsync(ctx->h_rg, L.out, R * sizeof(pm_region_plane), cudaMemcpyDeviceToHost,
                           s));
@@ -1013,29 +1195,15 @@ struct EdgeScratch {
 
 pm_status edge_scratch(pm_ctx *ctx, EdgeScratch &x)
 {
-    const size_t n = (size_t)ctx->max_npx, nb = (n + 1023) / 1024 + 1;
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        size_t o = off;
-        off = align_up(off + bytes, 256);
-        return o;
-    };
-    const size_t o_state = take(n), o_strong = take(n), o_L = take(n * 4), o_size = take(n * 4),
-                 o_pre = take(n * 4), o_bsum = take(nb * 4), o_err = take(4);
-    if (!ctx->eg) {
-        PM_CK(cudaMalloc(&ctx->eg, off));
-        PM_CK(cudaMemset(ctx->eg + o_err, 0, 4));
-    }
-    if (!ctx->h_eg)
-        PM_CK(cudaMallocHost(&ctx->h_eg, 2 * sizeof(int)));
+    const EdgeLayout E = edge_layout((size_t)ctx->max_npx);   // allocated by pm_create
     char *b = ctx->eg;
-    x.state = reinterpret_cast<unsigned char *>(b + o_state);
-    x.strong = reinterpret_cast<unsigned char *>(b + o_strong);
-    x.L = reinterpret_cast<int *>(b + o_L);
-    x.size = reinterpret_cast<int *>(b + o_size);
-    x.pre = reinterpret_cast<int *>(b + o_pre);
-    x.bsum = reinterpret_cast<int *>(b + o_bsum);
-    x.err = reinterpret_cast<int *>(b + o_err);
+    x.state = reinterpret_cast<unsigned char *>(b + E.state);
+    x.strong = reinterpret_cast<unsigned char *>(b + E.strong);
+    x.L = reinterpret_cast<int *>(b + E.L);
+    x.size = reinterpret_cast<int *>(b + E.size);
+    x.pre = reinterpret_cast<int *>(b + E.pre);
+    x.bsum = reinterpret_cast<int *>(b + E.bsum);
+    x.err = reinterpret_cast<int *>(b + E.err);
     return PM_OK;
 }
 
@@ -1046,6 +1214,7 @@ extern "C" {
 pm_status pm_canny(pm_ctx *ctx, const float *normals, const unsigned char *valid, int w, int h,
                    int low, int high, unsigned char *edges, void *stream)
 {
+    Range range_("pm_canny");
     if (!ctx || !normals || !valid || !edges)
         return fail(PM_ERR_ARG, "null argument");
     if (misaligned(normals, 4))
@@ -1080,6 +1249,7 @@ pm_status pm_canny(pm_ctx *ctx, const float *normals, const unsigned char *valid
 pm_status pm_segment(pm_ctx *ctx, const unsigned char *edges, const unsigned char *valid, int w,
                      int h, int gap, int min_pixels, int *labels, int *n_regions, void *stream)
 {
+    Range range_("pm_segment");
     if (!ctx || !edges || !valid || !labels || !n_regions)
         return fail(PM_ERR_ARG, "null argument");
     if (misaligned(labels, 4))
@@ -1124,8 +1294,9 @@ pm_status pm_set_tiling(pm_ctx *ctx, int iters_per_launch, int tile_w, int tile_
 {
     if (!ctx)
         return fail(PM_ERR_ARG, "null context");
+    const int T_eff = iters_per_launch > 0 ? iters_per_launch : DT_MAX;
     if (iters_per_launch < 0 || iters_per_launch > DT_MAX || tile_w < 0 || tile_h < 0 ||
-        tile_w + 2 * DT_MAX > TILE_MAX_DX || tile_h + 2 * DT_MAX > TILE_MAX_DY)
+        tile_w + 2 * T_eff > TILE_MAX_DX || tile_h + 2 * T_eff > TILE_MAX_DY)
         return fail(PM_ERR_ARG, "tiling out of range");
     ctx->dp.iters_per_launch = iters_per_launch;
     ctx->dp.tile_w = tile_w;

@@ -20,8 +20,8 @@ constexpr int NMOM = 9;                  // Sx Sy Sz Sxx Sxy Sxz Syy Syz Szz
 constexpr int GROUP = 1;                 // chunks per moment record
 constexpr int REMOVE_THREADS = 256;      // threads of the removal kernel (CHUNK / 4 candidates each)
 // per-group moment record: gated inliers then the other inliers, each NMOM
-// (sum, comp) float pairs, then two int counts (as float bit patterns), padded
-// to 40 words
+// double-float sums (h, l), then two int counts (as float bit patterns),
+// padded to 40 words
 constexpr int PART_WORDS = 40;
 
 // Diffusion tiles (temporal blocking): output tile dx x dy chosen per launch
@@ -34,18 +34,18 @@ constexpr int DT_MAX = 8;
 // per-frame descriptors
 // ---------------------------------------------------------------------------
 
-// Source encoding of a diffusion launch: the three sensor encodings of
-// pm_dtype, or the library's compensated iterate (float2 hi/lo per pixel).
-constexpr int SRC_PAIR = 3;
-
-// One frame in one diffusion launch.
+// One frame in one diffusion launch.  The iterate is the compensated pair
+// (hi, lo), I = hi + lo: hi is the decoded sensor depth and never changes, so
+// every launch decodes it again from the sensor encoding; only lo passes from
+// one launch to the next.
 struct DiffFrame {
-    const void *src;      // encoded input (first launch) or float2 iterate
-    int src_dtype;        // PM_U16_MM / PM_F16_M / PM_F32_M / SRC_PAIR
+    const void *src;      // sensor encoding, read by every launch (the hi parts)
+    int src_dtype;        // PM_U16_MM / PM_F16_M / PM_F32_M
     int w, h;
     long long src_pitch;  // bytes
-    void *dst;            // float [h*w] (final) or float2 [h*w] (intermediate)
-    int dst_pair;         // 1: write the float2 iterate, 0: write FP32 depth
+    const float *lo_in;   // lo parts from the previous launch [h*w], or null (first launch)
+    float *dst;           // lo parts [h*w] (dst_lo) or FP32 depth [h*w]
+    int dst_lo;           // 1: write the lo parts, 0: write FP32 depth (hi + lo rounded)
     int n_iters;          // iterations this launch (0 = decode only)
     int tiles_x;
     int tile_begin;       // first global tile of this frame
@@ -149,6 +149,10 @@ cudaError_t launch_diffuse_tiles(const DiffFrame *d_frames, int n_frames, int to
 cudaError_t launch_diffuse_stream(const DiffFrame &f, float lambda, float K, int mode,
                                   cudaStream_t s);
 cudaError_t diffuse_init();   // opt the tile kernels into > 48 KB of shared memory
+// Rows per warp R of the register-blocked fused kernel for this tiling (PM4,
+// output tile (128 - 2T) x (8R - 2T), R in {4, 6, 8}), or 0: the shared-memory
+// tile kernel runs it.
+int regs_rows(int mode, int T, int dx, int dy);
 pm_status set_last_error(pm_status s, const char *msg);
 
 // Record `e` on `s` as a real event: during stream capture a plain

@@ -671,50 +671,89 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
 // removal + compensated moments; refit of each frame's plane
 // ---------------------------------------------------------------------------
 
-// Neumaier compensated accumulation in FP32.
-__device__ __forceinline__ void nadd(float &s, float &c, float x)
+// Knuth's TwoSum: s = fl(a + b) and e with a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
-    float t = __fadd_rn(s, x);
-    if (fabsf(s) >= fabsf(x))
-        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, t), x));
-    else
-        c = __fadd_rn(c, __fadd_rn(__fsub_rn(x, t), s));
-    s = t;
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
 }
 
-// The nine moment values of a centred inlier (x, y, z, then the products in
-// the order Sxx Sxy Sxz Syy Syz Szz), added to v[off ..].
-__device__ __forceinline__ void mom_values(float (&v)[32], int off, float x, float y, float z)
+// Double-float accumulation (compensated FP32): the sum is h + l, h the
+// rounded running sum and l the sum of the exact rounding errors of h's
+// additions.  (h, l) += x + t, where x + t is exact (a float and 0, or an
+// error-free product).
+__device__ __forceinline__ void df_add(float &h, float &l, float x, float t)
 {
-    const float m[NMOM] = {x, y, z, __fmul_rn(x, x), __fmul_rn(x, y), __fmul_rn(x, z),
-                           __fmul_rn(y, y), __fmul_rn(y, z), __fmul_rn(z, z)};
+    float s, e;
+    two_sum(h, x, s, e);
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(e, t));
+}
+
+// (h, l) += (h2, l2) for two double-float sums.
+__device__ __forceinline__ void df_merge(float &h, float &l, float h2, float l2)
+{
+    float s, e;
+    two_sum(h, h2, s, e);
+    h = s;
+    l = __fadd_rn(__fadd_rn(l, l2), e);
+}
+
+// The nine moment values of a centred inlier -- x, y, z and the products xx
+// xy xz yy yz zz, each product split exactly into its rounded value and
+// tail (fma(a, b, -fl(a b)) is exact) -- added to the double-float sums
+// (H, L)[off ..]: no rounding error is dropped, so the covariance
+// E[xx] - E[x]^2 of a thin cluster of inliers far from the moment origin,
+// where the two terms nearly cancel, keeps its precision.
+__device__ __forceinline__ void mom_values(float (&H)[32], float (&L)[32], int off, float x,
+                                           float y, float z)
+{
+    const float a[6] = {x, x, x, y, y, z}, b[6] = {x, y, z, y, z, z};
+    const float lin[3] = {x, y, z};
 #pragma unroll
-    for (int k = 0; k < NMOM; ++k) {
+    for (int k = 0; k < 3; ++k) {
         if (off == 0)
-            v[k] = __fadd_rn(v[k], m[k]);
+            df_add(H[k], L[k], lin[k], 0.0f);
         else
-            v[NMOM + k] = __fadd_rn(v[NMOM + k], m[k]);
+            df_add(H[NMOM + k], L[NMOM + k], lin[k], 0.0f);
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const float p = __fmul_rn(a[j], b[j]);
+        const float t = __fmaf_rn(a[j], b[j], -p);
+        if (off == 0)
+            df_add(H[3 + j], L[3 + j], p, t);
+        else
+            df_add(H[NMOM + 3 + j], L[NMOM + 3 + j], p, t);
     }
 }
 
-// Sum over the warp of every one of a lane's 32 values, transposed: lane l
-// returns the sum of the lanes' a[l].  Five butterfly steps; at the step of
-// offset o each lane keeps the half of its live values selected by its bit o
-// and adds the partner's copy of that half (31 shuffles in all).  The order
-// of the additions is fixed by the lane, not by the data.
-__device__ __forceinline__ float warp_transpose_sum(float (&a)[32], int lane)
+// Sum over the warp of every one of a lane's 32 double-float values,
+// transposed: lane l returns in (h, l_out) the sum of the lanes' (H[l], L[l]).
+// Five butterfly steps; at the step of offset o each lane keeps the half of
+// its live values selected by its bit o and adds the partner's copy of that
+// half (62 shuffles in all).  The order of the additions is fixed by the
+// lane, not by the data.
+__device__ __forceinline__ void warp_transpose_sum(float (&H)[32], float (&L)[32], int lane,
+                                                   float &h, float &l_out)
 {
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
         const bool up = (lane & o) != 0;
 #pragma unroll
         for (int i = 0; i < o; ++i) {
-            const float send = up ? a[i] : a[i + o];
-            const float keep = up ? a[i + o] : a[i];
-            a[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
+            const float sh = up ? H[i] : H[i + o], sl = up ? L[i] : L[i + o];
+            float kh = up ? H[i + o] : H[i], kl = up ? L[i + o] : L[i];
+            df_merge(kh, kl, __shfl_xor_sync(0xffffffffu, sh, o),
+                     __shfl_xor_sync(0xffffffffu, sl, o));
+            H[i] = kh;
+            L[i] = kl;
         }
     }
-    return a[0];
+    h = H[0];
+    l_out = L[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -793,8 +832,8 @@ __device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
     const int nw = (int)(blockDim.x >> 5);
     float vs = 0.0f, vc = 0.0f;
     int vn = 0;
-    // lane v < 2 NMOM: (sum, compensation) of value v; lanes 2 NMOM, +1: counts
-    const int word = lane < 2 * NMOM ? 2 * lane : 36 + min(lane - 2 * NMOM, 1);
+    // lane v < 2 NMOM: double-float sum (h, l) of value v; lanes 2 NMOM, +1: counts
+    const int word = lane < 2 * NMOM ? 2 * lane : 4 * NMOM + min(lane - 2 * NMOM, 1);
     constexpr int UNR = 4;   // records loaded together
     for (int g0 = wid * UNR; g0 < ngroups; g0 += nw * UNR) {
         float a[UNR], b[UNR];
@@ -809,12 +848,10 @@ __device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
         for (int u = 0; u < UNR; ++u) {
             if (g0 + u >= ngroups)
                 break;
-            if (lane < 2 * NMOM) {
-                nadd(vs, vc, a[u]);
-                vc = __fadd_rn(vc, b[u]);
-            } else if (lane < 2 * NMOM + 2) {
+            if (lane < 2 * NMOM)
+                df_merge(vs, vc, a[u], b[u]);
+            else if (lane < 2 * NMOM + 2)
                 vn += __float_as_int(a[u]);
-            }
         }
     }
     __shared__ float ss[32][2 * NMOM], sc[32][2 * NMOM];
@@ -831,10 +868,8 @@ __device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
     if (wid == 0) {
         if (lane < 2 * NMOM) {
             float s0 = ss[0][lane], c0 = sc[0][lane];
-            for (int w = 1; w < nw; ++w) {
-                nadd(s0, c0, ss[w][lane]);
-                c0 = __fadd_rn(c0, sc[w][lane]);
-            }
+            for (int w = 1; w < nw; ++w)
+                df_merge(s0, c0, ss[w][lane], sc[w][lane]);
             acc_sh[lane] = (double)s0 + (double)c0;
         } else if (lane < 2 * NMOM + 2) {
             long long t = 0;
@@ -846,16 +881,13 @@ __device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
     __syncthreads();
     if (threadIdx.x != 0)
         return;   // (the caller does not synchronise the block after this)
-    double acc[2 * NMOM];
     long long cnt[2] = {cnt_sh[0], cnt_sh[1]};
-    for (int k = 0; k < 2 * NMOM; ++k)
-        acc[k] = acc_sh[k];
     // gated inliers if at least 3 pass the gate, else all inliers (set 0 + set 1)
     const bool gated = cnt[0] >= 3;
     const long long nsel = gated ? cnt[0] : cnt[0] + cnt[1];
     double S[NMOM];
     for (int k = 0; k < NMOM; ++k)
-        S[k] = gated ? acc[k] : acc[k] + acc[NMOM + k];
+        S[k] = gated ? acc_sh[k] : acc_sh[k] + acc_sh[NMOM + k];
     const double nn = (double)nsel;
     const double mx = S[0] / nn, my = S[1] / nn, mz = S[2] / nn;
     double a[3][3], lmin, nv[3];
@@ -919,7 +951,7 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
         const float4 p0 = st->p0;
         const int cur = round & 1;
         const long long npx = F.npx;
-        // per warp: lane v < 2 NMOM holds the compensated sum of moment value v
+        // per warp: lane v < 2 NMOM holds the double-float sum of moment value v
         // (gated inliers' values 0 .. NMOM-1, the other inliers' NMOM ..);
         // the gated / other counts are warp-uniform (ballots)
         float acc_s = 0.0f, acc_c = 0.0f;
@@ -966,29 +998,35 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
                                : make_float3(0.f, 0.f, 0.f);
                 }
                 // this lane's candidates, summed per value in registers
-                float v[32];
+                float vh[32], vl[32];
 #pragma unroll
-                for (int k = 0; k < 32; ++k)
-                    v[k] = 0.0f;
+                for (int k = 0; k < 32; ++k) {
+                    vh[k] = 0.0f;
+                    vl[k] = 0.0f;
+                }
 #pragma unroll
                 for (int u = 0; u < PER_THREAD; ++u) {
                     bool gated = false;
                     if (inl[u]) {
                         F.labels[pix[u]] = (short)round;
                         if (vb[u] & 2) {
-                            const float dot = nrm[u].x * pl.x + nrm[u].y * pl.y + nrm[u].z * pl.z;
+                            // the gate decides an integer set: FP32 with a fixed order
+                            const float dot = __fmaf_rn(nrm[u].z, pl.z,
+                                                        __fmaf_rn(nrm[u].y, pl.y,
+                                                                  __fmul_rn(nrm[u].x, pl.x)));
                             gated = fabsf(dot) >= prm.cos_gate;
                         }
                     }
                     cnt_g += __popc(__ballot_sync(0xffffffffu, inl[u] && gated));
                     cnt_o += __popc(__ballot_sync(0xffffffffu, inl[u] && !gated));
                     if (inl[u])
-                        mom_values(v, gated ? 0 : NMOM, __fsub_rn(p[u].x, p0.x),
+                        mom_values(vh, vl, gated ? 0 : NMOM, __fsub_rn(p[u].x, p0.x),
                                    __fsub_rn(p[u].y, p0.y), __fsub_rn(p[u].z, p0.z));
                 }
-                const float t = warp_transpose_sum(v, lane);
+                float th, tl;
+                warp_transpose_sum(vh, vl, lane, th, tl);
                 if (lane < 2 * NMOM)
-                    nadd(acc_s, acc_c, t);
+                    df_merge(acc_s, acc_c, th, tl);
             }
         }
         if (lane < 2 * NMOM) {
@@ -1005,10 +1043,8 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
         if ((int)threadIdx.x < 2 * NMOM) {
             const int v = threadIdx.x;
             float ss = sh_s[0][v], cc = sh_c[0][v];
-            for (int w = 1; w < nwarps; ++w) {
-                nadd(ss, cc, sh_s[w][v]);
-                cc = __fadd_rn(cc, sh_c[w][v]);
-            }
+            for (int w = 1; w < nwarps; ++w)
+                df_merge(ss, cc, sh_s[w][v], sh_c[w][v]);
             rec[2 * v] = ss;
             rec[2 * v + 1] = cc;
         } else if ((int)threadIdx.x < 2 * NMOM + 2) {
@@ -1016,7 +1052,7 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
             int nn = 0;
             for (int w = 0; w < nwarps; ++w)
                 nn += sh_n[w][set];
-            rec[36 + set] = __int_as_float(nn);
+            rec[4 * NMOM + set] = __int_as_float(nn);
         }
         __syncthreads();
     }

@@ -314,6 +314,38 @@ class Pipeline:
         self._pending = len(frames)
         self._pending_frames = list(frames)
 
+    def submit_batch_host(self, frames: Sequence[dict], use_graph: bool = True, stream=None):
+        """As submit_batch, with each frame's 'depth' a CPU tensor or numpy array
+        (pinned memory for asynchronous copies) that the call copies to the
+        device itself; it must stay unchanged until collect_batch()."""
+        n = len(frames)
+        arr = (_ffi.Frame * n)()
+        keep = []
+        for i, fr in enumerate(frames):
+            d = fr['depth']
+            if isinstance(d, torch.Tensor):
+                if d.is_cuda or d.dim() != 2 or d.dtype not in _DT or d.stride(1) != 1:
+                    raise ValueError('depth must be a 2-D host tensor with contiguous rows')
+                dt, ptr = _DT[d.dtype], d.data_ptr()
+                pitch = d.stride(0) * d.element_size()
+            else:
+                if d.ndim != 2 or d.dtype not in _NP_DT or d.strides[1] != d.itemsize:
+                    raise ValueError('depth must be a 2-D uint16/float16/float32 array')
+                dt, ptr, pitch = _NP_DT[d.dtype], d.ctypes.data, d.strides[0]
+            keep.append(d)
+            h, w = d.shape
+            lab = fr.get('labels')
+            out = fr.get('depth_out')
+            arr[i] = _ffi.Frame(ctypes.c_void_p(ptr), dt, w, h, pitch, _intr(fr['K']),
+                                int(fr.get('frame_idx', 0)), int(fr.get('iters', -1)),
+                                ctypes.c_void_p(lab.data_ptr()) if lab is not None else None,
+                                ctypes.c_void_p(out.data_ptr()) if out is not None else None)
+        check(self.lib.pm_process_batch_host_async(self._h, arr, n, int(use_graph),
+                                                   _stream_ptr(stream)))
+        self._pending = n
+        self._pending_frames = list(frames)
+        self._host_keep = keep
+
     def collect_batch(self) -> List[Planes]:
         n = self._pending
         mp = self.p.max_planes
@@ -327,6 +359,18 @@ class Pipeline:
                                                  ctypes.sizeof(_ffi.Plane))
             out.append(Planes.from_c(sub, counts[i], self._pending_frames[i].get('labels')))
         return out
+
+    def frame_geometry(self, frame: int, w: int, h: int, device=None, stream=None):
+        """Points, normals (float32 [3, h, w]) and validity (uint8 [h, w]) that
+        the RANSAC stage of the last whole-path call used for batch frame
+        `frame` (of size w x h)."""
+        dev = device if device is not None else torch.device('cuda', torch.cuda.current_device())
+        P = torch.empty((3, h, w), dtype=torch.float32, device=dev)
+        N = torch.empty((3, h, w), dtype=torch.float32, device=dev)
+        V = torch.empty((h, w), dtype=torch.uint8, device=dev)
+        check(self.lib.pm_frame_geometry(self._h, int(frame), _dev(P, 'P'), _dev(N, 'N'),
+                                         _dev(V, 'V'), _stream_ptr(stream)))
+        return P, N, V
 
     def set_tiling(self, iters_per_launch: int = 0, tile_w: int = 0, tile_h: int = 0):
         """Diffusion tiling (bit-identical results for every choice)."""
@@ -355,6 +399,15 @@ class Pipeline:
         ms = (ctypes.c_float * 3)()
         check(self.lib.pm_stage_times(self._h, ms))
         return {'diffuse_ms': ms[0], 'normals_ms': ms[1], 'ransac_ms': ms[2]}
+
+
+def measure_peaks(stream=None) -> dict:
+    """Measured FP32 FMA (TFLOP/s) and ex2 (Top/s) throughput of the current
+    device, and its SM count (pm_measure_peaks)."""
+    f, x, n = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_int(0)
+    check(_ffi.load().pm_measure_peaks(ctypes.byref(f), ctypes.byref(x), ctypes.byref(n),
+                                       _stream_ptr(stream)))
+    return {'fp32_tflops': f.value, 'ex2_tops': x.value, 'sm_count': n.value}
 
 
 def scratch_bytes(max_w, max_h, max_frames, hypotheses, max_planes) -> int:

@@ -3,10 +3,14 @@
 Requests (one depth frame of one camera stream) arrive over time.  The loop
 keeps `n_lanes` execution lanes, each a libpm context with its own CUDA
 stream and room for `max_batch` frames.  Whenever a lane is idle it takes the
-oldest admitted requests (at most one per stream per batch, so a stream's
-frames finish in order), copies their depth from pinned host memory into the
-stream's device buffer for that lane, and enqueues the whole path for the
-batch without waiting (pm_process_batch_async).  Requests that arrive while
+oldest admitted requests (at most one per stream per batch), copies their
+depth from pinned host memory into the stream's device buffer for that lane,
+and enqueues the whole path for the batch without waiting
+(pm_process_batch_async).  With one lane a stream's frames complete in
+arrival order; with several, a later frame of a stream can complete first
+when its lane's batch finishes sooner.  Frames carry no state between them,
+so each result is still exact; a consumer that needs them in order sorts
+them by `Request.k`.  Requests that arrive while
 batches are on the GPU are admitted as memory frees up and go into the next
 batch of whichever lane frees first; with two lanes one batch runs while the
 next is being filled and launched, so their work overlaps on the device.
@@ -55,6 +59,7 @@ class Request:
     t_done: Optional[float] = None
     planes: Optional[Planes] = None
     refused: bool = False
+    failed: bool = False        # admitted, but the launch of its batch failed
     error: Optional[str] = None  # why the request was refused as invalid, or its batch failed
 
 
@@ -65,6 +70,7 @@ class _Lane:
     index: int
     batch: List[Request] = field(default_factory=list)
     event: Optional[torch.cuda.Event] = None
+    seq: int = 0                # launch order of the lane's batch
 
     @property
     def busy(self):
@@ -74,7 +80,11 @@ class _Lane:
 class Server:
     def __init__(self, params: Params, budget_bytes: int = 4 << 30, max_batch: int = 16,
                  n_lanes: int = 2, max_w: int = 1280, max_h: int = 720,
-                 max_wait_s: float = 1.0, use_graph: bool = False):
+                 max_wait_s: float = 1.0, use_graph='full'):
+        """use_graph: True (every batch replays a CUDA graph captured once per
+        batch shape), False (direct launches), or 'full' (graphs for full
+        batches, whose shape repeats under load; direct launches for the
+        partial batches of light load, whose shapes vary)."""
         self.p = params
         self.max_batch = max_batch
         self.max_wait_s = max_wait_s
@@ -146,19 +156,24 @@ class Server:
                     buf = self._stream_buffers(r)[lane.index]
                     buf.copy_(r.depth, non_blocking=True)
                     frames.append(dict(depth=buf, K=r.K, frame_idx=r.frame_idx, iters=r.iters))
-                lane.pipe.submit_batch(frames, use_graph=self.use_graph, stream=lane.stream)
+                graph = (len(batch) == self.max_batch if self.use_graph == 'full'
+                         else bool(self.use_graph))
+                lane.pipe.submit_batch(frames, use_graph=graph, stream=lane.stream)
                 lane.event = torch.cuda.Event()
                 lane.event.record(lane.stream)
         except (PmError, ValueError) as e:
             # nothing was enqueued for the batch: its requests fail, the lane stays free
             for r in batch:
                 r.refused = True
+                r.failed = True
                 r.error = 'batch failed: %s' % e
                 self.in_use -= r.bytes
             self.stats['failed_batches'] += 1
             return
         lane.batch = batch
+        lane.seq = self.stats['batches']
         self.stats['batches'] += 1
+        self.stats['graph_batches'] += int(graph)
         self.stats['batched_frames'] += len(batch)
 
     def _finish(self, lane: _Lane, now: float, done: List[Request]):
@@ -245,9 +260,16 @@ class Server:
                         self._launch(lane, batch)
                         progressed = True
             if not progressed:
+                busy = [l for l in self.lanes if l.busy]
+                if len(busy) == len(self.lanes):
+                    # every lane is busy and nothing can start before one
+                    # finishes: wait for the oldest batch (a blocking event
+                    # wait; arrivals meanwhile are admitted right after it)
+                    min(busy, key=lambda l: l.seq).event.synchronize()
+                    continue
                 if realtime and i < len(reqs) and not admitted and not waiting:
                     nxt = reqs[i].t_arrival - (time.perf_counter() - t0)
-                    if nxt > 0 and not any(l.busy for l in self.lanes):
+                    if nxt > 0 and not busy:
                         time.sleep(min(nxt, 0.002))
                         continue
                 time.sleep(20e-6)
@@ -269,7 +291,8 @@ def summarize(reqs: Sequence[Request], elapsed: float) -> dict:
         return lat[min(len(lat) - 1, int(round(q / 100.0 * (len(lat) - 1))))]
 
     return {'frames': len(ok), 'refused': sum(r.refused for r in reqs),
-            'invalid': sum(r.error is not None for r in reqs),
+            'invalid': sum(r.error is not None and not r.failed for r in reqs),
+            'failed': sum(r.failed for r in reqs),
             'frames_per_s': len(ok) / elapsed if elapsed > 0 else None,
             'p50_ms': pct(50), 'p99_ms': pct(99), 'max_ms': lat[-1] if lat else None,
             'elapsed_s': elapsed}

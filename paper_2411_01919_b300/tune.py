@@ -18,7 +18,9 @@ from typing import Dict, List, Sequence, Tuple
 import torch
 
 # (iterations per launch, tile_w, tile_h)
-# The fused kernel computes, at iteration it of T, a region tile_w + 2 (T - it - 1)
+# For PM4, tiles of (128 - 2T) x (8R - 2T) (R = 4, 6, 8 rows per warp) run the
+# register-blocked kernel; every other tile the shared-memory kernel, which
+# computes, at iteration it of T, a region tile_w + 2 (T - it - 1)
 # columns wide in groups of 32 lanes; widths tile_w = 32 k - 2 (T - 1) fill every
 # group at the first iteration.
 CANDIDATES: List[Tuple[int, int, int]] = [

@@ -541,3 +541,20 @@ def stream_pool(n_streams: int, poses: int, seed: int = 0, workers: int = 0):
             s, k, f = _c5_job(job)
             out[s][k] = f
     return out
+
+
+def _render_job(job):
+    name, args = job
+    return globals()[name](*args)
+
+
+def render_many(name: str, arg_list, workers: int = 0):
+    """[name(*args) for args in arg_list] for one of this module's frame
+    functions (e.g. 'frame_c3'), rendered in a pool of spawned worker
+    processes when workers > 1 (safe to call after CUDA is initialised)."""
+    import multiprocessing as mp
+    jobs = [(name, tuple(a)) for a in arg_list]
+    if workers and workers > 1 and len(jobs) > 1:
+        with mp.get_context('spawn').Pool(min(workers, len(jobs))) as pool:
+            return pool.map(_render_job, jobs, chunksize=1)
+    return [_render_job(j) for j in jobs]

@@ -2,6 +2,7 @@
 bound, against the oracle.  Every decision is integer (8-bit codes from one
 FP32 FMA on both sides, integer Sobel, exact sector test, union-find
 components), so edges and region labels are compared bit-exactly."""
+import ctypes
 import functools
 
 import numpy as np
@@ -157,3 +158,29 @@ def test_argument_errors_raise():
         big = np.zeros((3, 9, 9), np.float32)
         with pytest.raises(PmError):
             pipe.canny(to_dev(big), to_dev(np.ones((9, 9), np.uint8)), 1, 2)
+
+
+def test_canny_allocates_nothing_and_captures_into_a_graph():
+    """The context allocates the edge scratch when it is created, so pm_canny
+    can be captured into a CUDA graph on its first call; the replay gives the
+    same edges as a direct call."""
+    N, V, _ = staircase_normals('c2')
+    _, h, w = N.shape
+    dN, dV = to_dev(N), to_dev(V)
+    with Pipeline(Params(iters=0), w, h, 1) as pipe:
+        E = torch.empty((h, w), dtype=torch.uint8, device=DEV)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                st = pipe.lib.pm_canny(pipe._h, ctypes.c_void_p(dN.data_ptr()),
+                                       ctypes.c_void_p(dV.data_ptr()), w, h, 60, 150,
+                                       ctypes.c_void_p(E.data_ptr()),
+                                       ctypes.c_void_p(s.cuda_stream))
+        assert st == 0, pipe.lib.pm_last_error()
+        g.replay()
+        torch.cuda.synchronize()
+        direct = pipe.canny(dN, dV, 60, 150)
+        assert torch.equal(E, direct)
+    assert np.array_equal(E.cpu().numpy(), oracle.canny(N, V, 60, 150))

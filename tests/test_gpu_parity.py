@@ -18,7 +18,7 @@ import torch
 import oracle
 import synth
 from paper_2411_01919_b300 import Params, Pipeline, PmError
-from e2e_check import check_end_to_end
+from e2e_check import chain_job, check_chain, check_end_to_end, oracle_chain
 
 pytestmark = pytest.mark.gpu
 
@@ -138,6 +138,29 @@ def test_temporal_blocking_is_bit_exact(mode):
         assert np.array_equal(o.view(np.uint32), outs[0].view(np.uint32))
 
 
+@pytest.mark.parametrize('dtype', ['f32', 'u16', 'f16'])
+@pytest.mark.parametrize('shape,pad', [((97, 130), 0), ((64, 256), 0), ((64, 256), 3),
+                                       ((5, 1029), 1), ((300, 7), 0)])
+@pytest.mark.parametrize('mode', [0, 1])
+def test_one_iteration_kernel_is_bit_exact_on_every_encoding(dtype, shape, pad, mode):
+    """The streaming kernel (vector loads when the row pitch allows, element
+    loads otherwise) against the tiled kernel, bit for bit, on every encoding."""
+    h, w = shape
+    enc = _random_depth(h, w, 7 * h + w, dtype=dtype)
+    wide = np.zeros((h, w + pad), dtype=enc.dtype)
+    wide[:, :w] = enc
+    d = to_dev(wide)[:, :w]
+    outs = []
+    for T, tw, th in ((1, 0, 0), (0, 0, 0), (5, 0, 0), (5, 48, 24)):
+        with Pipeline(Params(iters=11, mode=mode, iters_per_launch=T, tile_w=tw, tile_h=th),
+                      w, h) as pipe:
+            outs.append(pipe.diffuse(d).cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o.view(np.uint32), outs[0].view(np.uint32))
+    ref = oracle.diffuse(oracle.decode(enc, dtype, SCALE), 11, LAM, KC, mode)
+    assert np.abs(outs[0].astype(np.float64) - ref).max() <= DIFF_TOL
+
+
 def test_fp16_storage_path_within_bar():
     fr = frame('c3')
     with Pipeline(params('c3'), fr.w, fr.h) as pipe:
@@ -226,8 +249,8 @@ def compare_planes(gpu, orc, exact_labels=True):
         assert ang_deg(a[:3, None], b[:3, None])[0] <= PLANE_DEG
         assert abs(a[3] - b[3]) <= PLANE_OFF
         assert a[3] > 0
-        # the gate decision is FP32 on the GPU, FP64 in the oracle
-        assert abs(int(gpu.n_refit[k]) - int(orc.n_refit[k])) <= max(2, orc.n_refit[k] // 1000)
+    # the refit gate is the same FP32 decision on both sides
+    assert np.array_equal(gpu.n_refit, orc.n_refit)
 
 
 @pytest.mark.parametrize('name', ['c1', 'c2', 'c3'])
@@ -377,8 +400,11 @@ def test_box_inclusion_counts_whole_segments(z0, w, h):
 # the whole path
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize('name', ['c1', 'c2'])
+@pytest.mark.parametrize('name', ['c1', 'c2', 'c3'])
 def test_process_frame_matches_oracle(name):
+    """The whole path on one frame, stage by stage with teacher forcing (each
+    oracle stage on the GPU's output of the stage before: e2e_check), plus the
+    structural comparison with the oracle's own chain."""
     fr = frame(name)
     p = params(name)
     out = torch.empty((fr.h, fr.w), dtype=torch.float32, device=DEV)
@@ -386,16 +412,22 @@ def test_process_frame_matches_oracle(name):
     with Pipeline(p, fr.w, fr.h) as pipe:
         g = pipe.process_batch([dict(depth=to_dev(fr.encoded), K=fr.cam.intrinsics, frame_idx=0,
                                      labels=lab, depth_out=out)], use_graph=False)[0]
+        P, N, V = (t.cpu().numpy() for t in pipe.frame_geometry(0, fr.w, fr.h))
         single = pipe.process_frame(to_dev(fr.encoded), fr.cam.intrinsics, frame_idx=0)
-    res = oracle.process_frame(fr.encoded, fr.dtype, fr.cam.intrinsics, p.iters, LAM, KC,
-                               hypotheses=p.hypotheses, max_planes=p.max_planes,
-                               min_inliers=p.min_inliers, seed=p.seed, frame_idx=0,
-                               depth_scale=SCALE)
-    assert np.abs(out.cpu().numpy().astype(np.float64) - res.depth).max() <= DIFF_TOL
-    agree = check_end_to_end(fr, g, lab.cpu().numpy(), res.ransac,
-                             min_big=1000 if name == 'c2' else 300)
-    print('%s: end-to-end %d planes (oracle %d), label agreement %.5f'
-          % (name, len(g.planes), len(res.ransac.planes), agree))
+    job = chain_job(fr, p, p.iters, 0, out.cpu().numpy(), P, N, V)
+    r = oracle_chain(job)
+    n = check_chain(r, g, lab.cpu().numpy(), DIFF_TOL, name)
+    print('%s: %d planes equal to the oracle stage by stage; diffusion %.2e m, normals %.2e deg'
+          % (name, n, r['diff_err'], r['normal_err']))
+    if name != 'c3':
+        res = oracle.process_frame(fr.encoded, fr.dtype, fr.cam.intrinsics, p.iters, LAM, KC,
+                                   hypotheses=p.hypotheses, max_planes=p.max_planes,
+                                   min_inliers=p.min_inliers, seed=p.seed, frame_idx=0,
+                                   depth_scale=SCALE)
+        agree = check_end_to_end(fr, g, lab.cpu().numpy(), res.ransac,
+                                 min_big=300 if name == 'c1' else 1000)
+        print('%s: own-chain oracle %d planes, label agreement %.5f'
+              % (name, len(res.ransac.planes), agree))
     assert np.array_equal(single.planes, g.planes)
     assert np.array_equal(single.labels.cpu().numpy(), lab.cpu().numpy())
 
@@ -458,6 +490,32 @@ def test_host_entry_equals_device_entry():
     assert np.array_equal(d.labels.cpu().numpy(), lab)
 
 
+def test_host_batch_entry_equals_device_batch():
+    """pm_process_batch_host_async (depth in pinned or pageable host memory,
+    copied by the call) gives the device batch's results bit for bit, with
+    and without graph replay."""
+    frames = [synth.frame_c4(5, i) for i in range(6)]
+    p = Params(iters=20, hypotheses=512, max_planes=6, min_inliers=100, seed=4)
+    mw, mh = max(f.w for f in frames), max(f.h for f in frames)
+
+    def desc(depths):
+        return [dict(depth=depths[i], K=f.cam.intrinsics, frame_idx=50 + i, iters=f.meta['iters'])
+                for i, f in enumerate(frames)]
+
+    with Pipeline(p, mw, mh, len(frames)) as pipe:
+        ref = pipe.process_batch(desc([to_dev(f.encoded) for f in frames]), use_graph=False)
+        pinned = [torch.from_numpy(f.encoded).pin_memory() for f in frames]
+        for depths, use_graph in ((pinned, False), (pinned, True), (pinned, True),
+                                  ([f.encoded for f in frames], True)):
+            pipe.submit_batch_host(desc(depths), use_graph=use_graph)
+            torch.cuda.synchronize()
+            got = pipe.collect_batch()
+            for a, b in zip(got, ref):
+                assert np.array_equal(a.planes.view(np.uint64), b.planes.view(np.uint64))
+                assert np.array_equal(a.hyp_index, b.hyp_index)
+                assert np.array_equal(a.n_inliers, b.n_inliers)
+
+
 # ---------------------------------------------------------------------------
 # degenerate inputs and argument errors
 # ---------------------------------------------------------------------------
@@ -492,6 +550,33 @@ def test_argument_errors_raise():
             pipe.diffuse(torch.zeros((4, 4), dtype=torch.float64, device=DEV))
         with pytest.raises(PmError):
             pipe.process_batch([dict(depth=torch.zeros((4, 4), device=DEV), K=(0, 1, 0, 0))])
+
+
+@pytest.mark.parametrize('ipl', [0, 1])
+def test_calls_on_the_scratch_refuse_while_a_batch_is_pending(ipl):
+    """While a batch from the asynchronous entry point may still be running,
+    every call that would write the context's scratch returns PM_ERR_STATE
+    (the one-iteration diffusion path included) and launches nothing."""
+    from paper_2411_01919_b300 import _ffi
+    fr = frame('c1')
+    p = params('c1', iters_per_launch=ipl)
+    with Pipeline(p, fr.w, fr.h) as pipe:
+        d = to_dev(fr.encoded)
+        z0 = pipe.diffuse(d).clone()
+        pipe.submit_batch([dict(depth=d, K=fr.cam.intrinsics, frame_idx=3)])
+        calls = [lambda: pipe.diffuse(d),
+                 lambda: pipe.process_frame_host(fr.encoded, fr.cam.intrinsics),
+                 lambda: pipe.process_frame(d, fr.cam.intrinsics),
+                 lambda: pipe.frame_geometry(0, fr.w, fr.h)]
+        for call in calls:
+            with pytest.raises(PmError) as e:
+                call()
+            assert e.value.status == _ffi.PM_ERR_STATE
+        torch.cuda.synchronize()
+        got = pipe.collect_batch()[0]
+        ref = pipe.process_frame(d, fr.cam.intrinsics, frame_idx=3)
+        assert np.array_equal(got.planes, ref.planes)
+        assert torch.equal(pipe.diffuse(d), z0)
 
 
 def test_scratch_allocation_failure_is_reported_and_recoverable():

@@ -68,6 +68,21 @@ def test_saturated_mix_batches_and_matches_alone():
         assert np.array_equal(r.planes.planes, ref[(r.stream, r.k)].planes)
 
 
+def test_full_batches_replay_graphs_and_match_alone():
+    """Under saturation every batch is full, so the lanes replay CUDA graphs
+    (captured once per lane and batch shape); results equal each frame alone."""
+    fr, host = pool(8, 2)
+    reqs = make_reqs(fr, host, [(s, k, 0.0) for k in range(4) for s in range(8)], 2)
+    srv = Server(P, budget_bytes=8 << 30, max_batch=4, n_lanes=2)
+    out = srv.run(reqs, realtime=False)
+    srv.close()
+    assert srv.stats['graph_batches'] == srv.stats['batches'] == len(reqs) // 4
+    ref = alone(fr, out)
+    for r in out:
+        a, b = r.planes, ref[(r.stream, r.k)]
+        assert np.array_equal(a.planes, b.planes) and np.array_equal(a.n_inliers, b.n_inliers)
+
+
 def test_malformed_requests_are_refused_alone():
     """Requests that cannot be served -- bad intrinsics, a frame larger than
     the lanes, a stream that changes its frame size -- are refused with a

@@ -67,7 +67,9 @@ def test_summary_counts_and_percentiles():
     bad.refused, bad.error = True, 'intrinsics must be finite with fx, fy > 0'
     late = req(torch.zeros((2, 2)))
     late.refused = True
-    s = summarize(rs + [bad, late], elapsed=2.0)
-    assert s['frames'] == 101 and s['refused'] == 2 and s['invalid'] == 1
+    lost = req(torch.zeros((2, 2)))
+    lost.refused, lost.failed, lost.error = True, True, 'batch failed: PM_ERR_CUDA'
+    s = summarize(rs + [bad, late, lost], elapsed=2.0)
+    assert s['frames'] == 101 and s['refused'] == 3 and s['invalid'] == 1 and s['failed'] == 1
     assert s['p50_ms'] == 50.0 and s['p99_ms'] == 99.0 and s['max_ms'] == 100.0
     assert s['frames_per_s'] == 50.5

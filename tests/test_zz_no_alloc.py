@@ -7,7 +7,8 @@ For them libpm offers one entry point that needs no context and allocates
 nothing: its working iterate lives in a fixed device array inside the library.
 These tests call it through the C ABI and compare its output with the regular
 pm_diffuse on two calls in a row (the second call reuses the array the first
-one left behind), and check that an oversize image is refused.
+one left behind), with the FP64 oracle on ragged shapes, zero iterations and
+a padded row pitch, and check that an oversize image is refused.
 """
 import ctypes
 
@@ -15,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 from paper_2411_01919_b300 import Params, Pipeline, _ffi
 
@@ -50,6 +52,46 @@ def test_noalloc_matches_pm_diffuse_on_two_calls_in_a_row():
         err = (out.double() - ref.double()).abs().max().item()
         assert err <= DIFF_TOL, (fr.meta, err)
         assert torch.equal(out == 0, ref == 0)
+
+
+def ragged_depth(seed, h, w, dtype):
+    """A tilted plane with bumps and 3% holes in the given sensor encoding."""
+    rng = np.random.default_rng(seed)
+    v, u = np.mgrid[0:h, 0:w]
+    z = 1.2 + 0.004 * u + 0.002 * v + 0.01 * np.sin(u / 3.0) + rng.normal(0, 0.003, (h, w))
+    z[rng.random((h, w)) < 0.03] = 0.0
+    if dtype == 'u16':
+        return np.round(z * 1000.0).astype(np.uint16)
+    if dtype == 'f16':
+        return z.astype(np.float16)
+    return z.astype(np.float32)
+
+
+@pytest.mark.parametrize('h,w,dtype,iters,mode,pad', [
+    (37, 53, 'u16', 0, 0, 0),      # zero iterations: decode only
+    (61, 97, 'u16', 7, 1, 13),     # Alg. 1 form, u16 rows inside a wider buffer
+    (45, 33, 'f16', 9, 1, 0),      # Alg. 1 form on FP16 storage
+    (130, 257, 'f32', 12, 0, 3),   # odd width, padded pitch
+    (1, 300, 'u16', 4, 0, 0),      # a single row
+])
+def test_noalloc_matches_the_oracle(h, w, dtype, iters, mode, pad):
+    enc = ragged_depth(h * 1000 + w, h, w, dtype)
+    p = Params(iters=iters, mode=mode)
+    wide = np.zeros((h, w + pad), dtype=enc.dtype)
+    wide[:, :w] = enc
+    d = torch.from_numpy(wide).cuda()[:, :w]          # pitch = (w + pad) * element size
+    f32 = lambda x: float(np.float32(x))
+    ref = oracle.diffuse(oracle.decode(enc, dtype, f32(p.depth_scale)), iters, f32(p.lam),
+                         f32(p.K), mode)
+    for _ in range(2):                                  # two calls in a row
+        out = torch.full((h, w), -1.0, dtype=torch.float32, device='cuda')
+        _ffi.check(noalloc_diffuse(d, dtype, p, out))
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.float64)
+        assert np.abs(got - ref).max() <= DIFF_TOL
+        assert np.array_equal(got == 0, ref == 0)
+    with Pipeline(p, w, h) as pipe:
+        assert torch.equal(pipe.diffuse(d), out)
 
 
 def test_noalloc_refuses_images_above_its_limit():
