@@ -426,6 +426,18 @@ pm_status pm_diffuse_noalloc(const void *depth, int dtype, int w, int h, int pit
                              const pm_diffusion_params *dp, float depth_scale, float *out,
                              void *stream);
 
+/* Bounds checks of the bounds-checking build (libpm built with
+ * PM_DEBUG_BOUNDS, a stand-in for a memory sanitizer): every instrumented
+ * global access of the diffusion, normal and RANSAC kernels checks its index
+ * against the extent of its buffer, skips the access when it lies outside
+ * and records the first such index in a device status word; nothing traps.
+ * This call synchronises the device, returns the first recorded violation in
+ * *status (0 if none; otherwise bit 63 set, bits 48-62 the source site -- file
+ * id 1 diffusion, 2 normals, 3 RANSAC, times 4096, plus the line -- and bits
+ * 0-47 the offending index) and clears the words.  In the release build it
+ * returns PM_ERR_STATE and sets *status to 0. */
+pm_status pm_debug_bounds(unsigned long long *status);
+
 /* Text of the calling thread's last error ("" if none). */
 const char *pm_last_error(void);
 

@@ -80,9 +80,9 @@ EXPORTS = ['pm_create', 'pm_destroy', 'pm_diffuse', 'pm_normals', 'pm_ransac_pla
            'pm_stage_times', 'pm_kernel_stats', 'pm_ransac_regions', 'pm_canny', 'pm_segment',
            'pm_map_create', 'pm_map_destroy', 'pm_map_integrate', 'pm_map_size',
            'pm_map_polygon', 'pm_map_drift', 'pm_diffuse_noalloc', 'pm_measure_peaks',
-           'pm_set_tiling', 'pm_last_error']
+           'pm_set_tiling', 'pm_debug_bounds', 'pm_last_error']
 
-_lib = None
+_libs = {}
 
 
 class PmError(RuntimeError):
@@ -92,10 +92,10 @@ class PmError(RuntimeError):
 
 
 def load(path: str = LIB_PATH):
-    """Load libpm.so.  Raises if the library is missing: there is no fallback."""
-    global _lib
-    if _lib is not None:
-        return _lib
+    """Load libpm.so (or another build of it, e.g. the bounds-checking one).
+    Raises if the library is missing: there is no fallback."""
+    if path in _libs:
+        return _libs[path]
     if not os.path.exists(path):
         raise ImportError('libpm.so not found at %s; build it with '
                           '`python -m paper_2411_01919_b300.build`' % path)
@@ -133,13 +133,14 @@ def load(path: str = LIB_PATH):
         'pm_diffuse_noalloc': ([vp, i, i, i, i, P(DiffusionParams), ctypes.c_float, vp, vp], i),
         'pm_measure_peaks': ([P(ctypes.c_double), P(ctypes.c_double), P(i), vp], i),
         'pm_set_tiling': ([vp, i, i, i], i),
+        'pm_debug_bounds': ([P(ctypes.c_ulonglong)], i),
         'pm_last_error': ([], ctypes.c_char_p),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = res
-    _lib = L
+    _libs[path] = L
     return L
 
 

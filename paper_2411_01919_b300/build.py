@@ -18,27 +18,36 @@ def _nvcc():
     return 'nvcc'
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(HERE, '..', 'include', 'pm.h'))
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
+# the bounds-checking build (PM_DEBUG_BOUNDS): same sources, every instrumented
+# kernel access checked against its buffer (see pm_debug_bounds in pm.h)
+LIB_BOUNDS = os.path.join(HERE, 'libpm_bounds.so')
+
+
+def build(force: bool = False, verbose: bool = False, bounds: bool = False) -> str:
+    lib = LIB_BOUNDS if bounds else LIB
+    if not force and not _stale(lib):
+        return lib
     cmd = [_nvcc(), *ARCH, '-O3', '-lineinfo', '-std=c++17', '-shared', '-Xcompiler', '-fPIC',
-           '-Xcompiler', '-Wall', '-o', LIB + '.tmp']
+           '-Xcompiler', '-Wall', '-o', lib + '.tmp']
+    if bounds:
+        cmd += ['-DPM_DEBUG_BOUNDS']
     if verbose:
         cmd += ['-Xptxas', '-v']
     cmd += [os.path.join(CSRC, s) for s in SOURCES]
     subprocess.run(cmd, check=True)
-    os.replace(LIB + '.tmp', LIB)
-    return LIB
+    os.replace(lib + '.tmp', lib)
+    return lib
 
 
 if __name__ == '__main__':
-    print(build(force='--force' in sys.argv, verbose='-v' in sys.argv))
+    print(build(force='--force' in sys.argv, verbose='-v' in sys.argv,
+                bounds='--bounds' in sys.argv))

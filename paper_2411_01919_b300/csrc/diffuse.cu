@@ -32,6 +32,7 @@
 // J_q = I_p of the oracle (no flux across a hole or the border) without a
 // branch; a hole receives only zero fluxes and keeps its value.  The last
 // launch writes FP32 depth (hi + lo rounded to nearest; HOLE -> 0).
+#define PM_FILE_ID 1
 #include "pm_internal.cuh"
 
 namespace pm {
@@ -101,6 +102,8 @@ __device__ __forceinline__ float2 update_alg1(float2 Ip, float2 In, float2 Is, f
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned load_raw(const DiffFrame &f, int x, int y)
 {
+    if (!(PM_INB(y, f.h) && PM_INB(x, f.w)))
+        return 0u;
     const char *row = (const char *)f.src + (long long)y * f.src_pitch;
     if (f.src_dtype == PM_F32_M)
         return __float_as_uint(__ldg(reinterpret_cast<const float *>(row) + x));
@@ -117,7 +120,8 @@ __device__ __forceinline__ float2 decode(unsigned r, float scale)
     if (DT == PM_U16_MM) {
         if (!r)
             return make_float2(HOLE, 0.0f);
-        const float qf = (float)r;
+        // q exactly as a float: the bits of 2^23 + q (q < 2^16) minus 2^23
+        const float qf = __fsub_rn(__uint_as_float(0x4B000000u | r), 8388608.0f);
         const float hi = __fmul_rn(qf, scale);
         return make_float2(hi, __fmaf_rn(qf, scale, -hi));
     }
@@ -192,7 +196,8 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
                         const int x = x0 + lane + 32 * g, gx = tx0 - T + x;
                         const bool ok = row_ok && x < SX && gx >= 0 && gx < f.w;
                         rv[r][g] = ok ? load_raw(f, gx, gy) : 0u;
-                        lv[r][g] = ok && has_lo ? __ldg(f.lo_in + (long long)gy * f.w + gx) : 0.0f;
+                        lv[r][g] = ok && has_lo && PM_INB((long long)gy * f.w + gx, (long long)f.w * f.h)
+                                       ? __ldg(f.lo_in + (long long)gy * f.w + gx) : 0.0f;
                     }
                 }
 #pragma unroll
@@ -201,7 +206,7 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
                         const int x = x0 + lane + 32 * g;
-                        if (y < SY && x < SX) {
+                        if (y < SY && x < SX && PM_INB(y * SX + x, NC)) {
                             const float2 v = decode_rt(rv[r][g], f.src_dtype, f.scale);
                             Hs[y * SX + x] = v.x;
                             A[y * SX + x] = has_lo ? lv[r][g] : v.y;
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(256) k_diffuse_tiles(const DiffFrame *__restri
         for (int x = lane; x < dx; x += 32) {
             const int gx = tx0 + x;
             const int k = (y + T) * SX + x + T;
-            if (gx < f.w)
+            if (gx < f.w && PM_INB((long long)gy * f.w + gx, (long long)f.w * f.h) && PM_INB(k, NC))
                 f.dst[(long long)gy * f.w + gx] =
                     f.dst_lo ? A[k] : depth_out(make_float2(Hs[k], A[k]));
         }
@@ -317,15 +322,15 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b)
     return r;
 }
 __device__ __forceinline__ f2 neg2(f2 a) { return a ^ 0x8000000080000000ull; }
-// a b rounded once, for a product that feeds an addition: computed as
-// fma(a, b, -0), which equals the rounded product exactly (an exact product
-// plus -0 is itself) and leaves no separate multiply for the compiler to fuse
-// into the addition that follows (one rounding instead of two).
+// a b rounded once, for a product that feeds an addition: two scalar
+// multiplies.  The compiler may fuse a packed multiply into the packed
+// addition that consumes it (one rounding instead of two), which would break
+// the bit-identity with the scalar kernels; scalar multiplies followed by a
+// packed addition are kept apart.
 __device__ __forceinline__ f2 mulr2(f2 a, f2 b)
 {
-    f2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(0x8000000080000000ull));
-    return r;
+    const float2 x = unpk(a), y = unpk(b);
+    return pk(__fmul_rn(x.x, y.x), __fmul_rn(x.y, y.y));
 }
 
 // Two link fluxes at once, each exactly link_flux(p, q) of its half:
@@ -355,11 +360,11 @@ __device__ __forceinline__ f2 link_flux2(f2 ph, f2 pl, f2 qh, f2 ql, f2 c2)
 // out read them, and the output region lies inside every iteration's exact
 // region.
 template <int R>
-__global__ void __launch_bounds__(256, 2) k_diffuse_regs(const DiffFrame *__restrict__ frames,
+__global__ void __launch_bounds__(256, 3) k_diffuse_regs(const DiffFrame *__restrict__ frames,
                                                           int n_frames, int T, float lam, float c)
 {
-    __shared__ float4 bnd_lo[2][2][8][32];   // [buffer][first / last row][warp][lane]
-    __shared__ float4 bnd_hi[2][8][32];      // [first / last row][warp][lane]
+    __shared__ float4 hs[8 * R][32];            // hi parts: [tile row][lane] (4 columns)
+    __shared__ float4 bnd_lo[2][2][8][32];      // [buffer][first / last row][warp][lane]
     const int tile = blockIdx.x;
     int lo_f = 0, hi_f = n_frames - 1;
     while (lo_f < hi_f) {
@@ -378,7 +383,7 @@ __global__ void __launch_bounds__(256, 2) k_diffuse_regs(const DiffFrame *__rest
     const int x0 = tx0 + 4 * lane;
     const bool has_lo = f.lo_in != nullptr;
 
-    f2 h01[R], h23[R], l01[R], l23[R];          // the thread's cells, row r
+    f2 l01[R], l23[R];                          // the thread's lo parts, row r
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int gy = ty0 + w * R + r;
@@ -389,28 +394,15 @@ __global__ void __launch_bounds__(256, 2) k_diffuse_regs(const DiffFrame *__rest
             const bool ok = gy >= 0 && gy < f.h && gx >= 0 && gx < f.w;
             const float2 d = decode_rt(ok ? load_raw(f, gx, gy) : 0u, f.src_dtype, f.scale);
             hv[k] = d.x;
-            lv[k] = has_lo ? (ok ? __ldg(f.lo_in + (long long)gy * f.w + gx) : 0.0f) : d.y;
+            lv[k] = has_lo ? (ok && PM_INB((long long)gy * f.w + gx, (long long)f.w * f.h)
+                                  ? __ldg(f.lo_in + (long long)gy * f.w + gx) : 0.0f)
+                           : d.y;
         }
-        h01[r] = pk(hv[0], hv[1]);
-        h23[r] = pk(hv[2], hv[3]);
+        hs[w * R + r][lane] = make_float4(hv[0], hv[1], hv[2], hv[3]);
         l01[r] = pk(lv[0], lv[1]);
         l23[r] = pk(lv[2], lv[3]);
     }
-    // static neighbours: hi of the rows above and below the warp's rows
-    // (warps 0 and 7: outside the tile, holes)
-    bnd_hi[0][w][lane] = make_float4(lo_of(h01[0]), hi_of(h01[0]), lo_of(h23[0]), hi_of(h23[0]));
-    bnd_hi[1][w][lane] = make_float4(lo_of(h01[R - 1]), hi_of(h01[R - 1]), lo_of(h23[R - 1]),
-                                     hi_of(h23[R - 1]));
-    __syncthreads();
-    f2 hN01, hN23, hS01, hS23;
-    {
-        const float4 a = w > 0 ? bnd_hi[1][w - 1][lane] : make_float4(HOLE, HOLE, HOLE, HOLE);
-        const float4 b = w < 7 ? bnd_hi[0][w + 1][lane] : make_float4(HOLE, HOLE, HOLE, HOLE);
-        hN01 = pk(a.x, a.y);
-        hN23 = pk(a.z, a.w);
-        hS01 = pk(b.x, b.y);
-        hS23 = pk(b.z, b.w);
-    }
+    const float4 HOLE4 = make_float4(HOLE, HOLE, HOLE, HOLE);
     const f2 c2 = pk(c, c), lam2 = pk(lam, lam);
     constexpr int H2 = R / 2;
     for (int it = 0; it < f.n_iters; ++it) {
@@ -419,21 +411,24 @@ __global__ void __launch_bounds__(256, 2) k_diffuse_regs(const DiffFrame *__rest
                                               hi_of(l23[0]));
         bnd_lo[buf][1][w][lane] = make_float4(lo_of(l01[R - 1]), hi_of(l01[R - 1]),
                                               lo_of(l23[R - 1]), hi_of(l23[R - 1]));
-        __syncthreads();
+        __syncthreads();   // (the first one also publishes the hi tile)
         const float4 a = w > 0 ? bnd_lo[buf][1][w - 1][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 b = w < 7 ? bnd_lo[buf][0][w + 1][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const f2 lN01 = pk(a.x, a.y), lN23 = pk(a.z, a.w);
-        const f2 lS01 = pk(b.x, b.y), lS23 = pk(b.z, b.w);
+        const float4 hn = w > 0 ? hs[w * R - 1][lane] : HOLE4;
+        const float4 hsb = w < 7 ? hs[w * R + R][lane] : HOLE4;
         // Two chains walk the warp's rows top to bottom, rows [0, H2) and
         // [H2, R), independent of each other (more instructions in flight).
         // The flux between rows H2 - 1 and H2 is taken before either is
         // updated: it is the second chain's first north flux and, negated,
         // the first chain's last south flux.
-        const f2 fB01 = link_flux2(h01[H2], l01[H2], h01[H2 - 1], l01[H2 - 1], c2);
-        const f2 fB23 = link_flux2(h23[H2], l23[H2], h23[H2 - 1], l23[H2 - 1], c2);
+        float4 hc[2], hb = hs[w * R + H2 - 1][lane];
+        hc[0] = hs[w * R][lane];
+        hc[1] = hs[w * R + H2][lane];
+        const f2 fB01 = link_flux2(pk(hc[1].x, hc[1].y), l01[H2], pk(hb.x, hb.y), l01[H2 - 1], c2);
+        const f2 fB23 = link_flux2(pk(hc[1].z, hc[1].w), l23[H2], pk(hb.z, hb.w), l23[H2 - 1], c2);
         f2 fN01[2], fN23[2];
-        fN01[0] = link_flux2(h01[0], l01[0], hN01, lN01, c2);
-        fN23[0] = link_flux2(h23[0], l23[0], hN23, lN23, c2);
+        fN01[0] = link_flux2(pk(hc[0].x, hc[0].y), l01[0], pk(hn.x, hn.y), pk(a.x, a.y), c2);
+        fN23[0] = link_flux2(pk(hc[0].z, hc[0].w), l23[0], pk(hn.z, hn.w), pk(a.z, a.w), c2);
         fN01[1] = fB01;
         fN23[1] = fB23;
 #pragma unroll
@@ -441,24 +436,26 @@ __global__ void __launch_bounds__(256, 2) k_diffuse_regs(const DiffFrame *__rest
 #pragma unroll
             for (int ch = 0; ch < 2; ++ch) {
                 const int r = ch * H2 + j;
+                const float4 h = hc[ch];
+                const f2 h01 = pk(h.x, h.y), h23 = pk(h.z, h.w);
+                float4 hnext = h;   // hi of row r + 1 (the next step's row)
                 f2 fS01, fS23;
                 if (j + 1 < H2) {
                     const int rs = j + 1 < H2 ? r + 1 : r;
-                    fS01 = link_flux2(h01[r], l01[r], h01[rs], l01[rs], c2);
-                    fS23 = link_flux2(h23[r], l23[r], h23[rs], l23[rs], c2);
+                    hnext = hs[w * R + rs][lane];
+                    fS01 = link_flux2(h01, l01[r], pk(hnext.x, hnext.y), l01[rs], c2);
+                    fS23 = link_flux2(h23, l23[r], pk(hnext.z, hnext.w), l23[rs], c2);
                 } else if (ch == 0) {
                     fS01 = neg2(fB01);
                     fS23 = neg2(fB23);
                 } else {
-                    fS01 = link_flux2(h01[r], l01[r], hS01, lS01, c2);
-                    fS23 = link_flux2(h23[r], l23[r], hS23, lS23, c2);
+                    fS01 = link_flux2(h01, l01[r], pk(hsb.x, hsb.y), pk(b.x, b.y), c2);
+                    fS23 = link_flux2(h23, l23[r], pk(hsb.z, hsb.w), pk(b.z, b.w), c2);
                 }
-                // horizontal: (W of column 0, E of column 3) and (0-1, 2-3)
-                // packed, 1-2 alone
                 // the column left of the lane's and right of it (lanes 0 and
                 // 31: outside the tile, holes)
-                float hW = __shfl_up_sync(0xffffffffu, hi_of(h23[r]), 1);
-                float hE = __shfl_down_sync(0xffffffffu, lo_of(h01[r]), 1);
+                float hW = __shfl_up_sync(0xffffffffu, h.w, 1);
+                float hE = __shfl_down_sync(0xffffffffu, h.x, 1);
                 float lW = __shfl_up_sync(0xffffffffu, hi_of(l23[r]), 1);
                 float lE = __shfl_down_sync(0xffffffffu, lo_of(l01[r]), 1);
                 if (lane == 0) {
@@ -469,13 +466,13 @@ __global__ void __launch_bounds__(256, 2) k_diffuse_regs(const DiffFrame *__rest
                     hE = HOLE;
                     lE = 0.0f;
                 }
-                const float h0 = lo_of(h01[r]), h1 = hi_of(h01[r]), h2 = lo_of(h23[r]),
-                            h3 = hi_of(h23[r]);
                 const float v0 = lo_of(l01[r]), v1 = hi_of(l01[r]), v2 = lo_of(l23[r]),
                             v3 = hi_of(l23[r]);
-                const f2 fWE = link_flux2(pk(h0, h3), pk(v0, v3), pk(hW, hE), pk(lW, lE), c2);
-                const f2 fIn = link_flux2(pk(h0, h2), pk(v0, v2), pk(h1, h3), pk(v1, v3), c2);
-                const float f12 = link_flux(make_float2(h1, v1), make_float2(h2, v2), c);
+                // horizontal: (W of column 0, E of column 3) and (0-1, 2-3)
+                // packed, 1-2 alone
+                const f2 fWE = link_flux2(pk(h.x, h.w), pk(v0, v3), pk(hW, hE), pk(lW, lE), c2);
+                const f2 fIn = link_flux2(pk(h.x, h.z), pk(v0, v2), pk(h.y, h.w), pk(v1, v3), c2);
+                const float f12 = link_flux(make_float2(h.y, v1), make_float2(h.z, v2), c);
                 const float fW0 = lo_of(fWE), fE3 = hi_of(fWE);
                 const float f01 = lo_of(fIn), f23 = hi_of(fIn);
                 // column k: W flux, then E flux, as pm4_combine sums them
@@ -485,6 +482,7 @@ __global__ void __launch_bounds__(256, 2) k_diffuse_regs(const DiffFrame *__rest
                 l23[r] = add2(l23[r], mulr2(lam2, add2(add2(add2(fN23[ch], fS23), fW23), fE23)));
                 fN01[ch] = neg2(fS01);
                 fN23[ch] = neg2(fS23);
+                hc[ch] = hnext;
             }
         }
     }
@@ -495,12 +493,14 @@ __global__ void __launch_bounds__(256, 2) k_diffuse_regs(const DiffFrame *__rest
         const int gy = ty0 + ty;
         if (ty < T || ty >= 8 * R - T || gy >= f.h)
             continue;
-        const float hv[4] = {lo_of(h01[r]), hi_of(h01[r]), lo_of(h23[r]), hi_of(h23[r])};
+        const float4 h = hs[ty][lane];
+        const float hv[4] = {h.x, h.y, h.z, h.w};
         const float lv[4] = {lo_of(l01[r]), hi_of(l01[r]), lo_of(l23[r]), hi_of(l23[r])};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int tx = 4 * lane + k, gx = x0 + k;
-            if (tx >= T && tx < 128 - T && gx < f.w)
+            if (tx >= T && tx < 128 - T && gx < f.w &&
+                PM_INB((long long)gy * f.w + gx, (long long)f.w * f.h))
                 f.dst[(long long)gy * f.w + gx] =
                     f.dst_lo ? lv[k] : depth_out(make_float2(hv[k], lv[k]));
         }
@@ -519,9 +519,16 @@ __global__ void __launch_bounds__(256, 2) k_diffuse_regs(const DiffFrame *__rest
 // adjacent lanes by shuffle, and lanes 0 and 31 read the column just outside
 // the warp.  Every link enters the sum of pm4_combine with the same value and
 // in the same order as in the tiled kernel, so the results are bit-identical.
-// Two rows below the current one are in flight while it is computed.
+// Two rows below the current one are in flight while it is computed, and the
+// row STREAM_PF further down is prefetched into L2.
 constexpr int SCOLS = 4;
 constexpr int STREAM_ROWS = 16;
+constexpr int STREAM_PF = 4;
+
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 // One row of a lane's columns as read from memory: encoding containers, lo
 // parts, and the column outside the warp (lanes 0 and 31).
@@ -547,7 +554,7 @@ __device__ __forceinline__ void load_row(const DiffFrame &f, int y, int x0, int 
         return;
     const char *row = (const char *)f.src + (long long)y * f.src_pitch;
     const bool full = x0 + SCOLS <= f.w;
-    if (full && vsrc) {
+    if (full && vsrc && PM_INB(x0 + SCOLS - 1, f.w) && PM_INB(x0, f.w)) {
         if (DT == PM_F32_M) {
             const uint4 v = __ldg(reinterpret_cast<const uint4 *>(row) + (x0 >> 2));
             o.r[0] = v.x; o.r[1] = v.y; o.r[2] = v.z; o.r[3] = v.w;
@@ -564,16 +571,16 @@ __device__ __forceinline__ void load_row(const DiffFrame &f, int y, int x0, int 
     }
     if (HAS_LO) {
         const float *lrow = f.lo_in + (long long)y * f.w;
-        if (full && vlo) {
+        if (full && vlo && PM_INB(x0 + SCOLS - 1, f.w) && PM_INB(x0, f.w)) {
             const float4 v = __ldg(reinterpret_cast<const float4 *>(lrow + x0));
             o.l[0] = v.x; o.l[1] = v.y; o.l[2] = v.z; o.l[3] = v.w;
         } else {
 #pragma unroll
             for (int k = 0; k < SCOLS; ++k)
-                if (x0 + k < f.w)
+                if (x0 + k < f.w && PM_INB(x0 + k, f.w))
                     o.l[k] = __ldg(lrow + x0 + k);
         }
-        if (edge)
+        if (edge && PM_INB(xe, f.w))
             o.le = __ldg(lrow + xe);
     }
     if (edge)
@@ -600,7 +607,7 @@ __device__ __forceinline__ void decode_row(const RowRaw &o, float scale, float2 
 // the north fluxes of the row (PM4).
 struct StreamState {
     float2 u[SCOLS], a[SCOLS], ae;
-    float fN[SCOLS];
+    f2 fN01, fN23;      // north fluxes of columns 0-1 and 2-3 (PM4)
 };
 
 // Row y of the lane's columns, its row below already read into `below`, which
@@ -613,8 +620,19 @@ __device__ __forceinline__ void stream_row(const DiffFrame &f, int y, int x0, in
     const float2 Z = make_float2(HOLE, 0.0f);
     float2 d[SCOLS], de;
     decode_row<DT, HAS_LO>(below, f.scale, d, de);
-    if (more)
+    if (more) {
         load_row<DT, HAS_LO>(f, y + 3, x0, xe, edge, vsrc, vlo, below);
+        // the row STREAM_PF below that into L2, one request per 128-byte line
+        const int yp = y + 3 + STREAM_PF;
+        if (yp < f.h && x0 < f.w) {
+            constexpr int SRC_LANES = 128 / (SCOLS * (DT == PM_F32_M ? 4 : 2));
+            if (lane % SRC_LANES == 0)
+                prefetch_l2((const char *)f.src + (long long)yp * f.src_pitch +
+                            (long long)x0 * (DT == PM_F32_M ? 4 : 2));
+            if (HAS_LO && lane % 8 == 0)
+                prefetch_l2(f.lo_in + (long long)yp * f.w + x0);
+        }
+    }
     float2 L = make_float2(__shfl_up_sync(0xffffffffu, S.a[SCOLS - 1].x, 1),
                            __shfl_up_sync(0xffffffffu, S.a[SCOLS - 1].y, 1));
     float2 R = make_float2(__shfl_down_sync(0xffffffffu, S.a[0].x, 1),
@@ -625,22 +643,34 @@ __device__ __forceinline__ void stream_row(const DiffFrame &f, int y, int x0, in
         R = edge ? S.ae : Z;
     float2 n[SCOLS];
     if (MODE == 0) {
-        float fS[SCOLS], fH[SCOLS + 1];   // fH[k]: into column k from column k - 1
-        fH[0] = link_flux(S.a[0], L, c);
-#pragma unroll
-        for (int k = 1; k < SCOLS; ++k)
-            fH[k] = link_flux(S.a[k], S.a[k - 1], c);
-        fH[SCOLS] = link_flux(S.a[SCOLS - 1], R, c);   // into the last column from R
-#pragma unroll
-        for (int k = 0; k < SCOLS; ++k)
-            fS[k] = link_flux(S.a[k], d[k], c);
-#pragma unroll
-        for (int k = 0; k < SCOLS; ++k) {
-            const float fW = fH[k];
-            const float fE = k + 1 < SCOLS ? -fH[k + 1] : fH[SCOLS];
-            n[k] = pm4_combine(S.a[k], S.fN[k], fS[k], fW, fE, lam);
-            S.fN[k] = -fS[k];
-        }
+        // the links of columns 0-1 and 2-3 in packed pairs: fH[k] is the flux
+        // into column k from column k - 1 (fH[0] from L, fH[4] into column 3
+        // from R), each exactly the link_flux of the scalar kernels
+        const float2 *a = S.a;
+        const f2 c2 = pk(c, c), lam2 = pk(lam, lam);
+        const f2 fS01 = link_flux2(pk(a[0].x, a[1].x), pk(a[0].y, a[1].y), pk(d[0].x, d[1].x),
+                                   pk(d[0].y, d[1].y), c2);
+        const f2 fS23 = link_flux2(pk(a[2].x, a[3].x), pk(a[2].y, a[3].y), pk(d[2].x, d[3].x),
+                                   pk(d[2].y, d[3].y), c2);
+        const f2 fH04 = link_flux2(pk(a[0].x, a[3].x), pk(a[0].y, a[3].y), pk(L.x, R.x),
+                                   pk(L.y, R.y), c2);
+        const f2 fH13 = link_flux2(pk(a[1].x, a[3].x), pk(a[1].y, a[3].y), pk(a[0].x, a[2].x),
+                                   pk(a[0].y, a[2].y), c2);
+        const float fH2 = link_flux(a[2], a[1], c);
+        const float fH0 = lo_of(fH04), fH4 = hi_of(fH04), fH1 = lo_of(fH13), fH3 = hi_of(fH13);
+        // column k: W flux fH[k], E flux -fH[k + 1] (column 3: fH[4])
+        const f2 fW01 = pk(fH0, fH1), fE01 = pk(-fH1, -fH2);
+        const f2 fW23 = pk(fH2, fH3), fE23 = pk(-fH3, fH4);
+        const f2 l01 = add2(pk(a[0].y, a[1].y),
+                            mulr2(lam2, add2(add2(add2(S.fN01, fS01), fW01), fE01)));
+        const f2 l23 = add2(pk(a[2].y, a[3].y),
+                            mulr2(lam2, add2(add2(add2(S.fN23, fS23), fW23), fE23)));
+        n[0] = make_float2(a[0].x, lo_of(l01));
+        n[1] = make_float2(a[1].x, hi_of(l01));
+        n[2] = make_float2(a[2].x, lo_of(l23));
+        n[3] = make_float2(a[3].x, hi_of(l23));
+        S.fN01 = neg2(fS01);
+        S.fN23 = neg2(fS23);
     } else {
 #pragma unroll
         for (int k = 0; k < SCOLS; ++k)
@@ -657,7 +687,9 @@ __device__ __forceinline__ void stream_row(const DiffFrame &f, int y, int x0, in
     for (int k = 0; k < SCOLS; ++k)
         o[k] = DST_LO ? n[k].y : depth_out(n[k]);
     float *drow = f.dst + (long long)y * f.w;
-    if (vdst && x0 + SCOLS <= f.w) {
+    if (!PM_INB(y, f.h))
+        return;
+    if (vdst && x0 + SCOLS <= f.w && PM_INB(x0, f.w)) {
         *reinterpret_cast<float4 *>(drow + x0) = make_float4(o[0], o[1], o[2], o[3]);
     } else {
 #pragma unroll
@@ -701,9 +733,13 @@ __global__ void __launch_bounds__(256, 3) k_diffuse_stream(DiffFrame f, float la
     decode_row<DT, HAS_LO>(rB, f.scale, S.a, S.ae);
     load_row<DT, HAS_LO>(f, y0 + 1, x0, xe, edge, vsrc, vlo, rA);
     load_row<DT, HAS_LO>(f, y0 + 2, x0, xe, edge, vsrc, vlo, rB);
-#pragma unroll
-    for (int k = 0; k < SCOLS; ++k)
-        S.fN[k] = MODE == 0 ? link_flux(S.a[k], S.u[k], c) : 0.0f;
+    if (MODE == 0) {
+        const f2 c2 = pk(c, c);
+        S.fN01 = link_flux2(pk(S.a[0].x, S.a[1].x), pk(S.a[0].y, S.a[1].y),
+                            pk(S.u[0].x, S.u[1].x), pk(S.u[0].y, S.u[1].y), c2);
+        S.fN23 = link_flux2(pk(S.a[2].x, S.a[3].x), pk(S.a[2].y, S.a[3].y),
+                            pk(S.u[2].x, S.u[3].x), pk(S.u[2].y, S.u[3].y), c2);
+    }
     for (int y = y0; y < y1; y += 2) {
         stream_row<MODE, DT, HAS_LO, DST_LO>(f, y, x0, xe, edge, vsrc, vlo, vdst, lane, lam, c,
                                              rA, y + 2 < y1, S);
@@ -814,5 +850,7 @@ cudaError_t launch_diffuse_stream(const DiffFrame &f, float lambda, float K, int
     }
     return cudaGetLastError();
 }
+
+PM_BOUNDS_QUERY(bounds_diffuse)
 
 }  // namespace pm

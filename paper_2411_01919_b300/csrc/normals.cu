@@ -11,6 +11,7 @@
 // from FP64) instead of dividing: a few FP32 ulps on the points, no division
 // in the per-pixel work.  The same constant factor on every pixel changes
 // normal directions by about 1e-7 rad.
+#define PM_FILE_ID 2
 #include "pm_internal.cuh"
 
 namespace pm {
@@ -31,6 +32,12 @@ __device__ __forceinline__ float3 backproject(float z, int u, int v, const Cam &
     return make_float3(__fmul_rn(z, xt), __fmul_rn(z, yt), z);
 }
 
+// depth[i] of a frame of n pixels (bounds-checked in the PM_DEBUG_BOUNDS build)
+__device__ __forceinline__ float ld_depth(const float *__restrict__ depth, long long i, long long n)
+{
+    return PM_INB(i, n) ? __ldg(depth + i) : 0.0f;
+}
+
 template <int STENCIL>
 __device__ __forceinline__ void normal_at(const float *__restrict__ depth, int w, int h, int u,
                                           int v, const Cam &k, float *P, float *N,
@@ -38,20 +45,22 @@ __device__ __forceinline__ void normal_at(const float *__restrict__ depth, int w
 {
     const long long npx = (long long)w * h;
     const long long p = (long long)v * w + u;
-    const float z = __ldg(depth + p);
+    const float z = ld_depth(depth, p, npx);
     const bool ok = depth_ok(z);
     float3 Pp = ok ? backproject(z, u, v, k) : make_float3(0.f, 0.f, 0.f);
-    P[p] = Pp.x;
-    P[npx + p] = Pp.y;
-    P[2 * npx + p] = Pp.z;
+    if (PM_INB(2 * npx + p, 3 * npx)) {
+        P[p] = Pp.x;
+        P[npx + p] = Pp.y;
+        P[2 * npx + p] = Pp.z;
+    }
     unsigned char vb = ok ? 1 : 0;
     float3 n = make_float3(0.f, 0.f, 0.f);
     if (ok && u > 0 && v > 0 && u < w - 1 && v < h - 1) {
         float3 tu = make_float3(0.f, 0.f, 0.f), tv = make_float3(0.f, 0.f, 0.f);
         bool all = true;
         if (STENCIL == 0) {
-            float ze = __ldg(depth + p + 1), zw = __ldg(depth + p - 1);
-            float zs = __ldg(depth + p + w), zn = __ldg(depth + p - w);
+            float ze = ld_depth(depth, p + 1, npx), zw = ld_depth(depth, p - 1, npx);
+            float zs = ld_depth(depth, p + w, npx), zn = ld_depth(depth, p - w, npx);
             all = depth_ok(ze) && depth_ok(zw) && depth_ok(zs) && depth_ok(zn);
             float3 a = backproject(ze, u + 1, v, k), b = backproject(zw, u - 1, v, k);
             float3 c = backproject(zs, u, v + 1, k), d = backproject(zn, u, v - 1, k);
@@ -61,10 +70,10 @@ __device__ __forceinline__ void normal_at(const float *__restrict__ depth, int w
 #pragma unroll
             for (int j = -1; j <= 1; ++j) {
                 const float wt = j == 0 ? 2.0f : 1.0f;
-                float zr1 = __ldg(depth + p + (long long)j * w + 1);
-                float zr0 = __ldg(depth + p + (long long)j * w - 1);
-                float zc1 = __ldg(depth + p + w + j);
-                float zc0 = __ldg(depth + p - w + j);
+                float zr1 = ld_depth(depth, p + (long long)j * w + 1, npx);
+                float zr0 = ld_depth(depth, p + (long long)j * w - 1, npx);
+                float zc1 = ld_depth(depth, p + w + j, npx);
+                float zc0 = ld_depth(depth, p - w + j, npx);
                 all = all && depth_ok(zr1) && depth_ok(zr0) && depth_ok(zc1) && depth_ok(zc0);
                 float3 a = backproject(zr1, u + 1, v + j, k), b = backproject(zr0, u - 1, v + j, k);
                 float3 c = backproject(zc1, u + j, v + 1, k), d = backproject(zc0, u + j, v - 1, k);
@@ -86,10 +95,12 @@ __device__ __forceinline__ void normal_at(const float *__restrict__ depth, int w
             }
         }
     }
-    N[p] = n.x;
-    N[npx + p] = n.y;
-    N[2 * npx + p] = n.z;
-    valid[p] = vb;
+    if (PM_INB(2 * npx + p, 3 * npx) && PM_INB(p, npx)) {
+        N[p] = n.x;
+        N[npx + p] = n.y;
+        N[2 * npx + p] = n.z;
+        valid[p] = vb;
+    }
 }
 
 template <int STENCIL>
@@ -138,5 +149,7 @@ cudaError_t launch_normals_batch(const void *d_desc, int n_frames, int max_w, in
         k_normals_batch<1><<<grid, dim3(32, 8), 0, s>>>(f);
     return cudaGetLastError();
 }
+
+PM_BOUNDS_QUERY(bounds_normals)
 
 }  // namespace pm

@@ -337,12 +337,12 @@ Plan build_tables(pm_ctx *ctx, const std::vector<FrameJob> &jobs, int T, bool ra
         big_tiles += (long long)((jobs[f].w + 79) / 80) * ((jobs[f].h + 47) / 48);
     }
     // tile shape: for PM4 batches that fill the GPU twice over, the
-    // register-blocked kernel's (128 - 2T) x (48 - 2T) tiles; otherwise the
+    // register-blocked kernel's (128 - 2T) x (64 - 2T) tiles; otherwise the
     // shared-memory kernel's smaller tiles (more CTAs for small batches)
     const bool big = big_tiles >= 2LL * ctx->sms;
-    const bool regs = false;
+    const bool regs = big && ctx->dp.mode == 0;
     pl.dx = ctx->dp.tile_w > 0 ? ctx->dp.tile_w : (regs ? 128 - 2 * T : big ? 80 : 48);
-    pl.dy = ctx->dp.tile_h > 0 ? ctx->dp.tile_h : (regs ? 48 - 2 * T : big ? 48 : 24);
+    pl.dy = ctx->dp.tile_h > 0 ? ctx->dp.tile_h : (regs ? 64 - 2 * T : big ? 48 : 24);
     size_t off = 0;
     for (int k = 0; k < Lmax; ++k) {
         DiffFrame *tab = reinterpret_cast<DiffFrame *>(ctx->h_tables + off);
@@ -1350,6 +1350,25 @@ pm_status pm_stage_times(pm_ctx *ctx, float ms[3])
     for (int i = 0; i < 3; ++i)
         ms[i] = ctx->stage_ms[i];
     return PM_OK;
+}
+
+pm_status pm_debug_bounds(unsigned long long *status)
+{
+    if (!status)
+        return fail(PM_ERR_ARG, "null argument");
+    *status = 0ull;
+#ifdef PM_DEBUG_BOUNDS
+    unsigned long long v[3] = {0ull, 0ull, 0ull};
+    PM_CK(bounds_diffuse(&v[0]));
+    PM_CK(bounds_normals(&v[1]));
+    PM_CK(bounds_ransac(&v[2]));
+    for (unsigned long long x : v)
+        if (x && !*status)
+            *status = x;
+    return PM_OK;
+#else
+    return fail(PM_ERR_STATE, "not a bounds-checking build (PM_DEBUG_BOUNDS)");
+#endif
 }
 
 const char *pm_last_error(void) { return g_err.c_str(); }

@@ -10,6 +10,52 @@
 namespace pm {
 
 // ---------------------------------------------------------------------------
+// bounds-checking build (PM_DEBUG_BOUNDS): every instrumented global access
+// checks its index against the extent of its buffer; the first index outside
+// is recorded in a device status word of the translation unit (bit 63 set,
+// bits 48-62 the source site: file id and line, bits 0-47 the index) and the
+// access is skipped.  Nothing traps.  The release build compiles every check
+// to `true`.  pm_debug_bounds (pm_api.cu) reads and clears the words.
+// ---------------------------------------------------------------------------
+#ifndef PM_FILE_ID
+#define PM_FILE_ID 0
+#endif
+#ifdef PM_DEBUG_BOUNDS
+static __device__ unsigned long long g_pm_bounds = 0ull;
+__device__ __forceinline__ bool pm_inb(long long i, long long n, int site)
+{
+    if (i >= 0 && i < n)
+        return true;
+    atomicCAS(&g_pm_bounds, 0ull,
+              0x8000000000000000ull | ((unsigned long long)(site & 0x7fff) << 48) |
+                  ((unsigned long long)i & 0xffffffffffffull));
+    return false;
+}
+#define PM_INB(i, n) ::pm::pm_inb((long long)(i), (long long)(n), (PM_FILE_ID << 12) | (__LINE__ & 0xfff))
+#define PM_BOUNDS_QUERY(fn)                                                                   \
+    cudaError_t fn(unsigned long long *v)                                                     \
+    {                                                                                         \
+        cudaError_t e = cudaMemcpyFromSymbol(v, g_pm_bounds, sizeof(*v));                     \
+        const unsigned long long z = 0ull;                                                    \
+        if (e == cudaSuccess && *v)                                                           \
+            e = cudaMemcpyToSymbol(g_pm_bounds, &z, sizeof(z));                               \
+        return e;                                                                             \
+    }
+#else
+#define PM_INB(i, n) true
+#define PM_BOUNDS_QUERY(fn)                                                                   \
+    cudaError_t fn(unsigned long long *v)                                                     \
+    {                                                                                         \
+        *v = 0ull;                                                                            \
+        return cudaSuccess;                                                                   \
+    }
+#endif
+// status words of the kernels' translation units
+cudaError_t bounds_diffuse(unsigned long long *v);
+cudaError_t bounds_normals(unsigned long long *v);
+cudaError_t bounds_ransac(unsigned long long *v);
+
+// ---------------------------------------------------------------------------
 // compile-time layout constants
 // ---------------------------------------------------------------------------
 constexpr int CHUNK = 1024;              // candidates per chunk (RANSAC work unit)

@@ -27,6 +27,7 @@
 // frame's chunking never depends on the other frames of the batch, and every
 // reduction runs in a fixed order, so a frame's result is bit-identical alone
 // and in a batch.
+#define PM_FILE_ID 3
 #include "pm_internal.cuh"
 
 namespace pm {
@@ -62,6 +63,9 @@ __device__ __forceinline__ int frame_of(const int *__restrict__ base, int n, int
     }
     return lo;
 }
+
+// Chunks of a frame's largest candidate list (all its pixels).
+__device__ __forceinline__ int nchunks_of(const RFrame &F) { return (F.npx + CHUNK - 1) / CHUNK; }
 
 // ---------------------------------------------------------------------------
 // round planning (run by one block of any size that is a multiple of 32)
@@ -222,7 +226,8 @@ __global__ void __launch_bounds__(MARK_THREADS) k_mark0(RFrame *frames, int n,
             if (pix < F.npx)
                 F.labels[pix] = -1;
             const unsigned word = __ballot_sync(0xffffffffu, (vb[u] & 1) != 0);
-            if ((threadIdx.x & 31) == 0) {
+            if ((threadIdx.x & 31) == 0 &&
+                PM_INB((long long)c * CHUNK_WORDS + (j >> 5), (long long)nchunks_of(F) * CHUNK_WORDS)) {
                 F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)] = word;
                 kept += __popc(word);
             }
@@ -230,7 +235,7 @@ __global__ void __launch_bounds__(MARK_THREADS) k_mark0(RFrame *frames, int n,
         if ((threadIdx.x & 31) == 0)
             wsum[threadIdx.x >> 5] = kept;
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && PM_INB(c, nchunks_of(F))) {
             int s = 0;
             for (int w = 0; w < MARK_THREADS / 32; ++w)
                 s += wsum[w];
@@ -249,7 +254,8 @@ __device__ void compact_chunk(const RFrame &F, int c, int nchunks, int src, int 
                               bool src_image, int off)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned mine = F.keepbits[(long long)c * CHUNK_WORDS + lane];
+    const unsigned mine = PM_INB((long long)c * CHUNK_WORDS + lane, (long long)nchunks_of(F) * CHUNK_WORDS)
+                              ? F.keepbits[(long long)c * CHUNK_WORDS + lane] : 0u;
     const int x = __popc(mine);
     int incl = x;
 #pragma unroll
@@ -268,6 +274,8 @@ __device__ void compact_chunk(const RFrame &F, int c, int nchunks, int src, int 
         if (word >> lane & 1u) {
             const int pos = off + wpre + __popc(word & lt);
             const long long j = base + 32 * w + lane;
+            if (!(PM_INB(j, npx) && PM_INB(pos, npx)))
+                continue;
             float4 pt;
             if (src_image)
                 pt = make_float4(F.P[j], F.P[npx + j], F.P[2 * npx + j], __int_as_float((int)j));
@@ -349,7 +357,8 @@ __global__ void __launch_bounds__(128) k_hyp(RFrame *frames, RParams prm, int ro
         st->score_done = 0;
     // the removal adds each chunk's kept candidates warp by warp
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < st->nchunks; c += gridDim.x * blockDim.x)
-        F.kept[c] = 0;
+        if (PM_INB(c, nchunks_of(F)))
+            F.kept[c] = 0;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= prm.H)
         return;
@@ -357,9 +366,13 @@ __global__ void __launch_bounds__(128) k_hyp(RFrame *frames, RParams prm, int ro
     unsigned long long c[4] = {(unsigned long long)h, (unsigned long long)round, F.frame_idx, 0ull};
     philox4x64_10(c, prm.seed, 0ull);
     const float4 *pts = F.cpt[round & 1];
-    float4 q0 = pts[__umul64hi(c[0], M)];
-    float4 q1 = pts[__umul64hi(c[1], M)];
-    float4 q2 = pts[__umul64hi(c[2], M)];
+    const unsigned long long i0 = __umul64hi(c[0], M), i1 = __umul64hi(c[1], M),
+                             i2 = __umul64hi(c[2], M);
+    if (!(PM_INB(i0, F.npx) && PM_INB(i1, F.npx) && PM_INB(i2, F.npx)))
+        return;
+    float4 q0 = pts[i0];
+    float4 q1 = pts[i1];
+    float4 q2 = pts[i2];
     float4 pl;
     bool ok = hyp_plane(make_float3(q0.x, q0.y, q0.z), make_float3(q1.x, q1.y, q1.z),
                         make_float3(q2.x, q2.y, q2.z), pl);
@@ -561,14 +574,14 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
         const int nseg = (cnt + SEG - 1) / SEG;
         __syncthreads();
         for (int j = threadIdx.x; j < cnt; j += SCORE_THREADS)
-            pts[j] = src[j];
+            pts[j] = PM_INB(base + j, F.npx) ? src[j] : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int hb = hb_first; hb < hb_end; ++hb) {
             const int h0 = hb * HB;
             const int nh = min(HB, prm.H - h0);
             for (int k = threadIdx.x; k < HB; k += SCORE_THREADS) {
                 float4 pl = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
                 float sd = 0.0f;                     // n = 0, d = inf: culled everywhere
-                if (k < nh) {
+                if (k < nh && PM_INB(h0 + k, prm.H)) {
                     const float4 q = F.hyp[h0 + k];
                     if (fabsf(q.w) <= 3.0e38f) {     // degenerate planes carry d = +inf
                         pl = q;
@@ -967,7 +980,8 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
 #pragma unroll
             for (int u = 0; u < PER_THREAD; ++u) {
                 const int j = threadIdx.x + u * REMOVE_THREADS;
-                p[u] = j < cnt ? F.cpt[cur][base + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                p[u] = j < cnt && PM_INB(base + j, npx) ? F.cpt[cur][base + j]
+                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
             }
             unsigned any = 0u;
             int kept_w = 0;
@@ -978,7 +992,8 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
                 const unsigned word = __ballot_sync(0xffffffffu, j < cnt && !inl[u]);
                 any |= __ballot_sync(0xffffffffu, inl[u]);
                 kept_w += __popc(word);
-                if (lane == 0)
+                if (lane == 0 && PM_INB((long long)c * CHUNK_WORDS + (j >> 5),
+                                        (long long)nchunks_of(F) * CHUNK_WORDS))
                     F.keepbits[(long long)c * CHUNK_WORDS + (j >> 5)] = word;
             }
             if (lane == 0 && kept_w)
@@ -992,6 +1007,8 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
 #pragma unroll
                 for (int u = 0; u < PER_THREAD; ++u) {
                     pix[u] = __float_as_int(p[u].w);
+                    if (inl[u] && !PM_INB(pix[u], npx))
+                        inl[u] = false;
                     const bool g = inl[u] && F.N;
                     vb[u] = g ? F.valid[pix[u]] : 0;
                     nrm[u] = g ? make_float3(F.N[pix[u]], F.N[npx + pix[u]], F.N[2 * npx + pix[u]])
@@ -1040,6 +1057,10 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
         __syncthreads();
         // across warps: one thread per moment value, warps merged in order
         float *rec = F.partial + (long long)(c0 / GROUP) * PART_WORDS;
+        if (!PM_INB(c0 / GROUP, nchunks_of(F))) {
+            __syncthreads();
+            continue;
+        }
         if ((int)threadIdx.x < 2 * NMOM) {
             const int v = threadIdx.x;
             float ss = sh_s[0][v], cc = sh_c[0][v];
@@ -1187,5 +1208,7 @@ cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream
         return e;
     return cudaGetLastError();
 }
+
+PM_BOUNDS_QUERY(bounds_ransac)
 
 }  // namespace pm

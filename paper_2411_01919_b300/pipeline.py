@@ -119,9 +119,9 @@ class Pipeline:
     max_w x max_h pixels on the current CUDA device."""
 
     def __init__(self, params: Params = None, max_w: int = 640, max_h: int = 480,
-                 max_frames: int = 1):
+                 max_frames: int = 1, lib_path: str = None):
         self.p = params or Params()
-        self.lib = _ffi.load()
+        self.lib = _ffi.load(lib_path) if lib_path else _ffi.load()
         p = self.p
         self._dp = _ffi.DiffusionParams(p.iters, p.lam, p.K, p.mode, p.iters_per_launch,
                                         p.tile_w, p.tile_h)

@@ -27,6 +27,9 @@ CANDIDATES: List[Tuple[int, int, int]] = [
     (T, tw, th) for T in (4, 6, 8) for (tw, th) in ((48, 24), (64, 32), (80, 48), (64, 48))
 ] + [
     (T, 32 * k - 2 * (T - 1), th) for T in (4, 6) for k in (2, 3, 4) for th in (24, 32)
+] + [
+    # the register-blocked kernel (PM4): 128 - 2T columns x 8R - 2T rows
+    (T, 128 - 2 * T, 8 * R - 2 * T) for T in (4, 6, 8) for R in (4, 6, 8)
 ]
 
 

@@ -130,7 +130,10 @@ def test_temporal_blocking_is_bit_exact(mode):
     outs = []
     for T, tw, th in ((1, 0, 0), (2, 0, 0), (3, 0, 0), (5, 0, 0), (8, 0, 0), (8, 80, 48),
                       (8, 48, 24), (7, 17, 9), (4, 64, 1), (8, 1, 48), (6, 33, 40),
-                      (4, 122, 32), (8, 128, 48)):
+                      (4, 122, 32), (8, 128, 48),
+                      # (PM4) the register-blocked kernel's (128 - 2T) x (8R - 2T) tiles
+                      (8, 112, 48), (8, 112, 32), (8, 112, 16), (6, 116, 36), (4, 120, 56),
+                      (3, 122, 26), (1, 126, 62), (2, 124, 44), (5, 118, 22), (7, 114, 50)):
         p = params('c2', mode=mode, iters_per_launch=T, tile_w=tw, tile_h=th)
         with Pipeline(p, fr.w, fr.h) as pipe:
             outs.append(pipe.diffuse(to_dev(fr.encoded)).cpu().numpy())
@@ -151,7 +154,7 @@ def test_one_iteration_kernel_is_bit_exact_on_every_encoding(dtype, shape, pad, 
     wide[:, :w] = enc
     d = to_dev(wide)[:, :w]
     outs = []
-    for T, tw, th in ((1, 0, 0), (0, 0, 0), (5, 0, 0), (5, 48, 24)):
+    for T, tw, th in ((1, 0, 0), (0, 0, 0), (5, 0, 0), (5, 48, 24), (5, 118, 38), (4, 120, 24)):
         with Pipeline(Params(iters=11, mode=mode, iters_per_launch=T, tile_w=tw, tile_h=th),
                       w, h) as pipe:
             outs.append(pipe.diffuse(d).cpu().numpy())
