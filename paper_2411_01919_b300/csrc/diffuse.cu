@@ -511,19 +511,27 @@ __global__ void __launch_bounds__(256, 3) k_diffuse_regs(const DiffFrame *__rest
 // one iteration per launch, one pass over HBM
 // ---------------------------------------------------------------------------
 
-// Block = 32 x 8 threads; lane l of warp w covers the four columns
-// x0 = 128 blockIdx.x + 4 l .. x0 + 3 and walks STREAM_ROWS rows down.  The
-// north link flux of a row is the negated south link flux of the row before
-// and the three links inside a lane's columns are evaluated once (exactly
-// antisymmetric, see link_flux); the horizontal neighbours come from the
-// adjacent lanes by shuffle, and lanes 0 and 31 read the column just outside
-// the warp.  Every link enters the sum of pm4_combine with the same value and
-// in the same order as in the tiled kernel, so the results are bit-identical.
-// Two rows below the current one are in flight while it is computed, and the
-// row STREAM_PF further down is prefetched into L2.
-constexpr int SCOLS = 4;
-constexpr int STREAM_ROWS = 16;
-constexpr int STREAM_PF = 4;
+// Block = 32 x 8 threads; lane l of warp w covers SC consecutive columns,
+// x0 = 32 SC blockIdx.x + SC l .. x0 + SC - 1 (SC = 8 for the 2-byte
+// encodings, 4 for FP32: 16-byte loads of the encoding either way), and walks
+// STREAM_ROWS rows down.  The north link flux of a row is the negated south
+// link flux of the row before and the links inside a lane's columns are
+// evaluated once (exactly antisymmetric, see link_flux); the horizontal
+// neighbours come from the adjacent lanes by shuffle, and lanes 0 and 31 read
+// the column just outside the warp.  Every link enters the sum of pm4_combine
+// with the same value and in the same order as in the tiled kernels, so the
+// results are bit-identical.  Two rows below the current one are in flight
+// while it is computed, and the row STREAM_PF further down is prefetched into
+// L2.
+constexpr int STREAM_ROWS = 32;
+constexpr int STREAM_PF = 2;
+
+template <int DT>
+__host__ __device__ constexpr int stream_cols() { return DT == PM_F32_M ? 4 : 8; }
+// resident CTAs per SM the register budget is fitted to (8 columns per lane
+// need about 128 registers, 4 fit in 80)
+template <int DT>
+__host__ __device__ constexpr int stream_min_ctas() { return DT == PM_F32_M ? 3 : 2; }
 
 __device__ __forceinline__ void prefetch_l2(const void *p)
 {
@@ -532,19 +540,20 @@ __device__ __forceinline__ void prefetch_l2(const void *p)
 
 // One row of a lane's columns as read from memory: encoding containers, lo
 // parts, and the column outside the warp (lanes 0 and 31).
+template <int SC>
 struct RowRaw {
-    unsigned r[SCOLS];
-    float l[SCOLS];
+    unsigned r[SC];
+    float l[SC];
     unsigned re;
     float le;
 };
 
-template <int DT, bool HAS_LO>
+template <int DT, bool HAS_LO, int SC>
 __device__ __forceinline__ void load_row(const DiffFrame &f, int y, int x0, int xe, bool edge,
-                                         bool vsrc, bool vlo, RowRaw &o)
+                                         bool vsrc, bool vlo, RowRaw<SC> &o)
 {
 #pragma unroll
-    for (int k = 0; k < SCOLS; ++k) {
+    for (int k = 0; k < SC; ++k) {
         o.r[k] = 0u;
         o.l[k] = 0.0f;
     }
@@ -553,30 +562,34 @@ __device__ __forceinline__ void load_row(const DiffFrame &f, int y, int x0, int 
     if (y < 0 || y >= f.h)
         return;
     const char *row = (const char *)f.src + (long long)y * f.src_pitch;
-    const bool full = x0 + SCOLS <= f.w;
-    if (full && vsrc && PM_INB(x0 + SCOLS - 1, f.w) && PM_INB(x0, f.w)) {
-        if (DT == PM_F32_M) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(row) + (x0 >> 2));
-            o.r[0] = v.x; o.r[1] = v.y; o.r[2] = v.z; o.r[3] = v.w;
-        } else {
-            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(row) + (x0 >> 2));
-            o.r[0] = v.x & 0xffffu; o.r[1] = v.x >> 16;
-            o.r[2] = v.y & 0xffffu; o.r[3] = v.y >> 16;
-        }
+    const bool full = x0 + SC <= f.w;
+    if (full && vsrc && PM_INB(x0 + SC - 1, f.w) && PM_INB(x0, f.w)) {
+        // 16 bytes: 8 two-byte codes or 4 FP32 values
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(row) + x0 / SC);
+        const unsigned u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < SC; ++k)
+            o.r[k] = SC == 8 ? ((k & 1) ? u[k >> 1] >> 16 : u[k >> 1] & 0xffffu) : u[k];
     } else {
 #pragma unroll
-        for (int k = 0; k < SCOLS; ++k)
+        for (int k = 0; k < SC; ++k)
             if (x0 + k < f.w)
                 o.r[k] = load_raw(f, x0 + k, y);
     }
     if (HAS_LO) {
         const float *lrow = f.lo_in + (long long)y * f.w;
-        if (full && vlo && PM_INB(x0 + SCOLS - 1, f.w) && PM_INB(x0, f.w)) {
-            const float4 v = __ldg(reinterpret_cast<const float4 *>(lrow + x0));
-            o.l[0] = v.x; o.l[1] = v.y; o.l[2] = v.z; o.l[3] = v.w;
+        if (full && vlo && PM_INB(x0 + SC - 1, f.w) && PM_INB(x0, f.w)) {
+#pragma unroll
+            for (int q = 0; q < SC / 4; ++q) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(lrow + x0) + q);
+                o.l[4 * q] = v.x;
+                o.l[4 * q + 1] = v.y;
+                o.l[4 * q + 2] = v.z;
+                o.l[4 * q + 3] = v.w;
+            }
         } else {
 #pragma unroll
-            for (int k = 0; k < SCOLS; ++k)
+            for (int k = 0; k < SC; ++k)
                 if (x0 + k < f.w && PM_INB(x0 + k, f.w))
                     o.l[k] = __ldg(lrow + x0 + k);
         }
@@ -587,12 +600,12 @@ __device__ __forceinline__ void load_row(const DiffFrame &f, int y, int x0, int 
         o.re = load_raw(f, xe, y);
 }
 
-template <int DT, bool HAS_LO>
-__device__ __forceinline__ void decode_row(const RowRaw &o, float scale, float2 (&a)[SCOLS],
+template <int DT, bool HAS_LO, int SC>
+__device__ __forceinline__ void decode_row(const RowRaw<SC> &o, float scale, float2 (&a)[SC],
                                            float2 &e)
 {
 #pragma unroll
-    for (int k = 0; k < SCOLS; ++k) {
+    for (int k = 0; k < SC; ++k) {
         a[k] = decode<DT>(o.r[k], scale);
         if (HAS_LO)
             a[k].y = o.l[k];
@@ -604,101 +617,112 @@ __device__ __forceinline__ void decode_row(const RowRaw &o, float scale, float2 
 
 // State of a lane walking down its columns: the row being computed (a, with
 // the column outside the warp ae), the row above (u, for the Alg. 1 form) and
-// the north fluxes of the row (PM4).
+// the north fluxes of the row in packed column pairs (PM4).
+template <int SC>
 struct StreamState {
-    float2 u[SCOLS], a[SCOLS], ae;
-    f2 fN01, fN23;      // north fluxes of columns 0-1 and 2-3 (PM4)
+    float2 u[SC], a[SC], ae;
+    f2 fN[SC / 2];
 };
 
 // Row y of the lane's columns, its row below already read into `below`, which
 // is refilled with row y + 3 (the row read two steps ahead) when `more`.
-template <int MODE, int DT, bool HAS_LO, bool DST_LO>
+template <int MODE, int DT, bool HAS_LO, bool DST_LO, int SC>
 __device__ __forceinline__ void stream_row(const DiffFrame &f, int y, int x0, int xe, bool edge,
                                            bool vsrc, bool vlo, bool vdst, int lane, float lam,
-                                           float c, RowRaw &below, bool more, StreamState &S)
+                                           float c, RowRaw<SC> &below, bool more,
+                                           StreamState<SC> &S)
 {
     const float2 Z = make_float2(HOLE, 0.0f);
-    float2 d[SCOLS], de;
-    decode_row<DT, HAS_LO>(below, f.scale, d, de);
+    float2 d[SC], de;
+    decode_row<DT, HAS_LO, SC>(below, f.scale, d, de);
     if (more) {
-        load_row<DT, HAS_LO>(f, y + 3, x0, xe, edge, vsrc, vlo, below);
+        load_row<DT, HAS_LO, SC>(f, y + 3, x0, xe, edge, vsrc, vlo, below);
         // the row STREAM_PF below that into L2, one request per 128-byte line
         const int yp = y + 3 + STREAM_PF;
         if (yp < f.h && x0 < f.w) {
-            constexpr int SRC_LANES = 128 / (SCOLS * (DT == PM_F32_M ? 4 : 2));
+            constexpr int SRC_LANES = 128 / (SC * (DT == PM_F32_M ? 4 : 2));
             if (lane % SRC_LANES == 0)
                 prefetch_l2((const char *)f.src + (long long)yp * f.src_pitch +
                             (long long)x0 * (DT == PM_F32_M ? 4 : 2));
-            if (HAS_LO && lane % 8 == 0)
+            if (HAS_LO && lane % (32 / SC) == 0)
                 prefetch_l2(f.lo_in + (long long)yp * f.w + x0);
         }
     }
-    float2 L = make_float2(__shfl_up_sync(0xffffffffu, S.a[SCOLS - 1].x, 1),
-                           __shfl_up_sync(0xffffffffu, S.a[SCOLS - 1].y, 1));
+    float2 L = make_float2(__shfl_up_sync(0xffffffffu, S.a[SC - 1].x, 1),
+                           __shfl_up_sync(0xffffffffu, S.a[SC - 1].y, 1));
     float2 R = make_float2(__shfl_down_sync(0xffffffffu, S.a[0].x, 1),
                            __shfl_down_sync(0xffffffffu, S.a[0].y, 1));
     if (lane == 0)
         L = edge ? S.ae : Z;
     if (lane == 31)
         R = edge ? S.ae : Z;
-    float2 n[SCOLS];
+    float2 n[SC];
     if (MODE == 0) {
-        // the links of columns 0-1 and 2-3 in packed pairs: fH[k] is the flux
-        // into column k from column k - 1 (fH[0] from L, fH[4] into column 3
-        // from R), each exactly the link_flux of the scalar kernels
+        // fH[k]: the flux into column k from column k - 1 (fH[0] from L;
+        // fH[SC] into the last column from R), each exactly the link_flux of
+        // the scalar kernels, evaluated in packed pairs
         const float2 *a = S.a;
         const f2 c2 = pk(c, c), lam2 = pk(lam, lam);
-        const f2 fS01 = link_flux2(pk(a[0].x, a[1].x), pk(a[0].y, a[1].y), pk(d[0].x, d[1].x),
-                                   pk(d[0].y, d[1].y), c2);
-        const f2 fS23 = link_flux2(pk(a[2].x, a[3].x), pk(a[2].y, a[3].y), pk(d[2].x, d[3].x),
-                                   pk(d[2].y, d[3].y), c2);
-        const f2 fH04 = link_flux2(pk(a[0].x, a[3].x), pk(a[0].y, a[3].y), pk(L.x, R.x),
-                                   pk(L.y, R.y), c2);
-        const f2 fH13 = link_flux2(pk(a[1].x, a[3].x), pk(a[1].y, a[3].y), pk(a[0].x, a[2].x),
-                                   pk(a[0].y, a[2].y), c2);
-        const float fH2 = link_flux(a[2], a[1], c);
-        const float fH0 = lo_of(fH04), fH4 = hi_of(fH04), fH1 = lo_of(fH13), fH3 = hi_of(fH13);
-        // column k: W flux fH[k], E flux -fH[k + 1] (column 3: fH[4])
-        const f2 fW01 = pk(fH0, fH1), fE01 = pk(-fH1, -fH2);
-        const f2 fW23 = pk(fH2, fH3), fE23 = pk(-fH3, fH4);
-        const f2 l01 = add2(pk(a[0].y, a[1].y),
-                            mulr2(lam2, add2(add2(add2(S.fN01, fS01), fW01), fE01)));
-        const f2 l23 = add2(pk(a[2].y, a[3].y),
-                            mulr2(lam2, add2(add2(add2(S.fN23, fS23), fW23), fE23)));
-        n[0] = make_float2(a[0].x, lo_of(l01));
-        n[1] = make_float2(a[1].x, hi_of(l01));
-        n[2] = make_float2(a[2].x, lo_of(l23));
-        n[3] = make_float2(a[3].x, hi_of(l23));
-        S.fN01 = neg2(fS01);
-        S.fN23 = neg2(fS23);
+        float fH[SC + 1];
+        {
+            const f2 e = link_flux2(pk(a[0].x, a[SC - 1].x), pk(a[0].y, a[SC - 1].y),
+                                    pk(L.x, R.x), pk(L.y, R.y), c2);
+            fH[0] = lo_of(e);
+            fH[SC] = hi_of(e);
+        }
+#pragma unroll
+        for (int k = 1; k + 1 < SC; k += 2) {
+            const f2 e = link_flux2(pk(a[k].x, a[k + 1].x), pk(a[k].y, a[k + 1].y),
+                                    pk(a[k - 1].x, a[k].x), pk(a[k - 1].y, a[k].y), c2);
+            fH[k] = lo_of(e);
+            fH[k + 1] = hi_of(e);
+        }
+        fH[SC - 1] = link_flux(a[SC - 1], a[SC - 2], c);
+#pragma unroll
+        for (int q = 0; q < SC / 2; ++q) {
+            const int k = 2 * q;
+            const f2 fS = link_flux2(pk(a[k].x, a[k + 1].x), pk(a[k].y, a[k + 1].y),
+                                     pk(d[k].x, d[k + 1].x), pk(d[k].y, d[k + 1].y), c2);
+            // column k: W flux fH[k], E flux -fH[k + 1] (the last column: fH[SC])
+            const f2 fW = pk(fH[k], fH[k + 1]);
+            const f2 fE = pk(-fH[k + 1], k + 2 < SC ? -fH[k + 2] : fH[SC]);
+            const f2 l = add2(pk(a[k].y, a[k + 1].y),
+                              mulr2(lam2, add2(add2(add2(S.fN[q], fS), fW), fE)));
+            n[k] = make_float2(a[k].x, lo_of(l));
+            n[k + 1] = make_float2(a[k + 1].x, hi_of(l));
+            S.fN[q] = neg2(fS);
+        }
     } else {
 #pragma unroll
-        for (int k = 0; k < SCOLS; ++k)
+        for (int k = 0; k < SC; ++k)
             n[k] = update_alg1(S.a[k], S.u[k], d[k], k ? S.a[k - 1] : L,
-                               k + 1 < SCOLS ? S.a[k + 1] : R, lam, c);
+                               k + 1 < SC ? S.a[k + 1] : R, lam, c);
     }
     if (f.n_iters == 0) {
 #pragma unroll
-        for (int k = 0; k < SCOLS; ++k)
+        for (int k = 0; k < SC; ++k)
             n[k] = S.a[k];
     }
-    float o[SCOLS];
+    float o[SC];
 #pragma unroll
-    for (int k = 0; k < SCOLS; ++k)
+    for (int k = 0; k < SC; ++k)
         o[k] = DST_LO ? n[k].y : depth_out(n[k]);
     float *drow = f.dst + (long long)y * f.w;
-    if (!PM_INB(y, f.h))
-        return;
-    if (vdst && x0 + SCOLS <= f.w && PM_INB(x0, f.w)) {
-        *reinterpret_cast<float4 *>(drow + x0) = make_float4(o[0], o[1], o[2], o[3]);
-    } else {
+    if (PM_INB(y, f.h)) {
+        if (vdst && x0 + SC <= f.w && PM_INB(x0, f.w)) {
 #pragma unroll
-        for (int k = 0; k < SCOLS; ++k)
-            if (x0 + k < f.w)
-                drow[x0 + k] = o[k];
+            for (int q = 0; q < SC / 4; ++q)
+                reinterpret_cast<float4 *>(drow + x0)[q] =
+                    make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < SC; ++k)
+                if (x0 + k < f.w)
+                    drow[x0 + k] = o[k];
+        }
     }
 #pragma unroll
-    for (int k = 0; k < SCOLS; ++k) {
+    for (int k = 0; k < SC; ++k) {
         S.u[k] = S.a[k];
         S.a[k] = d[k];
     }
@@ -706,47 +730,51 @@ __device__ __forceinline__ void stream_row(const DiffFrame &f, int y, int x0, in
 }
 
 template <int MODE, int DT, bool HAS_LO, bool DST_LO>
-__global__ void __launch_bounds__(256, 3) k_diffuse_stream(DiffFrame f, float lam, float c)
+__global__ void __launch_bounds__(256, stream_min_ctas<DT>()) k_diffuse_stream(DiffFrame f,
+                                                                              float lam, float c)
 {
+    constexpr int SC = stream_cols<DT>();
     const int lane = threadIdx.x;
-    const int x0 = blockIdx.x * (32 * SCOLS) + SCOLS * lane;
+    const int x0 = blockIdx.x * (32 * SC) + SC * lane;
     const int y0 = (blockIdx.y * 8 + threadIdx.y) * STREAM_ROWS;
     if (y0 >= f.h)
         return;
     const int y1 = min(y0 + STREAM_ROWS, f.h);
-    constexpr int VB = SCOLS * (DT == PM_F32_M ? 4 : 2);   // bytes of a lane's encoding
+    constexpr int VB = SC * (DT == PM_F32_M ? 4 : 2);   // bytes of a lane's encoding: 16
     const bool vsrc = ((uintptr_t)f.src % VB) == 0 && f.src_pitch % VB == 0;
     const bool vlo = ((uintptr_t)f.lo_in % 16) == 0 && f.w % 4 == 0;
     const bool vdst = ((uintptr_t)f.dst % 16) == 0 && f.w % 4 == 0;
-    // the column just outside the warp: x0 - 1 for lane 0, x0 + 4 for lane 31
-    const int xe = lane == 0 ? x0 - 1 : x0 + SCOLS;
+    // the column just outside the warp: x0 - 1 for lane 0, x0 + SC for lane 31
+    const int xe = lane == 0 ? x0 - 1 : x0 + SC;
     const bool edge = (lane == 0 || lane == 31) && xe >= 0 && xe < f.w;
 
     // two read buffers alternate: while row y is computed, rows y + 1 and
     // y + 2 are in flight
-    RowRaw rA, rB;
-    StreamState S;
-    load_row<DT, HAS_LO>(f, y0 - 1, x0, xe, edge, vsrc, vlo, rA);
-    load_row<DT, HAS_LO>(f, y0, x0, xe, edge, vsrc, vlo, rB);
+    RowRaw<SC> rA, rB;
+    StreamState<SC> S;
+    load_row<DT, HAS_LO, SC>(f, y0 - 1, x0, xe, edge, vsrc, vlo, rA);
+    load_row<DT, HAS_LO, SC>(f, y0, x0, xe, edge, vsrc, vlo, rB);
     float2 ue;
-    decode_row<DT, HAS_LO>(rA, f.scale, S.u, ue);
-    decode_row<DT, HAS_LO>(rB, f.scale, S.a, S.ae);
-    load_row<DT, HAS_LO>(f, y0 + 1, x0, xe, edge, vsrc, vlo, rA);
-    load_row<DT, HAS_LO>(f, y0 + 2, x0, xe, edge, vsrc, vlo, rB);
+    decode_row<DT, HAS_LO, SC>(rA, f.scale, S.u, ue);
+    decode_row<DT, HAS_LO, SC>(rB, f.scale, S.a, S.ae);
+    load_row<DT, HAS_LO, SC>(f, y0 + 1, x0, xe, edge, vsrc, vlo, rA);
+    load_row<DT, HAS_LO, SC>(f, y0 + 2, x0, xe, edge, vsrc, vlo, rB);
     if (MODE == 0) {
         const f2 c2 = pk(c, c);
-        S.fN01 = link_flux2(pk(S.a[0].x, S.a[1].x), pk(S.a[0].y, S.a[1].y),
-                            pk(S.u[0].x, S.u[1].x), pk(S.u[0].y, S.u[1].y), c2);
-        S.fN23 = link_flux2(pk(S.a[2].x, S.a[3].x), pk(S.a[2].y, S.a[3].y),
-                            pk(S.u[2].x, S.u[3].x), pk(S.u[2].y, S.u[3].y), c2);
+#pragma unroll
+        for (int q = 0; q < SC / 2; ++q)
+            S.fN[q] = link_flux2(pk(S.a[2 * q].x, S.a[2 * q + 1].x),
+                                 pk(S.a[2 * q].y, S.a[2 * q + 1].y),
+                                 pk(S.u[2 * q].x, S.u[2 * q + 1].x),
+                                 pk(S.u[2 * q].y, S.u[2 * q + 1].y), c2);
     }
     for (int y = y0; y < y1; y += 2) {
-        stream_row<MODE, DT, HAS_LO, DST_LO>(f, y, x0, xe, edge, vsrc, vlo, vdst, lane, lam, c,
-                                             rA, y + 2 < y1, S);
+        stream_row<MODE, DT, HAS_LO, DST_LO, SC>(f, y, x0, xe, edge, vsrc, vlo, vdst, lane, lam,
+                                                 c, rA, y + 2 < y1, S);
         if (y + 1 >= y1)
             break;
-        stream_row<MODE, DT, HAS_LO, DST_LO>(f, y + 1, x0, xe, edge, vsrc, vlo, vdst, lane, lam,
-                                             c, rB, y + 3 < y1, S);
+        stream_row<MODE, DT, HAS_LO, DST_LO, SC>(f, y + 1, x0, xe, edge, vsrc, vlo, vdst, lane,
+                                                 lam, c, rB, y + 3 < y1, S);
     }
 }
 
@@ -826,8 +854,8 @@ static void launch_stream_io(const DiffFrame &f, dim3 grid, dim3 block, float la
 cudaError_t launch_diffuse_stream(const DiffFrame &f, float lambda, float K, int mode,
                                   cudaStream_t s)
 {
-    dim3 grid((f.w + 32 * SCOLS - 1) / (32 * SCOLS),
-              (f.h + 8 * STREAM_ROWS - 1) / (8 * STREAM_ROWS));
+    const int sc = f.src_dtype == PM_F32_M ? stream_cols<PM_F32_M>() : stream_cols<PM_U16_MM>();
+    dim3 grid((f.w + 32 * sc - 1) / (32 * sc), (f.h + 8 * STREAM_ROWS - 1) / (8 * STREAM_ROWS));
     const dim3 block(32, 8);
     const float c = conductance_scale(K);
     if (f.src_dtype != PM_U16_MM && f.src_dtype != PM_F16_M && f.src_dtype != PM_F32_M)
