@@ -511,19 +511,22 @@ __global__ void __launch_bounds__(256, 3) k_diffuse_regs(const DiffFrame *__rest
 // one iteration per launch, one pass over HBM
 // ---------------------------------------------------------------------------
 
-// Block = 32 x 8 threads; lane l of warp w covers SC consecutive columns,
-// x0 = 32 SC blockIdx.x + SC l .. x0 + SC - 1 (SC = 8 for the 2-byte
-// encodings, 4 for FP32: 16-byte loads of the encoding either way), and walks
-// STREAM_ROWS rows down.  The north link flux of a row is the negated south
-// link flux of the row before and the links inside a lane's columns are
-// evaluated once (exactly antisymmetric, see link_flux); the horizontal
-// neighbours come from the adjacent lanes by shuffle, and lanes 0 and 31 read
-// the column just outside the warp.  Every link enters the sum of pm4_combine
-// with the same value and in the same order as in the tiled kernels, so the
-// results are bit-identical.  Two rows below the current one are in flight
-// while it is computed, and the row STREAM_PF further down is prefetched into
-// L2.
-constexpr int STREAM_ROWS = 32;
+// Block = 32 x 8 threads, 8 independent warps.  The image is cut into strips
+// of 32 SC columns (SC = 8 for the 2-byte encodings, 4 for FP32: 16-byte
+// loads of the encoding either way) and bands of `rows` rows; block b takes
+// strip b % strips and the 8 bands 8 (b / strips) .. + 7, one per warp (the
+// blocks of a wave cover a contiguous slab of rows across the whole width).
+// Lane l covers columns x0 = 32 SC strip + SC l .. x0 + SC - 1 and walks its
+// band down.  The host picks the band height so that the blocks fill the
+// resident CTAs in whole waves as nearly as it can.  The north link flux of
+// a row is the negated south link flux of the row before and the links
+// inside a lane's columns are evaluated once (exactly antisymmetric, see
+// link_flux); the horizontal neighbours come from the adjacent lanes by
+// shuffle, and lanes 0 and 31 read the column just outside the warp.  Every
+// link enters the sum of pm4_combine with the same value and in the same
+// order as in the tiled kernels, so the results are bit-identical.  Two rows
+// below the current one are in flight while it is computed, and the row
+// STREAM_PF further down is prefetched into L2.
 constexpr int STREAM_PF = 2;
 
 template <int DT>
@@ -624,30 +627,16 @@ struct StreamState {
     f2 fN[SC / 2];
 };
 
-// Row y of the lane's columns, its row below already read into `below`, which
-// is refilled with row y + 3 (the row read two steps ahead) when `more`.
-template <int MODE, int DT, bool HAS_LO, bool DST_LO, int SC>
-__device__ __forceinline__ void stream_row(const DiffFrame &f, int y, int x0, int xe, bool edge,
-                                           bool vsrc, bool vlo, bool vdst, int lane, float lam,
-                                           float c, RowRaw<SC> &below, bool more,
-                                           StreamState<SC> &S)
+// Row y of the lane's columns from the rows above (in S) and the decoded row
+// below (d, with the column outside the warp de); written out, then S moves
+// down one row.
+template <int MODE, int DT, bool DST_LO, int SC>
+__device__ __forceinline__ void stream_compute(const DiffFrame &f, int y, int x0, bool edge,
+                                               bool vdst, int lane, float lam, float c,
+                                               const float2 (&d)[SC], float2 de,
+                                               StreamState<SC> &S)
 {
     const float2 Z = make_float2(HOLE, 0.0f);
-    float2 d[SC], de;
-    decode_row<DT, HAS_LO, SC>(below, f.scale, d, de);
-    if (more) {
-        load_row<DT, HAS_LO, SC>(f, y + 3, x0, xe, edge, vsrc, vlo, below);
-        // the row STREAM_PF below that into L2, one request per 128-byte line
-        const int yp = y + 3 + STREAM_PF;
-        if (yp < f.h && x0 < f.w) {
-            constexpr int SRC_LANES = 128 / (SC * (DT == PM_F32_M ? 4 : 2));
-            if (lane % SRC_LANES == 0)
-                prefetch_l2((const char *)f.src + (long long)yp * f.src_pitch +
-                            (long long)x0 * (DT == PM_F32_M ? 4 : 2));
-            if (HAS_LO && lane % (32 / SC) == 0)
-                prefetch_l2(f.lo_in + (long long)yp * f.w + x0);
-        }
-    }
     float2 L = make_float2(__shfl_up_sync(0xffffffffu, S.a[SC - 1].x, 1),
                            __shfl_up_sync(0xffffffffu, S.a[SC - 1].y, 1));
     float2 R = make_float2(__shfl_down_sync(0xffffffffu, S.a[0].x, 1),
@@ -729,17 +718,43 @@ __device__ __forceinline__ void stream_row(const DiffFrame &f, int y, int x0, in
     S.ae = de;
 }
 
+// Row y with its row below already read into `below`, which is refilled
+// with row y + 3 (the row read two steps ahead) when `more`.
+template <int MODE, int DT, bool HAS_LO, bool DST_LO, int SC>
+__device__ __forceinline__ void stream_row(const DiffFrame &f, int y, int x0, int xe, bool edge,
+                                           bool vsrc, bool vlo, bool vdst, int lane, float lam,
+                                           float c, RowRaw<SC> &below, bool more,
+                                           StreamState<SC> &S)
+{
+    float2 d[SC], de;
+    decode_row<DT, HAS_LO, SC>(below, f.scale, d, de);
+    if (more) {
+        load_row<DT, HAS_LO, SC>(f, y + 3, x0, xe, edge, vsrc, vlo, below);
+        // the row STREAM_PF below that into L2, one request per 128-byte line
+        const int yp = y + 3 + STREAM_PF;
+        if (yp < f.h && x0 < f.w) {
+            constexpr int SRC_LANES = 128 / (SC * (DT == PM_F32_M ? 4 : 2));
+            if (lane % SRC_LANES == 0)
+                prefetch_l2((const char *)f.src + (long long)yp * f.src_pitch +
+                            (long long)x0 * (DT == PM_F32_M ? 4 : 2));
+            if (HAS_LO && lane % (32 / SC) == 0)
+                prefetch_l2(f.lo_in + (long long)yp * f.w + x0);
+        }
+    }
+    stream_compute<MODE, DT, DST_LO, SC>(f, y, x0, edge, vdst, lane, lam, c, d, de, S);
+}
+
+// One unit: rows y0 .. y0 + rows - 1 of the strip, by one warp.
 template <int MODE, int DT, bool HAS_LO, bool DST_LO>
-__global__ void __launch_bounds__(256, stream_min_ctas<DT>()) k_diffuse_stream(DiffFrame f,
-                                                                              float lam, float c)
+__device__ __forceinline__ void stream_band(const DiffFrame &f, float lam, float c, int strip,
+                                            int y0, int rows)
 {
     constexpr int SC = stream_cols<DT>();
     const int lane = threadIdx.x;
-    const int x0 = blockIdx.x * (32 * SC) + SC * lane;
-    const int y0 = (blockIdx.y * 8 + threadIdx.y) * STREAM_ROWS;
+    const int x0 = strip * (32 * SC) + SC * lane;
     if (y0 >= f.h)
         return;
-    const int y1 = min(y0 + STREAM_ROWS, f.h);
+    const int y1 = min(y0 + rows, f.h);
     constexpr int VB = SC * (DT == PM_F32_M ? 4 : 2);   // bytes of a lane's encoding: 16
     const bool vsrc = ((uintptr_t)f.src % VB) == 0 && f.src_pitch % VB == 0;
     const bool vlo = ((uintptr_t)f.lo_in % 16) == 0 && f.w % 4 == 0;
@@ -776,6 +791,211 @@ __global__ void __launch_bounds__(256, stream_min_ctas<DT>()) k_diffuse_stream(D
         stream_row<MODE, DT, HAS_LO, DST_LO, SC>(f, y + 1, x0, xe, edge, vsrc, vlo, vdst, lane,
                                                  lam, c, rB, y + 3 < y1, S);
     }
+}
+
+template <int MODE, int DT, bool HAS_LO, bool DST_LO>
+__global__ void __launch_bounds__(256, stream_min_ctas<DT>()) k_diffuse_stream(DiffFrame f,
+                                                                              float lam, float c,
+                                                                              int rows, int strips,
+                                                                              int strip0)
+{
+    const int group = blockIdx.x / strips;
+    stream_band<MODE, DT, HAS_LO, DST_LO>(f, lam, c, strip0 + blockIdx.x - group * strips,
+                                          (group * 8 + threadIdx.y) * rows, rows);
+}
+
+// ---------------------------------------------------------------------------
+// the same walk with the rows staged in shared memory by asynchronous copies
+// ---------------------------------------------------------------------------
+// For FP32 frames whose strips are whole and whose rows are 16-byte aligned,
+// each warp keeps a ring of STREAM_RING rows of its strip in shared memory,
+// filled with cp.async (16-byte pieces: every lane copies its own encoding,
+// lo parts and, for lanes 0 and 31, the 4-byte word of the column outside the
+// warp): STREAM_RING - 1 rows are in flight while a row is computed, without
+// holding them in registers.  A lane reads back only what it copied itself,
+// so cp.async.wait_group alone orders the copies and the reads.  The rows
+// read back are exactly those load_row returns, so the arithmetic and the
+// results are those of the register walk.  (Timed on 8192 x 8192, 10
+// iterations: FP32 0.563 of the HBM peak on algorithmic bytes with registers,
+// 0.623 with a 4-row ring, 0.605 with 6, 0.558 with 8; the 2-byte encodings
+// reached 0.58 with a ring against 0.63 with registers in one wave, so they
+// keep the register walk.)
+constexpr int STREAM_RING = 4;
+
+template <int SC>
+struct RingSlot {
+    static constexpr int SRC = 32 * 16;       // the lanes' encoding, 16 bytes each
+    static constexpr int LO = 32 * SC * 4;    // lo parts: SC / 4 planes of 32 x 16 bytes
+    static constexpr int EDGE = 32 * 8;       // container word and lo part of the outside column
+    static constexpr int BYTES = SRC + LO + EDGE;
+};
+
+template <int DT>
+constexpr size_t stream_ring_smem() { return (size_t)8 * STREAM_RING * RingSlot<stream_cols<DT>()>::BYTES; }
+
+// resident CTAs per SM the ring kernel's registers are fitted to
+template <int DT>
+__host__ __device__ constexpr int stream_ring_ctas() { return DT == PM_F32_M ? 3 : 2; }
+
+__device__ __forceinline__ void cp_async16(unsigned saddr, const void *g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(unsigned saddr, const void *g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(g) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Row y of the lane's columns into the ring slot at shared address sb (rows
+// outside the image are not copied: ring_read returns zeros for them).
+template <int DT, bool HAS_LO, int SC>
+__device__ __forceinline__ void ring_issue(const DiffFrame &f, int y, int x0, int xe, bool edge,
+                                           int lane, unsigned sb)
+{
+    if (y < 0 || y >= f.h || !PM_INB(x0 + SC - 1, f.w))
+        return;
+    constexpr int ES = DT == PM_F32_M ? 4 : 2;
+    const char *row = (const char *)f.src + (long long)y * f.src_pitch;
+    cp_async16(sb + lane * 16, row + (long long)x0 * ES);
+    if (HAS_LO) {
+        const float *lrow = f.lo_in + (long long)y * f.w + x0;
+#pragma unroll
+        for (int q = 0; q < SC / 4; ++q)
+            cp_async16(sb + RingSlot<SC>::SRC + q * 512 + lane * 16, lrow + 4 * q);
+    }
+    if (edge && PM_INB(xe, f.w)) {
+        // the aligned 4-byte word holding column xe (for a 2-byte encoding the
+        // frame's width is a multiple of 8, so the word lies inside the row)
+        const long long xb = ((long long)xe * ES) & ~3ll;
+        const unsigned se = sb + RingSlot<SC>::SRC + RingSlot<SC>::LO + lane * 8;
+        cp_async4(se, row + xb);
+        if (HAS_LO)
+            cp_async4(se + 4, f.lo_in + (long long)y * f.w + xe);
+    }
+}
+
+// Row y from the ring slot at sp, as load_row would read it.
+template <int DT, bool HAS_LO, int SC>
+__device__ __forceinline__ void ring_read(const DiffFrame &f, int y, int xe, bool edge, int lane,
+                                          const unsigned char *sp, RowRaw<SC> &o)
+{
+#pragma unroll
+    for (int k = 0; k < SC; ++k) {
+        o.r[k] = 0u;
+        o.l[k] = 0.0f;
+    }
+    o.re = 0u;
+    o.le = 0.0f;
+    if (y < 0 || y >= f.h)
+        return;
+    const uint4 v = *reinterpret_cast<const uint4 *>(sp + lane * 16);
+    const unsigned u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < SC; ++k)
+        o.r[k] = SC == 8 ? ((k & 1) ? u[k >> 1] >> 16 : u[k >> 1] & 0xffffu) : u[k];
+    if (HAS_LO) {
+#pragma unroll
+        for (int q = 0; q < SC / 4; ++q) {
+            const float4 l = *reinterpret_cast<const float4 *>(sp + RingSlot<SC>::SRC + q * 512 +
+                                                               lane * 16);
+            o.l[4 * q] = l.x;
+            o.l[4 * q + 1] = l.y;
+            o.l[4 * q + 2] = l.z;
+            o.l[4 * q + 3] = l.w;
+        }
+    }
+    if (edge) {
+        const unsigned char *e = sp + RingSlot<SC>::SRC + RingSlot<SC>::LO + lane * 8;
+        const unsigned wv = *reinterpret_cast<const unsigned *>(e);
+        o.re = DT == PM_F32_M ? wv : ((xe & 1) ? wv >> 16 : wv & 0xffffu);
+        if (HAS_LO)
+            o.le = *reinterpret_cast<const float *>(e + 4);
+    }
+}
+
+// One band of a whole strip through the warp's ring (ring: shared address,
+// sp: the same memory as a generic pointer).  Row r lives in slot
+// (r - y0 + 1) % STREAM_RING; one copy group is committed per row, so
+// waiting for all but the STREAM_RING - 2 newest groups completes the row
+// below the one computed.
+template <int MODE, int DT, bool HAS_LO, bool DST_LO>
+__device__ __forceinline__ void stream_band_ring(const DiffFrame &f, float lam, float c, int strip,
+                                                 int y0, int rows, unsigned ring,
+                                                 const unsigned char *sp)
+{
+    constexpr int SC = stream_cols<DT>();
+    constexpr int P = STREAM_RING;
+    constexpr int SB = RingSlot<SC>::BYTES;
+    const int lane = threadIdx.x;
+    const int x0 = strip * (32 * SC) + SC * lane;
+    if (y0 >= f.h)
+        return;
+    const int y1 = min(y0 + rows, f.h);
+    const int xe = lane == 0 ? x0 - 1 : x0 + SC;
+    const bool edge = (lane == 0 || lane == 31) && xe >= 0 && xe < f.w;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        if (y0 - 1 + i <= y1)
+            ring_issue<DT, HAS_LO, SC>(f, y0 - 1 + i, x0, xe, edge, lane, ring + i * SB);
+        cp_async_commit();
+    }
+    cp_async_wait<P - 2>();
+    RowRaw<SC> r;
+    StreamState<SC> S;
+    float2 ue;
+    ring_read<DT, HAS_LO, SC>(f, y0 - 1, xe, edge, lane, sp, r);
+    decode_row<DT, HAS_LO, SC>(r, f.scale, S.u, ue);
+    ring_read<DT, HAS_LO, SC>(f, y0, xe, edge, lane, sp + SB, r);
+    decode_row<DT, HAS_LO, SC>(r, f.scale, S.a, S.ae);
+    if (y0 + P - 1 <= y1)
+        ring_issue<DT, HAS_LO, SC>(f, y0 + P - 1, x0, xe, edge, lane, ring);
+    cp_async_commit();
+    if (MODE == 0) {
+        const f2 c2 = pk(c, c);
+#pragma unroll
+        for (int q = 0; q < SC / 2; ++q)
+            S.fN[q] = link_flux2(pk(S.a[2 * q].x, S.a[2 * q + 1].x),
+                                 pk(S.a[2 * q].y, S.a[2 * q + 1].y),
+                                 pk(S.u[2 * q].x, S.u[2 * q + 1].x),
+                                 pk(S.u[2 * q].y, S.u[2 * q + 1].y), c2);
+    }
+    int sl = 2 % P;   // slot of row y + 1
+    for (int y = y0; y < y1; ++y) {
+        cp_async_wait<P - 2>();
+        ring_read<DT, HAS_LO, SC>(f, y + 1, xe, edge, lane, sp + sl * SB, r);
+        // row y's slot (read one step earlier) takes row y + P
+        const int sr = sl == 0 ? P - 1 : sl - 1;
+        if (y + P <= y1)
+            ring_issue<DT, HAS_LO, SC>(f, y + P, x0, xe, edge, lane, ring + sr * SB);
+        cp_async_commit();
+        float2 d[SC], de;
+        decode_row<DT, HAS_LO, SC>(r, f.scale, d, de);
+        stream_compute<MODE, DT, DST_LO, SC>(f, y, x0, edge, true, lane, lam, c, d, de, S);
+        sl = sl + 1 == P ? 0 : sl + 1;
+    }
+    cp_async_wait<0>();
+}
+
+template <int MODE, int DT, bool HAS_LO, bool DST_LO>
+__global__ void __launch_bounds__(256, stream_ring_ctas<DT>())
+    k_diffuse_stream_ring(DiffFrame f, float lam, float c, int rows, int strips)
+{
+    extern __shared__ __align__(16) unsigned char ring_sm[];
+    constexpr int SB = RingSlot<stream_cols<DT>()>::BYTES;
+    const int group = blockIdx.x / strips;
+    const unsigned char *sp = ring_sm + threadIdx.y * STREAM_RING * SB;
+    stream_band_ring<MODE, DT, HAS_LO, DST_LO>(
+        f, lam, c, blockIdx.x - group * strips, (group * 8 + threadIdx.y) * rows, rows,
+        (unsigned)__cvta_generic_to_shared(sp), sp);
 }
 
 static inline float conductance_scale(float K)
@@ -834,49 +1054,130 @@ cudaError_t launch_diffuse_tiles(const DiffFrame *d_frames, int n_frames, int to
 
 // The streaming kernel for the launch's iterate input and output (lo parts
 // read or not, lo parts or depth written).
-template <int M, int DT>
-static void launch_stream_io(const DiffFrame &f, dim3 grid, dim3 block, float lam, float c,
-                             cudaStream_t s)
+// The launch shape of the streaming kernel.  one_wave: bands of at least 8
+// rows, as tall as it takes for the blocks to fit the resident CTAs
+// (ctas_per_sm on each of the sms SMs) at once.  Otherwise the band height
+// in [32, 256] rows whose grid of strips x ceil(h / (8 rows)) blocks fills
+// the resident CTAs in whole waves most nearly, the smallest such height on
+// ties (images too small to fill one wave with 32-row bands as in one_wave).
+// (Timed on 8192 x 8192 u16: one wave of 114-row bands 0.632 of the HBM peak
+// on algorithmic bytes, 38-row bands in 2.9 waves 0.588, 32-row bands in 3.5
+// waves 0.557.)
+struct StreamShape {
+    int rows, strips, blocks;
+};
+
+StreamShape stream_shape(int w, int h, int sc, int sms, int ctas_per_sm, bool one_wave)
 {
+    StreamShape sh;
+    sh.strips = (w + 32 * sc - 1) / (32 * sc);
+    const long long resident = (long long)sms * ctas_per_sm;
+    if (one_wave || (long long)sh.strips * ((h + 8LL * 32 - 1) / (8LL * 32)) < resident) {
+        const long long per_strip = resident / sh.strips > 0 ? resident / sh.strips : 1;
+        long long r = (h + 8 * per_strip - 1) / (8 * per_strip);
+        r = r < 8 ? 8 : r;
+        sh.rows = (int)(r < h ? r : h);
+        sh.blocks = (int)((long long)sh.strips * ((h + 8LL * sh.rows - 1) / (8LL * sh.rows)));
+        return sh;
+    }
+    double best = -1.0;
+    sh.rows = 32;
+    for (int r = 32; r <= 256; ++r) {
+        const long long blocks = (long long)sh.strips * ((h + 8LL * r - 1) / (8LL * r));
+        const long long waves = (blocks + resident - 1) / resident;
+        const double fill = (double)blocks / (double)(waves * resident);
+        if (fill > best + 1e-9) {
+            best = fill;
+            sh.rows = r;
+        }
+        if ((h + 8LL * r - 1) / (8LL * r) == 1)
+            break;   // one block per strip: taller bands change nothing
+    }
+    sh.blocks = (int)((long long)sh.strips * ((h + 8LL * sh.rows - 1) / (8LL * sh.rows)));
+    return sh;
+}
+
+// One launch of the register walk (strips [strip0, strip0 + strips)) or of
+// the ring walk, for the launch's iterate input and output (lo parts read or
+// not, lo parts or depth written).
+template <int M, int DT, bool RING>
+static void launch_stream_io(const DiffFrame &f, float lam, float c, const StreamShape &sh,
+                             int strip0, cudaStream_t s)
+{
+    const dim3 block(32, 8);
+    const size_t smem = RING ? stream_ring_smem<DT>() : 0;
+#define PM_STREAM_LAUNCH(LO, DLO)                                                              \
+    do {                                                                                       \
+        if constexpr (RING)                                                                    \
+            k_diffuse_stream_ring<M, DT, LO, DLO><<<sh.blocks, block, smem, s>>>(             \
+                f, lam, c, sh.rows, sh.strips);                                                \
+        else                                                                                   \
+            k_diffuse_stream<M, DT, LO, DLO><<<sh.blocks, block, 0, s>>>(f, lam, c, sh.rows,  \
+                                                                         sh.strips, strip0);   \
+    } while (0)
     if (f.lo_in) {
         if (f.dst_lo)
-            k_diffuse_stream<M, DT, true, true><<<grid, block, 0, s>>>(f, lam, c);
+            PM_STREAM_LAUNCH(true, true);
         else
-            k_diffuse_stream<M, DT, true, false><<<grid, block, 0, s>>>(f, lam, c);
+            PM_STREAM_LAUNCH(true, false);
     } else {
         if (f.dst_lo)
-            k_diffuse_stream<M, DT, false, true><<<grid, block, 0, s>>>(f, lam, c);
+            PM_STREAM_LAUNCH(false, true);
         else
-            k_diffuse_stream<M, DT, false, false><<<grid, block, 0, s>>>(f, lam, c);
+            PM_STREAM_LAUNCH(false, false);
     }
+#undef PM_STREAM_LAUNCH
+}
+
+// FP32 frames with whole, aligned strips: the ring walk over those strips;
+// every other strip (and every 2-byte encoding): the register walk in one
+// wave.
+template <int M, int DT>
+static cudaError_t launch_stream_dt(const DiffFrame &f, float lam, float c, int sms,
+                                    cudaStream_t s)
+{
+    constexpr int SC = stream_cols<DT>();
+    static_assert(stream_ring_smem<PM_F32_M>() <= 48 * 1024, "ring within the default shared memory");
+    const bool aligned = DT == PM_F32_M && ((uintptr_t)f.src % 16) == 0 &&
+                         f.src_pitch % 16 == 0 && ((uintptr_t)f.lo_in % 16) == 0 &&
+                         ((uintptr_t)f.dst % 16) == 0 && f.w % 4 == 0;
+    const int whole = aligned ? f.w / (32 * SC) : 0;
+    if (whole > 0) {
+        const StreamShape sh =
+            stream_shape(whole * 32 * SC, f.h, SC, sms, stream_ring_ctas<DT>(), false);
+        launch_stream_io<M, PM_F32_M, true>(f, lam, c, sh, 0, s);
+    }
+    if (whole * 32 * SC < f.w) {
+        const StreamShape sh =
+            stream_shape(f.w - whole * 32 * SC, f.h, SC, sms, stream_min_ctas<DT>(), true);
+        launch_stream_io<M, DT, false>(f, lam, c, sh, whole, s);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_diffuse_stream(const DiffFrame &f, float lambda, float K, int mode,
                                   cudaStream_t s)
 {
-    const int sc = f.src_dtype == PM_F32_M ? stream_cols<PM_F32_M>() : stream_cols<PM_U16_MM>();
-    dim3 grid((f.w + 32 * sc - 1) / (32 * sc), (f.h + 8 * STREAM_ROWS - 1) / (8 * STREAM_ROWS));
-    const dim3 block(32, 8);
     const float c = conductance_scale(K);
     if (f.src_dtype != PM_U16_MM && f.src_dtype != PM_F16_M && f.src_dtype != PM_F32_M)
         return cudaErrorInvalidValue;
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 1;
     const int dt = f.src_dtype;
     if (mode == 0) {
         if (dt == PM_U16_MM)
-            launch_stream_io<0, PM_U16_MM>(f, grid, block, lambda, c, s);
-        else if (dt == PM_F16_M)
-            launch_stream_io<0, PM_F16_M>(f, grid, block, lambda, c, s);
-        else
-            launch_stream_io<0, PM_F32_M>(f, grid, block, lambda, c, s);
-    } else {
-        if (dt == PM_U16_MM)
-            launch_stream_io<1, PM_U16_MM>(f, grid, block, lambda, c, s);
-        else if (dt == PM_F16_M)
-            launch_stream_io<1, PM_F16_M>(f, grid, block, lambda, c, s);
-        else
-            launch_stream_io<1, PM_F32_M>(f, grid, block, lambda, c, s);
+            return launch_stream_dt<0, PM_U16_MM>(f, lambda, c, sms, s);
+        if (dt == PM_F16_M)
+            return launch_stream_dt<0, PM_F16_M>(f, lambda, c, sms, s);
+        return launch_stream_dt<0, PM_F32_M>(f, lambda, c, sms, s);
     }
-    return cudaGetLastError();
+    if (dt == PM_U16_MM)
+        return launch_stream_dt<1, PM_U16_MM>(f, lambda, c, sms, s);
+    if (dt == PM_F16_M)
+        return launch_stream_dt<1, PM_F16_M>(f, lambda, c, sms, s);
+    return launch_stream_dt<1, PM_F32_M>(f, lambda, c, sms, s);
 }
 
 PM_BOUNDS_QUERY(bounds_diffuse)

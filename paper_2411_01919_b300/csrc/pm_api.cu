@@ -81,7 +81,7 @@ Layout make_layout(long long npx, int frames, int H, int max_chunks)
     L.state = take(F * sizeof(RState));
     L.planes = take(F * MAX_PLANES * sizeof(pm_plane));
     L.chunk_base = take((F + 1) * 4);
-    L.counter = take(4);
+    L.counter = take(4 * (1 + MAX_PLANES));   // compaction grid counter, scoring work counters
     L.total = off;
     return L;
 }
@@ -187,8 +187,6 @@ struct pm_ctx {
     char *eg = nullptr;                   // edge / region scratch for max_npx (on first use)
     int *h_eg = nullptr;                  // pinned: region count, error flag
     cudaStream_t gstream = nullptr;       // graph stream when the caller passes the legacy stream
-    cudaStream_t rstream = nullptr;       // side stream of the plane refits
-    cudaEvent_t rev[2] = {nullptr, nullptr};
     cudaEvent_t gev[2] = {nullptr, nullptr};
     long long launches = 0;               // kernels launched by the last call
     int last_n = 0;                       // frames of the last call
@@ -455,6 +453,12 @@ pm_status enqueue_ransac(pm_ctx *ctx, RFrame *d_rframes, int n, long long total_
     L.prm = ransac_params(ctx);
     L.d_counter = ctx->at<unsigned>(ctx->lay.counter);
     L.fine_score = total_chunks < (long long)ctx->sms * 32;
+    // small batches draw the hypotheses inside the compaction launch (one
+    // launch less per round on a latency-bound path); large ones keep the
+    // hypothesis launch, whose blocks would otherwise queue behind the
+    // compaction's resident grid
+    L.hyp_fold_chunks =
+        L.fine_score && ctx->max_chunks <= HYP_FOLD_MAX_CHUNKS ? ctx->max_chunks : 0;
     const int hb = score_hyp_block(L.fine_score, L.prm.H);
     const long long score_items = total_chunks * (L.fine_score ? (L.prm.H + hb - 1) / hb : 1);
     const long long sb = (long long)ctx->sms * score_ctas_per_sm(L.fine_score, L.prm.H);
@@ -471,14 +475,6 @@ pm_status enqueue_ransac(pm_ctx *ctx, RFrame *d_rframes, int n, long long total_
         L.chunk_blocks = 1;
     if (L.remove_blocks < 1)
         L.remove_blocks = 1;
-    if (!ctx->rstream) {
-        PM_CK(cudaStreamCreateWithFlags(&ctx->rstream, cudaStreamNonBlocking));
-        for (int i = 0; i < 2; ++i)
-            PM_CK(cudaEventCreateWithFlags(&ctx->rev[i], cudaEventDisableTiming));
-    }
-    L.side = ctx->rstream;
-    L.ev_fork = ctx->rev[0];
-    L.ev_join = ctx->rev[1];
     PM_CK(ransac_init(L, s));
     ctx->launches += RANSAC_INIT_LAUNCHES;
     for (int r = 0; r < ctx->rp.max_planes; ++r) {
@@ -486,7 +482,7 @@ pm_status enqueue_ransac(pm_ctx *ctx, RFrame *d_rframes, int n, long long total_
         cudaEvent_t a = ctx->timing == 2 ? ctx->kev[2 * r] : nullptr;
         cudaEvent_t b = ctx->timing == 2 ? ctx->kev[2 * r + 1] : nullptr;
         PM_CK(ransac_round(L, r, last, s, a, b));
-        ctx->launches += ransac_round_launches(L.fine_score) - (last ? 1 : 0);
+        ctx->launches += ransac_round_launches(L.fine_score, L.hyp_fold_chunks > 0);
     }
     return PM_OK;
 }
@@ -730,7 +726,7 @@ pm_status pm_create(const pm_diffusion_params *dp, const pm_ransac_params *rp,
         e = cudaMallocHost(&ctx->h_rg, CREATE_REGIONS * sizeof(pm_region_plane));
     if (e == cudaSuccess) {
         ctx->h_rg_cap = CREATE_REGIONS;
-        e = cudaMemset(ctx->arena + ctx->lay.counter, 0, 4);
+        e = cudaMemset(ctx->arena + ctx->lay.counter, 0, 4 * (1 + MAX_PLANES));
     }
     if (e == cudaSuccess)
         e = cudaMallocHost(&ctx->h_state, max_frames * sizeof(RState));
@@ -768,11 +764,6 @@ void pm_destroy(pm_ctx *ctx)
         cudaFreeHost(ctx->h_eg);
     if (ctx->gstream)
         cudaStreamDestroy(ctx->gstream);
-    if (ctx->rstream)
-        cudaStreamDestroy(ctx->rstream);
-    for (int i = 0; i < 2; ++i)
-        if (ctx->rev[i])
-            cudaEventDestroy(ctx->rev[i]);
     for (int i = 0; i < 2; ++i)
         if (ctx->gev[i])
             cudaEventDestroy(ctx->gev[i]);

@@ -65,6 +65,7 @@ constexpr int MAX_PLANES = 64;
 constexpr int NMOM = 9;                  // Sx Sy Sz Sxx Sxy Sxz Syy Syz Szz
 constexpr int GROUP = 1;                 // chunks per moment record
 constexpr int REMOVE_THREADS = 256;      // threads of the removal kernel (CHUNK / 4 candidates each)
+constexpr int REFIT_WARPS = 8;          // warps of a refit block (the scoring and removal block size)
 // per-group moment record: gated inliers then the other inliers, each NMOM
 // double-float sums (h, l), then two int counts (as float bit patterns),
 // padded to 40 words
@@ -108,8 +109,13 @@ struct RState {
     int score_done;   // scoring work items finished this round
     int best_h;
     int best_count;
-    int refit_pending;  // 1 from an accepted selection until its refit
-    int refit_groups;   // moment records of that round
+    // what the refit of an accepted round needs, kept per round parity: the
+    // refit of round r runs beside the scoring (and selection) of round r + 1
+    int rf_pending[2];  // [round & 1]: 1 from an accepted selection until its refit
+    int rf_groups[2];   // moment records of that round
+    int rf_h[2];        // its winning hypothesis
+    int rf_count[2];    // and the winner's inlier count
+    float4 rf_p0[2];    // its first sample point (the moment origin)
     float4 best_plane;
     float4 p0;        // first sample point of the winner (moment origin)
     int m_hist[MAX_PLANES];  // candidates scored in each round (0 once stopped)
@@ -238,10 +244,14 @@ struct RansacLaunch {
     int score_blocks;     // persistent grid sizes
     int chunk_blocks;     // grid of k_mark0 / k_compact (their resident CTAs, at most one per chunk)
     int remove_blocks;    // grid of k_remove
-    unsigned *d_counter;  // grid-completion counter of the compaction kernel
+    unsigned *d_counter;  // [0] grid-completion counter of the compaction kernel,
+                          // [1 + r] work counter of round r's scoring
     bool fine_score;      // smaller hypothesis blocks, selection fused (small batches)
-    cudaStream_t side;    // the refit's stream
-    cudaEvent_t ev_fork, ev_join;   // removal done -> refit; refit done -> next selection
+    // > 0: the next round's hypotheses are drawn by extra blocks of the
+    // compaction launch, with a shared-memory kept-count prefix of this many
+    // chunks (a frame's largest chunk count; small batches only); 0: by a
+    // launch of their own
+    int hyp_fold_chunks;
 };
 // Per-region RANSAC (regions.cu): all pointers device memory.
 struct RegionLaunch {
@@ -298,8 +308,16 @@ int compact_ctas_per_sm();                 // ... of k_compact (and k_mark0)
 cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream_t s,
                          cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
 constexpr int RANSAC_INIT_LAUNCHES = 3;
-// launches per round: 5 with the selection fused into scoring (small
-// batches), 6 without; the last round skips compaction
-inline int ransac_round_launches(bool fine) { return fine ? 5 : 6; }
+// chunk count up to which the hypotheses are drawn inside the compaction
+// launch (the kept-count prefix of a frame's chunks held in shared memory)
+constexpr int HYP_FOLD_MAX_CHUNKS = 4096;
+// launches per round: scoring (with the selection fused for small batches,
+// else a selection launch), removal and compaction, plus a hypothesis launch
+// unless the hypotheses are drawn inside the compaction; the last round
+// launches its refit in place of the compaction
+inline int ransac_round_launches(bool fine, bool hyp_fold)
+{
+    return (fine ? 3 : 4) + (hyp_fold ? 0 : 1);
+}
 
 }  // namespace pm

@@ -2,8 +2,13 @@
 // sm_103a, batched over frames.
 //
 // One plane round of every frame still running:
-//   k_hyp     : Philox4x64-10 -> three candidate indices -> FP32 plane (Alg. 2
-//               "select random subset of 3 points", "fit plane model")
+//   hypotheses: Philox4x64-10 -> three candidate indices -> FP32 plane (Alg. 2
+//               "select random subset of 3 points", "fit plane model").  Drawn
+//               by extra blocks of the previous compaction launch, which find
+//               candidate i of the list being built in the list it is built
+//               from (kept-count prefix, then the keep bits of one chunk);
+//               k_hyp draws them from the compacted list for frames of more
+//               than HYP_FOLD_MAX_CHUNKS chunks.
 //   k_score   : every hypothesis against every candidate on FP32 CUDA cores
 //               (Alg. 2 inner parallel loop); a box test per 32-candidate
 //               segment settles the pairs it proves to hold no inlier or
@@ -14,14 +19,16 @@
 //               key); for large ones k_select does, one block per frame.
 //   k_remove  : labels of the winner's inliers, keep bitmask of the rest,
 //               compensated-FP32 moments of the inliers, one record per chunk.
-//   k_refit   : the group records reduced in compensated FP32 in a fixed
-//               order, the 3x3 eigenproblem solved in FP64 -> plane.  It runs
-//               on a side stream beside the compaction and the next round's
-//               hypotheses (and, for large batches, scoring): the next
-//               selection, which overwrites the winner it reads, waits for it.
-//   k_compact : order-preserving compaction of the kept candidates; the last
-//               CTA of the grid plans the next round (candidate counts, stop
-//               rule, cross-frame prefix of chunks).
+//   refit     : the group records reduced in compensated FP32 in a fixed
+//               order, the 3x3 eigenproblem solved in FP64 -> plane.  A round's
+//               refit runs in n extra blocks of the next round's scoring
+//               launch (its inputs are kept per round parity, so the next
+//               selection does not overwrite them); only the last round's
+//               refit is a launch of its own (k_refit).
+//   k_compact : order-preserving compaction of the kept candidates (and the
+//               next round's hypotheses); the last CTA of the grid plans the
+//               next round (candidate counts, stop rule, cross-frame prefix of
+//               chunks).
 // "Last CTA" is detected with a __threadfence() and an atomic counter; no CTA
 // ever waits for another.  Work is split into chunks of CHUNK candidates; a
 // frame's chunking never depends on the other frames of the batch, and every
@@ -126,8 +133,11 @@ __device__ void plan_round(RFrame *frames, int n, int *chunk_base, int min_inlie
             st->n_planes = 0;
             st->best_h = -1;
             st->best_count = -1;
-            st->refit_pending = 0;
-            st->refit_groups = 0;
+            st->rf_pending[0] = 0;
+            st->rf_pending[1] = 0;
+            st->rf_groups[0] = 0;
+            st->rf_groups[1] = 0;
+            st->score_done = 0;
             for (int r = 0; r < MAX_PLANES; ++r)
                 st->m_hist[r] = 0;
             st->pairs_eval = 0ull;
@@ -140,6 +150,7 @@ __device__ void plan_round(RFrame *frames, int n, int *chunk_base, int min_inlie
             }
             nc = st->done ? 0 : (st->M + CHUNK - 1) / CHUNK;
             st->m_hist[round] = st->done ? 0 : st->M;
+            st->score_done = 0;
         }
         st->nchunks = nc;
         mine += nc;
@@ -159,6 +170,8 @@ __global__ void __launch_bounds__(1024) k_plan0(RFrame *frames, int n, int *chun
 {
     if (threadIdx.x == 0)
         *grid_counter = 0u;
+    if (threadIdx.x < MAX_PLANES)
+        grid_counter[1 + threadIdx.x] = 0u;   // the scoring rounds' work counters
     plan_round(frames, n, chunk_base, 0, 0, true);
 }
 
@@ -314,18 +327,183 @@ __device__ int kept_before(const RFrame &F, int c)
     return s_sum;
 }
 
-// Compaction of every chunk; the last CTA of the grid plans round `next`.
-// src_image: round 0 (the source list is the pixel array itself).
-__global__ void __launch_bounds__(256) k_compact(RFrame *frames, int n, int *chunk_base,
-                                                 int round, bool src_image, int next,
-                                                 int min_inliers, unsigned *grid_counter)
+// ---------------------------------------------------------------------------
+// hypotheses
+// ---------------------------------------------------------------------------
+// Candidate index k (0..2) of hypothesis h of round `round` in the round's list
+// of M: a Philox4x64-10 draw on (h, round, frame index), index umulhi(draw, M).
+__device__ __forceinline__ unsigned long long sample_index(const RFrame &F, const RParams &prm,
+                                                           int round, int h, int k,
+                                                           unsigned long long M)
 {
-    // each CTA takes a contiguous run of chunks, so the running offset within
-    // a frame is summed once per run and then advanced chunk by chunk
+    unsigned long long c[4] = {(unsigned long long)h, (unsigned long long)round, F.frame_idx, 0ull};
+    philox4x64_10(c, prm.seed, 0ull);
+    return __umul64hi(k == 0 ? c[0] : k == 1 ? c[1] : c[2], M);
+}
+
+// The FP32 plane through the three candidates of hypothesis h; degenerate
+// triples get count -1.
+__device__ __forceinline__ void store_hypothesis(const RFrame &F, int h, float4 q0, float4 q1,
+                                                 float4 q2)
+{
+    float4 pl;
+    const bool ok = hyp_plane(make_float3(q0.x, q0.y, q0.z), make_float3(q1.x, q1.y, q1.z),
+                              make_float3(q2.x, q2.y, q2.z), pl);
+    F.hyp[h] = pl;
+    F.hyp_p0[h] = q0;
+    F.counts[h] = ok ? 0 : -1;
+}
+
+// The round's hypotheses from its compacted list (frames larger than the
+// compaction launch's shared-memory prefix).
+__global__ void __launch_bounds__(128) k_hyp(RFrame *frames, RParams prm, int round)
+{
+    const RFrame &F = frames[blockIdx.y];
+    if (F.st->done)
+        return;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= prm.H)
+        return;
+    const float4 *pts = F.cpt[round & 1];
+    const unsigned long long M = (unsigned long long)F.st->M;
+    float4 q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const unsigned long long i = sample_index(F, prm, round, h, k, M);
+        q[k] = PM_INB(i, F.npx) ? pts[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    store_hypothesis(F, h, q[0], q[1], q[2]);
+}
+
+constexpr int COMPACT_THREADS = 256;
+constexpr int HYP_PER_BLOCK = 85;   // hypotheses per drawing block (3 threads each of 256)
+
+// Candidate i of the compacted list, read from the source list before the
+// compaction: the chunk c with pre[c] <= i < pre[c + 1] (pre: exclusive prefix
+// of the frame's kept counts over its nc chunks), then the (i - pre[c])-th set
+// bit of the chunk's keep words -- the same candidate the compaction moves to
+// position i.
+__device__ float4 kept_candidate(const RFrame &F, const int *pre, int nc, bool src_image, int src,
+                                 unsigned long long i)
+{
+    int lo = 0, hi = nc - 1;   // the last chunk whose prefix is <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((unsigned long long)pre[mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    int r = (int)(i - (unsigned long long)pre[lo]);
+    unsigned kw[CHUNK_WORDS];
+    const long long wbase = (long long)lo * CHUNK_WORDS;
+    if (PM_INB(wbase + CHUNK_WORDS - 1, (long long)nchunks_of(F) * CHUNK_WORDS)) {
+        const uint4 *k4 = reinterpret_cast<const uint4 *>(F.keepbits + wbase);
+#pragma unroll
+        for (int q = 0; q < CHUNK_WORDS / 4; ++q) {
+            const uint4 v = __ldcg(k4 + q);
+            kw[4 * q] = v.x;
+            kw[4 * q + 1] = v.y;
+            kw[4 * q + 2] = v.z;
+            kw[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < CHUNK_WORDS; ++q)
+            kw[q] = 0u;
+    }
+    // the word holding the r-th kept candidate of the chunk, then the bit
+    int w = 0;
+    unsigned word = 0u;
+    bool found = false;
+#pragma unroll
+    for (int q = 0; q < CHUNK_WORDS; ++q) {
+        const int pc = __popc(kw[q]);
+        if (!found) {
+            if (r < pc) {
+                found = true;
+                w = q;
+                word = kw[q];
+            } else {
+                r -= pc;
+            }
+        }
+    }
+    int bit = 0;
+#pragma unroll
+    for (int width = 16; width > 0; width >>= 1) {
+        const unsigned low = word & ((1u << width) - 1u);
+        const int pc = __popc(low);
+        if (r >= pc) {
+            r -= pc;
+            word >>= width;
+            bit += width;
+        } else {
+            word = low;
+        }
+    }
+    const long long j = (long long)lo * CHUNK + 32 * w + bit;
+    const long long npx = F.npx;
+    if (!PM_INB(j, npx))
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (src_image)
+        return make_float4(F.P[j], F.P[npx + j], F.P[2 * npx + j], __int_as_float((int)j));
+    return F.cpt[src][j];
+}
+
+// The hypotheses [hb * HYP_PER_BLOCK, hb * HYP_PER_BLOCK + HYP_PER_BLOCK) of
+// round `next` of a frame, drawn beside the compaction that builds that
+// round's list (same draws and the same candidates as from the compacted
+// list): thread t finds candidate t % 3 of hypothesis t / 3, and the planes
+// are formed from shared memory.  pre: shared memory for cap + 1 prefix
+// entries.
+__device__ void hyp_block(const RFrame &F, const RParams &prm, int next, int hb, bool src_image,
+                          int src, int min_inliers, int *pre, int cap)
+{
+    __shared__ float4 q[3 * HYP_PER_BLOCK];
+    RState *st = F.st;
+    const int nc = st->nchunks;
+    if (st->done || nc < 1 || !PM_INB(nc, cap + 1))   // (block-uniform; cap bounds every frame)
+        return;
+    const int per = (nc + blockDim.x - 1) / blockDim.x;
+    const int c0 = threadIdx.x * per, c1 = min(nc, c0 + per);
+    int mine = 0;
+    for (int c = c0; c < c1; ++c)
+        mine += __ldcg(F.kept + c);
+    int total;
+    int off = block_exscan(mine, &total);
+    for (int c = c0; c < c1; ++c) {
+        pre[c] = off;
+        off += __ldcg(F.kept + c);
+    }
+    if (threadIdx.x == 0)
+        pre[nc] = total;
+    __syncthreads();
+    // the stop rule of the next round's planning: no round, no hypotheses
+    if (total < 3 || total < min_inliers)
+        return;
+    const int t = (int)threadIdx.x;
+    const int h0 = hb * HYP_PER_BLOCK;
+    if (t < 3 * HYP_PER_BLOCK && h0 + t / 3 < prm.H) {
+        const unsigned long long i =
+            sample_index(F, prm, next, h0 + t / 3, t % 3, (unsigned long long)total);
+        q[t] = PM_INB(i, (unsigned long long)total) ? kept_candidate(F, pre, nc, src_image, src, i)
+                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    if (t < HYP_PER_BLOCK && h0 + t < prm.H)
+        store_hypothesis(F, h0 + t, q[3 * t], q[3 * t + 1], q[3 * t + 2]);
+}
+
+// Compaction by block b of nb: each takes a contiguous run of chunks, so the
+// running offset within a frame is summed once per run and then advanced
+// chunk by chunk.
+__device__ void compact_run(RFrame *frames, int n, const int *chunk_base, int src, int dst,
+                            bool src_image, int b, int nb)
+{
     const int total = chunk_base[n];
-    const int src = round & 1, dst = src_image ? 0 : src ^ 1;
-    const int per = (total + gridDim.x - 1) / gridDim.x;
-    const int w0 = blockIdx.x * per, w1 = min(total, w0 + per);
+    const int per = (total + nb - 1) / nb;
+    const int w0 = b * per, w1 = min(total, w0 + per);
     int cur_f = -1, off = 0;
     for (int wi = w0; wi < w1; ++wi) {
         const int f = frame_of(chunk_base, n, wi);
@@ -340,51 +518,37 @@ __global__ void __launch_bounds__(256) k_compact(RFrame *frames, int n, int *chu
         compact_chunk(F, c, F.st->nchunks, src, dst, src_image, off);
         off += __ldcg(F.kept + c);
     }
+}
+
+// Compaction of every chunk; the last CTA of the grid plans round `next`.
+// src_image: round 0 (the source list is the pixel array itself).  With
+// hyp_cap > 0 the first n * ceil(H / HYP_PER_BLOCK) blocks draw round
+// `next`'s hypotheses instead (hyp_cap: the largest chunk count of a frame,
+// for the dynamic shared memory of the prefix) and the other ncompact blocks
+// compact.
+__global__ void __launch_bounds__(COMPACT_THREADS)
+    k_compact(RFrame *frames, int n, int *chunk_base, int round, bool src_image, int next,
+              int min_inliers, unsigned *grid_counter, RParams prm, int hyp_cap, int ncompact)
+{
+    extern __shared__ int pre_sm[];
+    const int src = round & 1, dst = src_image ? 0 : src ^ 1;
+    const int per_frame = hyp_cap > 0 ? (prm.H + HYP_PER_BLOCK - 1) / HYP_PER_BLOCK : 0;
+    const int nhyp = n * per_frame;
+    if ((int)blockIdx.x < nhyp) {
+        const int f = (int)blockIdx.x / per_frame;
+        hyp_block(frames[f], prm, next, (int)blockIdx.x - f * per_frame, src_image, src,
+                  min_inliers, pre_sm, hyp_cap);
+    } else {
+        compact_run(frames, n, chunk_base, src, dst, src_image, (int)blockIdx.x - nhyp, ncompact);
+    }
     if (last_cta_of_grid(grid_counter))
         plan_round(frames, n, chunk_base, min_inliers, next, false);
 }
 
 // ---------------------------------------------------------------------------
-// hypotheses
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_hyp(RFrame *frames, RParams prm, int round)
-{
-    const RFrame &F = frames[blockIdx.y];
-    RState *st = F.st;
-    if (st->done)
-        return;
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        st->score_done = 0;
-    // the removal adds each chunk's kept candidates warp by warp
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < st->nchunks; c += gridDim.x * blockDim.x)
-        if (PM_INB(c, nchunks_of(F)))
-            F.kept[c] = 0;
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= prm.H)
-        return;
-    const unsigned long long M = (unsigned long long)st->M;
-    unsigned long long c[4] = {(unsigned long long)h, (unsigned long long)round, F.frame_idx, 0ull};
-    philox4x64_10(c, prm.seed, 0ull);
-    const float4 *pts = F.cpt[round & 1];
-    const unsigned long long i0 = __umul64hi(c[0], M), i1 = __umul64hi(c[1], M),
-                             i2 = __umul64hi(c[2], M);
-    if (!(PM_INB(i0, F.npx) && PM_INB(i1, F.npx) && PM_INB(i2, F.npx)))
-        return;
-    float4 q0 = pts[i0];
-    float4 q1 = pts[i1];
-    float4 q2 = pts[i2];
-    float4 pl;
-    bool ok = hyp_plane(make_float3(q0.x, q0.y, q0.z), make_float3(q1.x, q1.y, q1.z),
-                        make_float3(q2.x, q2.y, q2.z), pl);
-    F.hyp[h] = pl;
-    F.hyp_p0[h] = q0;
-    F.counts[h] = ok ? 0 : -1;
-}
-
-// ---------------------------------------------------------------------------
 // selection: argmax of (count, -h) by one block
 // ---------------------------------------------------------------------------
-__device__ void select_winner(const RFrame &F, const RParams &prm)
+__device__ void select_winner(const RFrame &F, const RParams &prm, int round)
 {
     __shared__ unsigned long long wk[32];
     RState *st = F.st;
@@ -415,10 +579,15 @@ __device__ void select_winner(const RFrame &F, const RParams &prm)
             st->best_count = best_count;
             st->best_plane = __ldcg(F.hyp + best_h);
             st->p0 = __ldcg(F.hyp_p0 + best_h);
-            // what this round's refit needs, fixed before the next round's
-            // planning changes the frame's state
-            st->refit_groups = (st->nchunks + GROUP - 1) / GROUP;
-            st->refit_pending = 1;
+            // what this round's refit needs, in this round's parity slot: the
+            // refit runs beside the next round's selection, which fills the
+            // other slot
+            const int slot = round & 1;
+            st->rf_groups[slot] = (st->nchunks + GROUP - 1) / GROUP;
+            st->rf_h[slot] = best_h;
+            st->rf_count[slot] = best_count;
+            st->rf_p0[slot] = st->p0;
+            st->rf_pending[slot] = 1;
         }
     }
     __syncthreads();
@@ -535,14 +704,35 @@ __device__ __forceinline__ void score_list(const float4 *hpl, const unsigned sho
         score_batch<1, FULL>(hpl, lst, e0, len, sp, sc, nthr2, hcnt, lane);
 }
 
+// Block-shared scratch of a refit (the scoring kernel lends it part of its
+// dynamic shared memory).
+struct RefitShared {
+    float ss[REFIT_WARPS][2 * NMOM];   // per-warp double-float sums
+    float sc[REFIT_WARPS][2 * NMOM];
+    int sn[REFIT_WARPS][2];            // per-warp counts of the two sets
+    double acc[2 * NMOM];
+    long long cnt[2];
+};
+
+static_assert(SCORE_THREADS == 32 * REFIT_WARPS && REMOVE_THREADS == 32 * REFIT_WARPS,
+              "a refit runs in scoring and in removal-sized blocks");
+static_assert(sizeof(RefitShared) <= score_smem_bytes<256>(), "refit scratch fits the scoring smem");
+
+__device__ __noinline__ void refit_frame(const RFrame &F, const RParams &prm, int round, RefitShared &rs);
+
 // INNER: a work item is a whole chunk, its hypothesis blocks scored one
 // after another on the same points and boxes (large batches); otherwise a
 // work item is one (chunk, hypothesis block) pair (more items for small
-// batches).
+// batches).  Blocks take work items from a counter (`work`, zeroed when the
+// batch starts), so a grid of the resident CTAs ends together whatever the
+// items cost.  From the second round on, the blocks first refit the previous
+// round's winners (frame f by block f mod grid): the refit reads only that
+// round's moment records and its parity slot of the state, which nothing in
+// this round's scoring and selection writes.
 template <int HB, bool FUSE, bool INNER>
 __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
                                                          const int *chunk_base, RParams prm,
-                                                         int round)
+                                                         int round, unsigned *work)
 {
     extern __shared__ float4 sm[];
     float4 *pts = sm;                  // [CHUNK] candidates of the chunk
@@ -561,7 +751,23 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
     const float nthr2 = -prm.thr2;
     const float cull_thr = prm.cull_thr, incl_thr = prm.incl_thr;
     unsigned short *my = lst + wid * HB;
-    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    __shared__ int s_item;
+    if (round > 0) {
+        for (int f = blockIdx.x; f < n; f += gridDim.x) {
+            const RFrame &F = frames[f];
+            if (F.st->rf_pending[(round - 1) & 1])   // (block-uniform)
+                refit_frame(F, prm, round - 1, *reinterpret_cast<RefitShared *>(sm));
+            __syncthreads();   // thread 0 ends the refit before the scratch is reused
+        }
+    }
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0)
+            s_item = (int)atomicAdd(work, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= total)
+            break;
         const int wi = it / per_chunk;
         const int hb_first = INNER ? 0 : it - wi * nhb, hb_end = INNER ? nhb : hb_first + 1;
         const int f = frame_of(chunk_base, n, wi);
@@ -571,6 +777,9 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
         const int base = c * CHUNK;
         const int cnt = max(0, min(CHUNK, st->M - base));
         const float4 *src = F.cpt[round & 1] + base;
+        // the removal adds the chunk's kept candidates warp by warp
+        if (threadIdx.x == 0 && hb_first == 0 && PM_INB(c, nchunks_of(F)))
+            F.kept[c] = 0;
         const int nseg = (cnt + SEG - 1) / SEG;
         __syncthreads();
         for (int j = threadIdx.x; j < cnt; j += SCORE_THREADS)
@@ -676,7 +885,7 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
             __syncthreads();   // hpl, hw, hcnt are refilled for the next block
         }
         if (FUSE && last_item_of_frame(&st->score_done, st->nchunks * per_chunk))
-            select_winner(F, prm);
+            select_winner(F, prm, round);
     }
 }
 
@@ -832,17 +1041,18 @@ __device__ void smallest_eigenpair(const double a[3][3], double &lmin, double v[
     }
 }
 
-// FP64 reduction of a frame's group records in a fixed order and the refit;
-// run by one block of REMOVE_THREADS threads.
-__device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
+// FP64 reduction of a frame's group records in a fixed order and the refit
+// of round `round`'s winner; run by one block of REFIT_WARPS warps.
+__device__ __noinline__ void refit_frame(const RFrame &F, const RParams &prm, int round, RefitShared &rs)
 {
     // The group records are reduced in compensated FP32, in a fixed order
     // (warp w takes records w, w + 8, ...; lane v value v; then the warps in
     // order); only the final sums are widened to FP64 for the eigen-solve.
     RState *st = F.st;
-    const int ngroups = st->refit_groups;
+    const int slot = round & 1;
+    const int ngroups = st->rf_groups[slot];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = (int)(blockDim.x >> 5);
+    const int nw = REFIT_WARPS;
     float vs = 0.0f, vc = 0.0f;
     int vn = 0;
     // lane v < 2 NMOM: double-float sum (h, l) of value v; lanes 2 NMOM, +1: counts
@@ -867,40 +1077,36 @@ __device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
                 vn += __float_as_int(a[u]);
         }
     }
-    __shared__ float ss[32][2 * NMOM], sc[32][2 * NMOM];
-    __shared__ int sn[32][2];
     if (lane < 2 * NMOM) {
-        ss[wid][lane] = vs;
-        sc[wid][lane] = vc;
+        rs.ss[wid][lane] = vs;
+        rs.sc[wid][lane] = vc;
     } else if (lane < 2 * NMOM + 2) {
-        sn[wid][lane - 2 * NMOM] = vn;
+        rs.sn[wid][lane - 2 * NMOM] = vn;
     }
     __syncthreads();
-    __shared__ double acc_sh[2 * NMOM];
-    __shared__ long long cnt_sh[2];
     if (wid == 0) {
         if (lane < 2 * NMOM) {
-            float s0 = ss[0][lane], c0 = sc[0][lane];
+            float s0 = rs.ss[0][lane], c0 = rs.sc[0][lane];
             for (int w = 1; w < nw; ++w)
-                df_merge(s0, c0, ss[w][lane], sc[w][lane]);
-            acc_sh[lane] = (double)s0 + (double)c0;
+                df_merge(s0, c0, rs.ss[w][lane], rs.sc[w][lane]);
+            rs.acc[lane] = (double)s0 + (double)c0;
         } else if (lane < 2 * NMOM + 2) {
             long long t = 0;
             for (int w = 0; w < nw; ++w)
-                t += sn[w][lane - 2 * NMOM];
-            cnt_sh[lane - 2 * NMOM] = t;
+                t += rs.sn[w][lane - 2 * NMOM];
+            rs.cnt[lane - 2 * NMOM] = t;
         }
     }
     __syncthreads();
     if (threadIdx.x != 0)
         return;   // (the caller does not synchronise the block after this)
-    long long cnt[2] = {cnt_sh[0], cnt_sh[1]};
+    long long cnt[2] = {rs.cnt[0], rs.cnt[1]};
     // gated inliers if at least 3 pass the gate, else all inliers (set 0 + set 1)
     const bool gated = cnt[0] >= 3;
     const long long nsel = gated ? cnt[0] : cnt[0] + cnt[1];
     double S[NMOM];
     for (int k = 0; k < NMOM; ++k)
-        S[k] = gated ? acc_sh[k] : acc_sh[k] + acc_sh[NMOM + k];
+        S[k] = gated ? rs.acc[k] : rs.acc[k] + rs.acc[NMOM + k];
     const double nn = (double)nsel;
     const double mx = S[0] / nn, my = S[1] / nn, mz = S[2] / nn;
     double a[3][3], lmin, nv[3];
@@ -912,7 +1118,7 @@ __device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
     a[2][2] = S[8] / nn - mz * mz;
     smallest_eigenpair(a, lmin, nv);
     double n0 = nv[0], n1 = nv[1], n2 = nv[2];
-    const float4 p0 = st->p0;
+    const float4 p0 = st->rf_p0[slot];
     const double cx = (double)p0.x + mx, cy = (double)p0.y + my, cz = (double)p0.z + mz;
     double d = -(n0 * cx + n1 * cy + n2 * cz);
     if (d < 0.0) {
@@ -923,12 +1129,12 @@ __device__ void refit_frame(const RFrame &F, const RParams &prm, int round)
     out.n[1] = n1;
     out.n[2] = n2;
     out.d = d;
-    out.n_inliers = st->best_count;
+    out.n_inliers = st->rf_count[slot];
     out.n_refit = (int)nsel;
     out.rms = (float)sqrt(fmax(lmin, 0.0));
-    out.hyp_index = st->best_h;
+    out.hyp_index = st->rf_h[slot];
     st->n_planes += 1;
-    st->refit_pending = 0;
+    st->rf_pending[slot] = 0;
     if (round + 1 >= prm.max_planes)
         st->done = 1;
 }
@@ -1082,33 +1288,46 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
 // Large batches: selection and refit as their own launches, one block per
 // frame (fusing them costs every scoring / removal work item a fence that
 // waits for its atomics, which a batch with many work items per CTA feels).
-__global__ void __launch_bounds__(1024) k_select(RFrame *frames, RParams prm)
+__global__ void __launch_bounds__(1024) k_select(RFrame *frames, RParams prm, int round)
 {
     const RFrame &F = frames[blockIdx.x];
     if (F.st->done)
         return;
-    select_winner(F, prm);
+    select_winner(F, prm, round);
 }
 
-// Runs beside the next round's planning, which may already stop the frame:
-// it refits the frames whose selection accepted a winner this round.
+// The last round's refit (every earlier round's runs inside the next round's
+// scoring launch): the frames whose selection accepted a winner that round.
 __global__ void __launch_bounds__(REMOVE_THREADS) k_refit(RFrame *frames, RParams prm, int round)
 {
     const RFrame &F = frames[blockIdx.x];
-    if (!F.st->refit_pending)
+    __shared__ RefitShared rs;
+    if (!F.st->rf_pending[round & 1])
         return;
-    refit_frame(F, prm, round);
+    refit_frame(F, prm, round, rs);
 }
 
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+// The compaction of round `round` into round `next`'s list; with the
+// hypothesis fold, extra blocks draw round `next`'s hypotheses.
+static void launch_compact(const RansacLaunch &L, int round, bool src_image, int next,
+                           cudaStream_t s)
+{
+    const int cap = L.hyp_fold_chunks;
+    const int nhyp = cap > 0 ? L.n * ((L.prm.H + HYP_PER_BLOCK - 1) / HYP_PER_BLOCK) : 0;
+    const size_t smem = cap > 0 ? (size_t)(cap + 1) * sizeof(int) : 0;
+    k_compact<<<L.chunk_blocks + nhyp, COMPACT_THREADS, smem, s>>>(
+        L.d_frames, L.n, L.d_chunk_base, round, src_image, next, L.prm.min_inliers, L.d_counter,
+        L.prm, cap, L.chunk_blocks);
+}
+
 cudaError_t ransac_init(const RansacLaunch &L, cudaStream_t s)
 {
     k_plan0<<<1, 1024, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, L.d_counter);
     k_mark0<<<L.chunk_blocks, MARK_THREADS, 0, s>>>(L.d_frames, L.n, L.d_chunk_base);
-    k_compact<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, 0, true, 0,
-                                             L.prm.min_inliers, L.d_counter);
+    launch_compact(L, 0, true, 0, s);
     return cudaGetLastError();
 }
 
@@ -1116,7 +1335,7 @@ template <int HB, bool FUSE, bool INNER>
 static void launch_score(const RansacLaunch &L, int round, cudaStream_t s)
 {
     k_score<HB, FUSE, INNER><<<L.score_blocks, SCORE_THREADS, score_smem_bytes<HB>(), s>>>(
-        L.d_frames, L.n, L.d_chunk_base, L.prm, round);
+        L.d_frames, L.n, L.d_chunk_base, L.prm, round, L.d_counter + 1 + round);
 }
 
 template <int HB, bool FUSE, bool INNER>
@@ -1145,7 +1364,8 @@ cudaError_t score_init()
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_remove_ctas, k_remove,
                                                           REMOVE_THREADS, 0);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_compact_ctas, k_compact, 256, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_compact_ctas, k_compact, 256,
+                                                          (HYP_FOLD_MAX_CHUNKS + 1) * sizeof(int));
     return e;
 }
 
@@ -1164,48 +1384,30 @@ cudaError_t ransac_round(const RansacLaunch &L, int round, bool last, cudaStream
                          cudaEvent_t ev_before, cudaEvent_t ev_after)
 {
     const RParams &p = L.prm;
-    k_hyp<<<dim3((p.H + 127) / 128, L.n), 128, 0, s>>>(L.d_frames, p, round);
+    if (L.hyp_fold_chunks == 0)
+        k_hyp<<<dim3((p.H + 127) / 128, L.n), 128, 0, s>>>(L.d_frames, p, round);
     if (ev_before)
         record_event(ev_before, s);
     // coarse work items (512-hypothesis blocks, separate selection) when there
     // are enough chunks to fill the GPU; 256-hypothesis blocks with the
-    // selection folded into the scoring launch for small batches.  The
-    // selection overwrites the winner the previous round's refit reads, so it
-    // waits for that refit.
+    // selection folded into the scoring launch for small batches.  Either
+    // scoring launch also refits the previous round's winners.
     const bool fine = L.fine_score;
-    cudaError_t e = cudaSuccess;
-    if (fine) {
-        if (round > 0)
-            e = cudaStreamWaitEvent(s, L.ev_join, 0);
+    if (fine)
         launch_score<256, true, false>(L, round, s);
-    } else {
-        if (p.H <= 256)
-            launch_score<256, false, true>(L, round, s);
-        else
-            launch_score<512, false, true>(L, round, s);
-        if (round > 0)
-            e = cudaStreamWaitEvent(s, L.ev_join, 0);
-    }
-    if (e != cudaSuccess)
-        return e;
+    else if (p.H <= 256)
+        launch_score<256, false, true>(L, round, s);
+    else
+        launch_score<512, false, true>(L, round, s);
     if (ev_after)
         record_event(ev_after, s);
     if (!fine)
-        k_select<<<L.n, 1024, 0, s>>>(L.d_frames, p);
+        k_select<<<L.n, 1024, 0, s>>>(L.d_frames, p, round);
     k_remove<<<L.remove_blocks, REMOVE_THREADS, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, p, round);
-    // the refit runs beside the compaction (and the next round's hypotheses
-    // and scoring) on the side stream: nothing there reads its result
-    if ((e = cudaEventRecord(L.ev_fork, s)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(L.side, L.ev_fork, 0)) != cudaSuccess)
-        return e;
-    k_refit<<<L.n, REMOVE_THREADS, 0, L.side>>>(L.d_frames, p, round);
-    if ((e = cudaEventRecord(L.ev_join, L.side)) != cudaSuccess)
-        return e;
     if (!last)
-        k_compact<<<L.chunk_blocks, 256, 0, s>>>(L.d_frames, L.n, L.d_chunk_base, round, false,
-                                                 round + 1, p.min_inliers, L.d_counter);
-    else if ((e = cudaStreamWaitEvent(s, L.ev_join, 0)) != cudaSuccess)
-        return e;
+        launch_compact(L, round, false, round + 1, s);
+    else
+        k_refit<<<L.n, REMOVE_THREADS, 0, s>>>(L.d_frames, p, round);
     return cudaGetLastError();
 }
 

@@ -7,7 +7,7 @@ of the path runs in libpm's CUDA kernels; there is no CPU or PyTorch fallback.
 from __future__ import annotations
 
 import ctypes
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -120,7 +120,9 @@ class Pipeline:
 
     def __init__(self, params: Params = None, max_w: int = 640, max_h: int = 480,
                  max_frames: int = 1, lib_path: str = None):
-        self.p = params or Params()
+        # a copy: set_tiling changes this context's parameters, never those of
+        # another context built from the same Params
+        self.p = replace(params) if params is not None else Params()
         self.lib = _ffi.load(lib_path) if lib_path else _ffi.load()
         p = self.p
         self._dp = _ffi.DiffusionParams(p.iters, p.lam, p.K, p.mode, p.iters_per_launch,
