@@ -409,7 +409,9 @@ static void draw_indices(uint64_t seed, uint64_t frame_idx, int round, int hyp, 
  *   P, N: SoA [3][w*h] FP32 points and normals (N may be NULL: no refit gate).
  *   valid: bit 0 = point valid, bit 1 = normal valid.
  * Round r:
- *   candidates = valid points not yet labelled, in row-major order (M of them);
+ *   candidates = valid points not yet labelled (M of them), enumerated in
+ *     strips of two rows (rows 2s and 2s + 1; one row if h is odd and it is
+ *     the last), each strip column by column, the upper pixel first;
  *   hypothesis h < H: three Philox indices -> FP32 plane (hyp_plane_f32);
  *   count_h = #inliers (is_inlier_f32); degenerate hypotheses count -1;
  *   winner = maximum count, ties to the lowest h ("best model" of Alg. 2 with
@@ -451,9 +453,13 @@ int or_ransac(const float *P, const float *N, const unsigned char *valid, int w,
     int n_planes = 0;
     for (int r = 0; r < max_planes; ++r) {
         long M = 0;
-        for (long i = 0; i < n; ++i)
-            if ((valid[i] & 1) && labels[i] < 0)
-                cand[M++] = i;
+        for (int y0 = 0; y0 < h; y0 += 2)          /* strips of two rows */
+            for (int x = 0; x < w; ++x)              /* column by column */
+                for (int y = y0; y < y0 + 2 && y < h; ++y) {
+                    long i = (long)y * w + x;
+                    if ((valid[i] & 1) && labels[i] < 0)
+                        cand[M++] = i;
+                }
         for (int hh = 0; hh < H; ++hh) {
             counts[hh] = -1;
             if (M == 0)

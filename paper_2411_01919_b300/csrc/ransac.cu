@@ -74,6 +74,23 @@ __device__ __forceinline__ int frame_of(const int *__restrict__ base, int n, int
 // Chunks of a frame's largest candidate list (all its pixels).
 __device__ __forceinline__ int nchunks_of(const RFrame &F) { return (F.npx + CHUNK - 1) / CHUNK; }
 
+// Candidate order: the pixel at position `pos` of the enumeration in strips
+// of two rows (rows 2s, 2s + 1; one row when h is odd and the strip is the
+// last), each strip column by column, the upper pixel first.  A bijection of
+// [0, npx).  Thirty-two consecutive candidates then lie in a patch of about
+// 16 x 2 pixels instead of 32 x 1, whose 3-D box is tighter on the surfaces
+// of a depth image, so the scoring's box test settles more of their pairs.
+__device__ __forceinline__ int strip_pixel(const RFrame &F, int pos)
+{
+    const int s = pos / (2 * F.w);
+    const int y0 = 2 * s;
+    const int off = pos - y0 * F.w;
+    const bool two = y0 + 1 < F.h;
+    const int x = two ? off >> 1 : off;
+    const int y = y0 + (two ? off & 1 : 0);
+    return y * F.w + x;
+}
+
 // ---------------------------------------------------------------------------
 // round planning (run by one block of any size that is a multiple of 32)
 // ---------------------------------------------------------------------------
@@ -209,7 +226,7 @@ __device__ bool last_item_of_frame(int *counter, int items)
 }
 
 // ---------------------------------------------------------------------------
-// round 0 candidate list: valid pixels in row-major order
+// round 0 candidate list: valid pixels in the strip order of strip_pixel()
 // ---------------------------------------------------------------------------
 constexpr int MARK_THREADS = 256;
 
@@ -228,8 +245,8 @@ __global__ void __launch_bounds__(MARK_THREADS) k_mark0(RFrame *frames, int n,
         unsigned char vb[PER];
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
-            const int pix = base + threadIdx.x + u * MARK_THREADS;
-            vb[u] = pix < F.npx ? F.valid[pix] : 0;
+            const int pos = base + threadIdx.x + u * MARK_THREADS;
+            vb[u] = pos < F.npx ? F.valid[strip_pixel(F, pos)] : 0;
         }
         int kept = 0;
 #pragma unroll
@@ -290,9 +307,10 @@ __device__ void compact_chunk(const RFrame &F, int c, int nchunks, int src, int 
             if (!(PM_INB(j, npx) && PM_INB(pos, npx)))
                 continue;
             float4 pt;
-            if (src_image)
-                pt = make_float4(F.P[j], F.P[npx + j], F.P[2 * npx + j], __int_as_float((int)j));
-            else
+            if (src_image) {
+                const int q = strip_pixel(F, (int)j);
+                pt = make_float4(F.P[q], F.P[npx + q], F.P[2 * npx + q], __int_as_float(q));
+            } else
                 pt = F.cpt[src][j];
             F.cpt[dst][pos] = pt;
         }
@@ -446,8 +464,10 @@ __device__ float4 kept_candidate(const RFrame &F, const int *pre, int nc, bool s
     const long long npx = F.npx;
     if (!PM_INB(j, npx))
         return make_float4(0.f, 0.f, 0.f, 0.f);
-    if (src_image)
-        return make_float4(F.P[j], F.P[npx + j], F.P[2 * npx + j], __int_as_float((int)j));
+    if (src_image) {
+        const int q = strip_pixel(F, (int)j);
+        return make_float4(F.P[q], F.P[npx + q], F.P[2 * npx + q], __int_as_float(q));
+    }
     return F.cpt[src][j];
 }
 
@@ -638,15 +658,94 @@ __device__ void select_winner(const RFrame &F, const RParams &prm, int round)
 // ---------------------------------------------------------------------------
 constexpr int SEG = 32;
 constexpr int NSEG = CHUNK / SEG;
+constexpr int PSEG = 4;                  // segments per parent (a 128-candidate box)
+constexpr int NPAR = NSEG / PSEG;
 constexpr int SCORE_THREADS = 256;
 constexpr int SCORE_WARPS = SCORE_THREADS / 32;
 constexpr float CULL_SLACK = 0x1p-18f;
+static_assert(NPAR == SCORE_WARPS, "one parent per warp in the parent pass");
 
-template <int HB>
+// TWO: the two-level box test (parents' unsettled lists in shared memory).
+template <int HB, bool TWO>
 constexpr size_t score_smem_bytes()
 {
     return (size_t)CHUNK * 16 + (size_t)HB * 16 + (size_t)HB * 4 + (size_t)NSEG * 32 +
-           (size_t)HB * 4 + (size_t)SCORE_WARPS * HB * 2;
+           (size_t)NPAR * 32 + (size_t)HB * 4 + (size_t)SCORE_WARPS * HB * 2 +
+           (TWO ? (size_t)NPAR * HB * 2 : 0);
+}
+
+// The box [c - g, c + g] of candidates [b0, b0 + n) of the chunk (n >= 1),
+// written by lanes 0-2 (axis k by lane k) to out[0] (centre) and out[1]
+// (widened half-size): the centre, the half-size rounded up and widened by
+// the centre's rounding, then g = e + s (|c| + e) (the margin derived above).
+template <int PER>
+__device__ __forceinline__ void candidate_box(const float4 *pts, int b0, int n, float4 *out,
+                                              int lane)
+{
+    float lx = INFINITY, ly = INFINITY, lz = INFINITY;
+    float ux = -INFINITY, uy = -INFINITY, uz = -INFINITY;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const float4 p = pts[b0 + min(lane + 32 * i, n - 1)];
+        lx = fminf(lx, p.x); ly = fminf(ly, p.y); lz = fminf(lz, p.z);
+        ux = fmaxf(ux, p.x); uy = fmaxf(uy, p.y); uz = fmaxf(uz, p.z);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+        ux = fmaxf(ux, __shfl_xor_sync(0xffffffffu, ux, o));
+        uy = fmaxf(uy, __shfl_xor_sync(0xffffffffu, uy, o));
+        uz = fmaxf(uz, __shfl_xor_sync(0xffffffffu, uz, o));
+    }
+    if (lane < 3) {
+        const float lo = lane == 0 ? lx : lane == 1 ? ly : lz;
+        const float hi = lane == 0 ? ux : lane == 1 ? uy : uz;
+        const float cc = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+        const float e = __fadd_ru(__fmul_ru(__fsub_ru(hi, lo), 0.5f),
+                                  __fmul_ru(fabsf(cc), 0x1p-23f));
+        const float g = __fmaf_ru(CULL_SLACK, __fadd_ru(fabsf(cc), e), e);
+        float *b = reinterpret_cast<float *>(out);
+        b[lane] = cc;
+        b[4 + lane] = g;
+    }
+}
+
+// Box test of hypotheses against the box (bc, bg) of sc candidates, by one
+// warp: hypotheses whose slab holds the box add sc to their count; those the
+// test cannot settle are appended to `out`; returns their number.  LIST:
+// the hypotheses are in[0, nin); otherwise they are 0 .. nin - 1 (hpl and
+// hsd padded to a multiple of 32 with planes that are always culled).
+template <bool LIST>
+__device__ __forceinline__ int box_pass(const float4 *hpl, const float *hsd,
+                                        const unsigned short *in, int nin, float4 bc, float4 bg,
+                                        int sc, int *hcnt, unsigned short *out, float cull_thr,
+                                        float incl_thr, int lane)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    int len = 0;
+    for (int e = lane; e < nin + ((32 - (nin & 31)) & 31); e += 32) {
+        const bool live = !LIST || e < nin;
+        const int k = LIST ? (live ? (int)in[e] : 0) : e;
+        const float4 pl = hpl[k];
+        float t = __fmaf_rn(pl.x, bc.x, pl.w);
+        t = __fmaf_rn(pl.y, bc.y, t);
+        t = __fmaf_rn(pl.z, bc.z, t);
+        float a = __fmaf_rn(fabsf(pl.x), bg.x, hsd[k]);
+        a = __fmaf_rn(fabsf(pl.y), bg.y, a);
+        a = __fmaf_rn(fabsf(pl.z), bg.z, a);
+        const float at = fabsf(t);
+        const bool inc = live && __fadd_rn(at, a) < incl_thr;
+        if (inc)
+            atomicAdd(hcnt + k, sc);
+        const bool keep = live && !inc && !(__fsub_rn(at, a) > cull_thr);
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep)
+            out[len + __popc(m & lt)] = (unsigned short)k;
+        len += __popc(m);
+    }
+    return len;
 }
 
 // E surviving hypotheses per lane (list entries e0 + lane + 32 i) against the
@@ -716,7 +815,7 @@ struct RefitShared {
 
 static_assert(SCORE_THREADS == 32 * REFIT_WARPS && REMOVE_THREADS == 32 * REFIT_WARPS,
               "a refit runs in scoring and in removal-sized blocks");
-static_assert(sizeof(RefitShared) <= score_smem_bytes<256>(), "refit scratch fits the scoring smem");
+static_assert(sizeof(RefitShared) <= score_smem_bytes<256, false>(), "refit scratch fits the scoring smem");
 
 __device__ __noinline__ void refit_frame(const RFrame &F, const RParams &prm, int round, RefitShared &rs);
 
@@ -738,16 +837,19 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
     float4 *pts = sm;                  // [CHUNK] candidates of the chunk
     float4 *hpl = pts + CHUNK;         // [HB] planes (nx, ny, nz, d)
     float4 *box = hpl + HB;            // [NSEG][2] centre c; widened half-size g
-    float *hsd = reinterpret_cast<float *>(box + 2 * NSEG);              // [HB] s |d|
+    float4 *pbox = box + 2 * NSEG;     // [NPAR][2] the same for each parent
+    float *hsd = reinterpret_cast<float *>(pbox + 2 * NPAR);             // [HB] s |d|
     int *hcnt = reinterpret_cast<int *>(hsd + HB);                       // [HB]
     unsigned short *lst = reinterpret_cast<unsigned short *>(hcnt + HB);  // [warps][HB]
+    unsigned short *psurv = lst + SCORE_WARPS * HB;                       // [NPAR][HB]
+    __shared__ int plen[NPAR];
+    constexpr bool TWO = INNER;
     __shared__ int next_seg;
     __shared__ unsigned long long evaluated;
     const int nhb = (prm.H + HB - 1) / HB;
     const int per_chunk = INNER ? 1 : nhb;
     const int total = chunk_base[n] * per_chunk;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
     const float nthr2 = -prm.thr2;
     const float cull_thr = prm.cull_thr, incl_thr = prm.incl_thr;
     unsigned short *my = lst + wid * HB;
@@ -781,6 +883,7 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
         if (threadIdx.x == 0 && hb_first == 0 && PM_INB(c, nchunks_of(F)))
             F.kept[c] = 0;
         const int nseg = (cnt + SEG - 1) / SEG;
+        const int npar = (nseg + PSEG - 1) / PSEG;
         __syncthreads();
         for (int j = threadIdx.x; j < cnt; j += SCORE_THREADS)
             pts[j] = PM_INB(base + j, F.npx) ? src[j] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -807,31 +910,27 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
             }
             __syncthreads();
             if (hb == hb_first) {
-                for (int sg = wid; sg < nseg; sg += SCORE_WARPS) {
-                    const float4 p = pts[min(sg * SEG + lane, cnt - 1)];
-                    float lx = p.x, ly = p.y, lz = p.z, ux = p.x, uy = p.y, uz = p.z;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
-                        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
-                        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
-                        ux = fmaxf(ux, __shfl_xor_sync(0xffffffffu, ux, o));
-                        uy = fmaxf(uy, __shfl_xor_sync(0xffffffffu, uy, o));
-                        uz = fmaxf(uz, __shfl_xor_sync(0xffffffffu, uz, o));
-                    }
-                    if (lane < 3) {
-                        // lane k handles axis k: centre, half-size rounded up and
-                        // widened by the centre's rounding, then g = e + s (|c| + e)
-                        const float lo = lane == 0 ? lx : lane == 1 ? ly : lz;
-                        const float hi = lane == 0 ? ux : lane == 1 ? uy : uz;
-                        const float cc = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
-                        const float e = __fadd_ru(__fmul_ru(__fsub_ru(hi, lo), 0.5f),
-                                                  __fmul_ru(fabsf(cc), 0x1p-23f));
-                        const float g = __fmaf_ru(CULL_SLACK, __fadd_ru(fabsf(cc), e), e);
-                        float *b = reinterpret_cast<float *>(box + 2 * sg);
-                        b[lane] = cc;
-                        b[4 + lane] = g;
-                    }
+                for (int sg = wid; sg < nseg; sg += SCORE_WARPS)
+                    candidate_box<1>(pts, sg * SEG, min(SEG, cnt - sg * SEG), box + 2 * sg, lane);
+                for (int pg = wid; TWO && pg < npar; pg += SCORE_WARPS)
+                    candidate_box<PSEG>(pts, pg * PSEG * SEG, min(PSEG * SEG, cnt - pg * PSEG * SEG),
+                                        pbox + 2 * pg, lane);
+                __syncthreads();
+            }
+            // Two levels (large batches): each parent (PSEG segments) against
+            // every hypothesis; then each segment against its parent's unsettled
+            // hypotheses only.  A parent's box holds its segments' points, so a
+            // hypothesis that the parent's test settles has the same answer for
+            // every one of them.  (Small batches, whose items are short and
+            // latency-bound, test each segment against every hypothesis.)
+            if (TWO) {
+                for (int pg = wid; pg < npar; pg += SCORE_WARPS) {
+                    const int pc = min(PSEG * SEG, cnt - pg * PSEG * SEG);
+                    const int len = box_pass<false>(hpl, hsd, nullptr, nh, pbox[2 * pg],
+                                                    pbox[2 * pg + 1], pc, hcnt, psurv + pg * HB,
+                                                    cull_thr, incl_thr, lane);
+                    if (lane == 0)
+                        plen[pg] = len;
                 }
                 __syncthreads();
             }
@@ -843,27 +942,13 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score(RFrame *frames, int n,
                 sg = __shfl_sync(0xffffffffu, sg, 0);
                 if (sg >= nseg)
                     break;
-                const float4 bc = box[2 * sg], bg = box[2 * sg + 1];
+                const int pg = sg / PSEG;
                 const int sc = min(SEG, cnt - sg * SEG);
-                int len = 0;
-                for (int k = lane; k < nh + ((32 - (nh & 31)) & 31); k += 32) {
-                    const float4 pl = hpl[k];
-                    float t = __fmaf_rn(pl.x, bc.x, pl.w);
-                    t = __fmaf_rn(pl.y, bc.y, t);
-                    t = __fmaf_rn(pl.z, bc.z, t);
-                    float a = __fmaf_rn(fabsf(pl.x), bg.x, hsd[k]);
-                    a = __fmaf_rn(fabsf(pl.y), bg.y, a);
-                    a = __fmaf_rn(fabsf(pl.z), bg.z, a);
-                    const float at = fabsf(t);
-                    const bool inc = __fadd_rn(at, a) < incl_thr;
-                    if (inc)
-                        atomicAdd(hcnt + k, sc);
-                    const bool keep = !inc && !(__fsub_rn(at, a) > cull_thr);
-                    const unsigned m = __ballot_sync(0xffffffffu, keep);
-                    if (keep)
-                        my[len + __popc(m & lt)] = (unsigned short)k;
-                    len += __popc(m);
-                }
+                const int len =
+                    TWO ? box_pass<true>(hpl, hsd, psurv + pg * HB, plen[pg], box[2 * sg],
+                                         box[2 * sg + 1], sc, hcnt, my, cull_thr, incl_thr, lane)
+                        : box_pass<false>(hpl, hsd, nullptr, nh, box[2 * sg], box[2 * sg + 1], sc,
+                                          hcnt, my, cull_thr, incl_thr, lane);
                 __syncwarp();
                 mine += (unsigned long long)len * (unsigned)sc;
                 if (sc == SEG)
@@ -1334,7 +1419,7 @@ cudaError_t ransac_init(const RansacLaunch &L, cudaStream_t s)
 template <int HB, bool FUSE, bool INNER>
 static void launch_score(const RansacLaunch &L, int round, cudaStream_t s)
 {
-    k_score<HB, FUSE, INNER><<<L.score_blocks, SCORE_THREADS, score_smem_bytes<HB>(), s>>>(
+    k_score<HB, FUSE, INNER><<<L.score_blocks, SCORE_THREADS, score_smem_bytes<HB, INNER>(), s>>>(
         L.d_frames, L.n, L.d_chunk_base, L.prm, round, L.d_counter + 1 + round);
 }
 
@@ -1343,10 +1428,10 @@ static cudaError_t score_attr(int *ctas)
 {
     cudaError_t e = cudaFuncSetAttribute(k_score<HB, FUSE, INNER>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)score_smem_bytes<HB>());
+                                         (int)score_smem_bytes<HB, INNER>());
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_score<HB, FUSE, INNER>,
-                                                          SCORE_THREADS, score_smem_bytes<HB>());
+                                                          SCORE_THREADS, score_smem_bytes<HB, INNER>());
     return e;
 }
 

@@ -123,12 +123,30 @@ def surface_of(labels, k, plane_id):
     return int(np.bincount(g).argmax()) if g.size else -1
 
 
-def check_end_to_end(fr, gpu_planes, gpu_labels, orc, min_big=1000):
+def surface_map(labels, plane_id, n_planes):
+    """Per pixel, the ground-truth surface of the plane that labels it (the
+    surface most of that plane's labelled pixels lie on; -1 if unlabelled)."""
+    m = np.full(labels.shape, -1)
+    for k in range(n_planes):
+        m[labels == k] = surface_of(labels, k, plane_id)
+    return m
+
+
+def check_end_to_end(fr, gpu_planes, gpu_labels, orc, min_big=2000, min_agree=0.9):
     """Structural comparison with the oracle's own chain (no teacher forcing):
     the dominant first plane within tolerance, every oracle plane with at
-    least `min_big` inliers on a ground-truth surface the GPU also found, and
-    the labels agreeing on at least 95% of the pixels.  gpu_planes: Planes;
-    gpu_labels: int16 [h, w] numpy; orc: RansacResult."""
+    least `min_big` inliers on a ground-truth surface the GPU also found, and,
+    on the pixels both chains label, the ground-truth surface of the labelling
+    plane the same on at least `min_agree` of them.  gpu_planes: Planes;
+    gpu_labels: int16 [h, w] numpy; orc: RansacResult.  Returns that share.
+    The two chains draw from different candidate lists once a near-threshold
+    decision differs, so they find the surfaces in different rounds (label
+    values are not comparable) and small surfaces come and go: the 640x480
+    staircase's 1484-pixel landing edge gets 347 to 1851 inliers over five
+    seeds of the oracle alone, and some draws split it.  Between eight seeds
+    of the oracle the surface share is 0.958-0.990 on that frame (the band
+    where two surfaces meet goes to whichever is found first) and 1.0 on the
+    160x120 one."""
     assert len(gpu_planes.planes) >= 1 and len(orc.planes) >= 1
     g0, o0 = gpu_planes.planes[0], orc.planes[0]
     assert ang(g0[:3], o0[:3]) <= PLANE_DEG and abs(g0[3] - o0[3]) <= PLANE_OFF, (g0, o0)
@@ -137,6 +155,9 @@ def check_end_to_end(fr, gpu_planes, gpu_labels, orc, min_big=1000):
         if orc.n_inliers[k] >= min_big:
             s = surface_of(orc.labels, k, fr.plane_id)
             assert s in gpu_surf, ('oracle plane %d on surface %d not found' % (k, s))
-    agree = float((gpu_labels == orc.labels).mean())
-    assert agree >= 0.95, agree
+    mg = surface_map(gpu_labels, fr.plane_id, len(gpu_planes.planes))
+    mo = surface_map(orc.labels, fr.plane_id, len(orc.planes))
+    both = (mg >= 0) & (mo >= 0)
+    agree = float((mg[both] == mo[both]).mean())
+    assert agree >= min_agree, agree
     return agree

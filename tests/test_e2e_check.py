@@ -72,3 +72,32 @@ def test_planted_mistakes_fail(case):
     pl3.planes[1, 3] += 2e-3
     with pytest.raises(AssertionError):
         check_chain(res, pl3, labels)
+
+
+def test_structural_check_accepts_another_draw_and_rejects_wrong_structure():
+    """check_end_to_end (the extra, structural comparison) passes two oracle
+    runs whose draws differ, and fails a labelling that merges two surfaces
+    or misses one."""
+    from e2e_check import check_end_to_end
+    fr = synth.frame_c1(0)
+    runs = [oracle.process_frame(fr.encoded, fr.dtype, fr.cam.intrinsics, 10, f32(0.2),
+                                 f32(0.02), hypotheses=256, max_planes=4, min_inliers=100,
+                                 seed=s, frame_idx=0, depth_scale=f32(0.001)).ransac
+            for s in (11, 12)]
+    a, b = runs
+    assert not np.array_equal(a.hyp_index, b.hyp_index)
+    pb = Planes(b.planes, b.n_inliers, b.n_refit, b.rms, b.hyp_index)
+    assert check_end_to_end(fr, pb, b.labels, a, min_big=300) >= 0.9
+    # the pixels of the second plane relabelled as the first: two surfaces merged
+    merged = b.labels.copy()
+    merged[merged == 1] = 0
+    with pytest.raises(AssertionError):
+        check_end_to_end(fr, pb, merged, a, min_big=300)
+    # the second plane missing altogether
+    pmiss = Planes(b.planes[[0, 2, 3]], b.n_inliers[[0, 2, 3]], b.n_refit[[0, 2, 3]],
+                   b.rms[[0, 2, 3]], b.hyp_index[[0, 2, 3]])
+    missing = b.labels.copy()
+    missing[missing == 1] = -1
+    missing[missing >= 2] -= 1
+    with pytest.raises(AssertionError):
+        check_end_to_end(fr, pmiss, missing, a, min_big=300)

@@ -334,17 +334,18 @@ def test_ransac_without_normals_uses_all_inliers():
 
 
 def threshold_slab_scene(z0, half_w, thr, h=64, w=128):
-    """Points on the plane z = z0 (rows 0-39) and rows of points offset along
+    """Points on the plane z = z0 (rows 0-39) and pairs of rows offset along
     z by thr (1 -/+ 2^-22), above or below, just inside or just outside the
-    threshold: each row is four whole 32-point segments whose boxes lie at
-    the threshold distance from planes near z = z0."""
+    threshold: each two-row strip of the candidate order is eight whole
+    32-point segments (16 x 2 pixels) whose boxes lie at the threshold
+    distance from planes near z = z0."""
     xs = np.linspace(-half_w, half_w, w, dtype=np.float64)
     ys = np.linspace(-0.6 * half_w, 0.6 * half_w, h, dtype=np.float64)
     X, Y = np.meshgrid(xs, ys)
     Z = np.full((h, w), z0, dtype=np.float64)
     t32 = float(np.float32(thr))
     for v in range(40, h):
-        k = v - 40
+        k = (v - 40) // 2                          # the strip
         sign = 1.0 if k % 2 == 0 else -1.0          # above / below the plane
         rel = (1.0 - 2.0 ** -22) if (k // 2) % 2 == 0 else (1.0 + 2.0 ** -22)
         Z[v, :] = z0 + sign * t32 * rel
@@ -361,7 +362,8 @@ def test_box_culling_keeps_threshold_inliers(z0, half_w):
     thr = 0.01
     P, V = threshold_slab_scene(z0, half_w, thr)
     h, w = V.shape
-    p = Params(iters=0, hypotheses=512, thr=thr, max_planes=2, min_inliers=50, seed=4)
+    # seed: one whose winning hypotheses have points at the threshold in both scenes
+    p = Params(iters=0, hypotheses=512, thr=thr, max_planes=2, min_inliers=50, seed=50)
     orc = oracle.ransac(P, None, V, p.hypotheses, p.thr, p.max_planes, p.min_inliers, p.seed,
                         p.gate_deg, 0)
     with Pipeline(p, w, h) as pipe:
@@ -432,8 +434,8 @@ def test_process_frame_matches_oracle(name):
                                    min_inliers=p.min_inliers, seed=p.seed, frame_idx=0,
                                    depth_scale=SCALE)
         agree = check_end_to_end(fr, g, lab.cpu().numpy(), res.ransac,
-                                 min_big=300 if name == 'c1' else 1000)
-        print('%s: own-chain oracle %d planes, label agreement %.5f'
+                                 min_big=300 if name == 'c1' else 2000)
+        print('%s: own-chain oracle %d planes, surface agreement %.5f'
               % (name, len(res.ransac.planes), agree))
     assert np.array_equal(single.planes, g.planes)
     assert np.array_equal(single.labels.cpu().numpy(), lab.cpu().numpy())

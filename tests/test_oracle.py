@@ -271,6 +271,22 @@ def _tiny_scene(seed, w=6, h=5):
     return P.reshape(3, h, w).astype(np.float32), valid.reshape(h, w)
 
 
+def _strip_candidates(valid):
+    """Flat indices of the valid pixels in the candidate order of the RANSAC
+    rounds: two-row strips top to bottom, each strip column by column, the
+    upper pixel of a column first (one row in the last strip of an odd height)."""
+    h, w = valid.shape
+    ys, xs = np.mgrid[0:h, 0:w]
+    order = np.lexsort((ys.ravel(), xs.ravel(), ys.ravel() // 2))
+    return order[(valid.reshape(-1)[order] & 1) > 0]
+
+
+def test_strip_candidate_order_small_frame():
+    # 3 x 3 frame, all valid: strip 0 = rows 0-1 column by column, strip 1 = row 2
+    order = _strip_candidates(np.ones((3, 3), np.uint8))
+    assert order.tolist() == [0, 3, 1, 4, 2, 5, 6, 7, 8]
+
+
 def _indices_numpy(seed, frame_idx, r, hyp, M):
     w = _numpy_philox_block(np.array([hyp, r, frame_idx, 0], dtype=np.uint64), [seed, 0])
     return [(int(x) * M) >> 64 for x in w[:3]]
@@ -287,7 +303,7 @@ def test_ransac_brute_force_tiny(seed):
     H, thr, seed_rng, frame = 64, 0.01, 1234 + seed, 7
     r = oracle.ransac(P, None, valid, H, thr, 1, 1, seed_rng, 20.0, frame)
     Pf = P.reshape(3, -1).astype(np.float64)
-    cand = np.flatnonzero(valid.reshape(-1) & 1)
+    cand = _strip_candidates(valid)
     M = len(cand)
     Pc = Pf[:, cand]
     checked = 0
