@@ -1312,9 +1312,11 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
                     vh[k] = 0.0f;
                     vl[k] = 0.0f;
                 }
+                bool gated[PER_THREAD];
+                int ng = 0, no = 0;
 #pragma unroll
                 for (int u = 0; u < PER_THREAD; ++u) {
-                    bool gated = false;
+                    gated[u] = false;
                     if (inl[u]) {
                         F.labels[pix[u]] = (short)round;
                         if (vb[u] & 2) {
@@ -1322,14 +1324,32 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
                             const float dot = __fmaf_rn(nrm[u].z, pl.z,
                                                         __fmaf_rn(nrm[u].y, pl.y,
                                                                   __fmul_rn(nrm[u].x, pl.x)));
-                            gated = fabsf(dot) >= prm.cos_gate;
+                            gated[u] = fabsf(dot) >= prm.cos_gate;
                         }
                     }
-                    cnt_g += __popc(__ballot_sync(0xffffffffu, inl[u] && gated));
-                    cnt_o += __popc(__ballot_sync(0xffffffffu, inl[u] && !gated));
-                    if (inl[u])
-                        mom_values(vh, vl, gated ? 0 : NMOM, __fsub_rn(p[u].x, p0.x),
-                                   __fsub_rn(p[u].y, p0.y), __fsub_rn(p[u].z, p0.z));
+                    const int g = __popc(__ballot_sync(0xffffffffu, inl[u] && gated[u]));
+                    const int o = __popc(__ballot_sync(0xffffffffu, inl[u] && !gated[u]));
+                    ng += g;
+                    no += o;
+                }
+                cnt_g += ng;
+                cnt_o += no;
+                // each set's sums in a pass of its own, skipped by a warp with no
+                // candidate in it: the register set a value goes to is then fixed
+                // at compile time, not chosen per lane
+                if (ng) {
+#pragma unroll
+                    for (int u = 0; u < PER_THREAD; ++u)
+                        if (inl[u] && gated[u])
+                            mom_values(vh, vl, 0, __fsub_rn(p[u].x, p0.x),
+                                       __fsub_rn(p[u].y, p0.y), __fsub_rn(p[u].z, p0.z));
+                }
+                if (no) {
+#pragma unroll
+                    for (int u = 0; u < PER_THREAD; ++u)
+                        if (inl[u] && !gated[u])
+                            mom_values(vh, vl, NMOM, __fsub_rn(p[u].x, p0.x),
+                                       __fsub_rn(p[u].y, p0.y), __fsub_rn(p[u].z, p0.z));
                 }
                 float th, tl;
                 warp_transpose_sum(vh, vl, lane, th, tl);
