@@ -40,6 +40,17 @@ FP32_FLOP_PER_PAIR = 8          # 3 FMA residual + 1 FMA squared-threshold test
 SCORE_DRAM_BYTES_PER_PAIR = (152.75e6 + 3.11e6) / 9.73e9   # ncu, k_score round 0, 32 frames
 SEGMENT, BOX_TEST_FLOP = 32, 14   # box test: 6 FFMA + 2 FADD
 N_SETS = 4                      # device copies of the batch the timed steps cycle through
+
+
+def shared_config(batch):
+    """The workload both arms measure (the same dict in both JSON lines);
+    what each arm runs it on goes in its own top-level keys."""
+    mb = N_SETS * batch * 640 * 480 * 2 / 1e6
+    return {'workload': WORKLOAD, 'batch_per_gpu': batch,
+            'l2': 'inputs larger than L2: the steps cycle through %d copies of the batch '
+                  '(%.0f MB > 126 MB L2)' % (N_SETS, mb),
+            'parallelism': 'frames sharded across ranks, no collective (the oracle arm: rank 0 '
+                           'alone)'}
 REGION_FLOP_PER_PAIR = 9     # 3 FMA residual, |r| x 2^32, 1 FMA inlier test
 FP32_LANES = 128              # FP32 lanes per SM (the derived peak printed beside the measured one)
 
@@ -209,10 +220,9 @@ def run_reference(args):
             'n_gpus': world, 'steps': args.steps, 'warmup': args.warmup,
             'ms_per_step': 1e3 * tot / args.steps, 'higher_is_better': True, 'scaling': 'weak',
             'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-            'config': {'workload': WORKLOAD, 'batch_per_gpu': args.batch,
-                       'form': 'FP64 CPU oracle; each step times one frame of the batch (a '
-                               'bounded sample), frames/s from those frames',
-                       'parallelism': 'one host core'},
+            'config': shared_config(args.batch),
+            'form': 'FP64 CPU oracle on one host core; each step times one frame of the batch '
+                    '(a bounded sample), frames/s from those frames',
             'cpu_baseline': {'value': value, 'unit': 'frames/s', 'cores': 1, 'kind': 'oracle',
                              'sample': sample},
             'e2e': {'value': value, 'unit': 'frames/s', 'h2d_bytes_per_step': 0,
@@ -906,15 +916,11 @@ def run_ours(args):
             'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': tot_ms / args.steps,
             'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32',
             'data': 'synthetic',
-            'config': {'workload': WORKLOAD, 'batch_per_gpu': B,
-                       'form': 'batched, CUDA graph; %d lanes take the steps in turn through '
-                               'the asynchronous batch API' % NL,
-                       'l2': 'steps cycle through %d device copies of the batch (%.0f MB > 126 MB '
-                             'L2)' % (N_SETS, N_SETS * sum(d.numel() * d.element_size()
-                                                           for d in dframes) / 1e6),
-                       'parallelism': 'frames sharded across GPUs, no collective',
-                       'diffusion_tiling': (dict(zip(('iters_per_launch', 'tile_w', 'tile_h'),
-                                                     tuned['best'])) if tuned else 'library default')},
+            'config': shared_config(B),
+            'form': 'batched, CUDA graph; %d lanes take the steps in turn through the '
+                    'asynchronous batch API; the batch in %d device copies' % (NL, N_SETS),
+            'diffusion_tiling': (dict(zip(('iters_per_launch', 'tile_w', 'tile_h'), tuned['best']))
+                                 if tuned else 'library default'),
             'latency_ms': {'p50': percentile(step_ms, 50), 'p99': percentile(step_ms, 99),
                            'note': 'submit to collect of a step (%d steps in flight); a batched '
                                    'frame completes with its step' % NL},

@@ -25,6 +25,10 @@ def test_reference_arm_prints_one_contract_line():
     assert d['value'] > 0 and abs(d['ms_per_step'] - 1e3 / d['value']) < 1e-6 * d['ms_per_step']
     assert d['data'] == 'synthetic' and d['vs_baseline'] is None
     assert 'workload' in d['config']
+    # the same workload dict as the GPU arm's line
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d['config'] == bench.shared_config(d['config']['batch_per_gpu'])
     cb = d['cpu_baseline']
     assert cb['kind'] == 'oracle' and cb['cores'] >= 1 and cb['value'] == d['value']
     assert isinstance(cb['sample'], str) and cb['sample']
