@@ -71,6 +71,22 @@ __device__ __forceinline__ int frame_of(const int *__restrict__ base, int n, int
     return lo;
 }
 
+// The batch's chunk prefix (chunk_base, n + 1 entries) staged in shared
+// memory by the whole block when it fits, so that finding a work item's frame
+// (a binary search) costs shared-memory loads instead of a chain of dependent
+// global loads; larger batches search the global table.
+constexpr int BASE_SMEM = 256;
+
+__device__ __forceinline__ const int *stage_base(const int *chunk_base, int n, int *sb)
+{
+    if (n + 1 > BASE_SMEM)
+        return chunk_base;
+    for (int i = threadIdx.x; i <= n; i += blockDim.x)
+        sb[i] = chunk_base[i];
+    __syncthreads();
+    return sb;
+}
+
 // Chunks of a frame's largest candidate list (all its pixels).
 __device__ __forceinline__ int nchunks_of(const RFrame &F) { return (F.npx + CHUNK - 1) / CHUNK; }
 
@@ -234,12 +250,14 @@ __global__ void __launch_bounds__(MARK_THREADS) k_mark0(RFrame *frames, int n,
                                                         const int *chunk_base)
 {
     __shared__ int wsum[MARK_THREADS / 32];
+    __shared__ int sbase[BASE_SMEM];
     constexpr int PER = CHUNK / MARK_THREADS;
-    const int total = chunk_base[n];
+    const int *cb = stage_base(chunk_base, n, sbase);
+    const int total = cb[n];
     for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
-        const int f = frame_of(chunk_base, n, wi);
+        const int f = frame_of(cb, n, wi);
         const RFrame &F = frames[f];
-        const int c = wi - chunk_base[f];
+        const int c = wi - cb[f];
         const int base = c * CHUNK;
         // the thread's PER pixels loaded together, then marked
         unsigned char vb[PER];
@@ -521,16 +539,18 @@ __device__ void hyp_block(const RFrame &F, const RParams &prm, int next, int hb,
 __device__ void compact_run(RFrame *frames, int n, const int *chunk_base, int src, int dst,
                             bool src_image, int b, int nb)
 {
-    const int total = chunk_base[n];
+    __shared__ int sbase[BASE_SMEM];
+    const int *cb = stage_base(chunk_base, n, sbase);
+    const int total = cb[n];
     const int per = (total + nb - 1) / nb;
     const int w0 = b * per, w1 = min(total, w0 + per);
     int cur_f = -1, off = 0;
     for (int wi = w0; wi < w1; ++wi) {
-        const int f = frame_of(chunk_base, n, wi);
+        const int f = frame_of(cb, n, wi);
         const RFrame &F = frames[f];
         if (F.st->done)
             continue;
-        const int c = wi - chunk_base[f];
+        const int c = wi - cb[f];
         if (f != cur_f) {
             off = kept_before(F, c);
             cur_f = f;
@@ -1237,12 +1257,14 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
 {
     __shared__ float sh_s[8][2 * NMOM], sh_c[8][2 * NMOM];
     __shared__ int sh_n[8][2];
-    const int total = chunk_base[n];
+    __shared__ int sbase[BASE_SMEM];
+    const int *cb = stage_base(chunk_base, n, sbase);
+    const int total = cb[n];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nwarps = REMOVE_THREADS >> 5;
     for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
-        const int f = frame_of(chunk_base, n, wi);
-        const int c0 = wi - chunk_base[f];
+        const int f = frame_of(cb, n, wi);
+        const int c0 = wi - cb[f];
         if (c0 % GROUP)
             continue;
         const RFrame &F = frames[f];
