@@ -637,8 +637,9 @@ __device__ void select_winner(const RFrame &F, const RParams &prm, int round)
 // scoring with exact box culling and inclusion.
 //
 // A work item is (frame, chunk of CHUNK candidates, block of HB hypotheses).
-// The chunk is cut into segments of SEG consecutive candidates (a few pixels
-// of one image row, so a small patch of one surface); each segment gets an
+// The chunk is cut into segments of SEG consecutive candidates (in the strip
+// order, a patch of about 16 x 2 pixels, so a small patch of one surface);
+// large batches also into parents of PSEG segments; each segment gets an
 // axis-aligned box [c - e, c + e] that holds its points.  A hypothesis whose
 // plane stays farther than the threshold from the whole box, by a margin that
 // covers every rounding of the FP32 residual and of the test, has no inlier
