@@ -293,6 +293,43 @@ def diffusion_hbm(torch, pm, dev, pk, side=8192, iters=10, reps=5, dtype='u16'):
             'frac': gbs / pk['hbm_gbs'], 'moved_gbs': mgbs, 'moved_frac': mgbs / pk['hbm_gbs']}
 
 
+def normals_hbm(torch, pm, dev, pk, side=8192, reps=5):
+    """Back-projection and normals (pm_normals) on a side x side FP32 depth
+    image with 2% holes, outputs preallocated.  Algorithmic bytes per pixel:
+    the depth read once (4 B; the stencil's neighbours come from cache) and
+    the points, normals and validity written (12 + 12 + 1 B).  The working set
+    (about 1.9 GB at 8192^2) is >= 15x L2."""
+    g = torch.Generator(device=dev).manual_seed(2)
+    z = 1.0 + 2.0 * torch.rand((side, side), generator=g, device=dev)
+    z[torch.rand((side, side), generator=g, device=dev) < 0.02] = 0.0
+    out = (torch.empty((3, side, side), dtype=torch.float32, device=dev),
+           torch.empty((3, side, side), dtype=torch.float32, device=dev),
+           torch.empty((side, side), dtype=torch.uint8, device=dev))
+    K = (0.6 * side, 0.6 * side, side / 2.0, side / 2.0)
+    pipe = pm.Pipeline(pm.Params(iters=1), side, side, 1)
+    s = torch.cuda.current_stream()
+    for _ in range(2):
+        pipe.normals(z, K, out=out)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        pipe.normals(z, K, out=out)
+        b.record(s)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    pipe.close()
+    ms = statistics.median(ts)
+    alg = float(side) * side * 29.0
+    gbs = alg / (ms * 1e-3) / 1e9
+    return {'kernel': 'k_normals via pm_normals (back-projection, normals, validity)',
+            'image': '%dx%d f32' % (side, side), 'algorithmic_bytes_per_call': alg,
+            'algorithmic_bytes': 'px x 29: depth read (4 B), points + normals + validity written '
+                                 '(12 + 12 + 1 B)',
+            'ms': ms, 'achieved': gbs, 'peak': pk['hbm_gbs'], 'unit': 'GB/s',
+            'frac': gbs / pk['hbm_gbs']}
+
+
 def run_regions(torch, pm, pipe, frames, dframes, fp32_peak, n_frames=8, H=256, reps=3):
     """The step after the path, all on the GPU: Canny edges of the normal image,
     the regions they bound, and per-region RANSAC (one model per region) on
@@ -889,6 +926,7 @@ def run_ours(args):
     hbm = diffusion_hbm(torch, pm, dev, pk) if not args.skip_hbm else None
     hbm_f32 = (diffusion_hbm(torch, pm, dev, pk, dtype='f32', reps=3)
                if not args.skip_hbm else None)
+    nrm_hbm = normals_hbm(torch, pm, dev, pk) if not args.skip_hbm else None
     regions = (run_regions(torch, pm, pipe, frames, dframes, peak_tflops)
                if not args.skip_regions else None)
     forms = run_forms(torch, pm, dev, peak_tflops, flush) if not args.skip_forms else None
@@ -929,6 +967,7 @@ def run_ours(args):
                                          if served else None),
             'served': served, 'regions': regions, 'sweep': sweep,
             'e2e': e2e, 'roofline': roof, 'diffusion_hbm': hbm, 'diffusion_hbm_f32': hbm_f32,
+            'normals_hbm': nrm_hbm,
             'diffusion_fused': fused, 'forms': forms,
             'measured_peaks': dict(meas, how='pm_measure_peaks: FFMA-only and ex2-only kernels on '
                                              'every SM, CUDA events, device clocks as found'),

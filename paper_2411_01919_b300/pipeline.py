@@ -166,13 +166,23 @@ class Pipeline:
                                   _dev(out, 'out'), _stream_ptr(stream)))
         return out
 
-    def normals(self, depth: torch.Tensor, K, stream=None):
+    def normals(self, depth: torch.Tensor, K, stream=None, out=None):
+        """Points, normals and validity of an FP32 depth image; `out` = (P, N, V)
+        to write into given tensors (float32 [3, h, w] twice, uint8 [h, w])."""
         if depth.dtype != torch.float32 or not depth.is_contiguous() or depth.dim() != 2:
             raise ValueError('depth must be a contiguous float32 [h, w] tensor')
         h, w = depth.shape
-        P = torch.empty((3, h, w), dtype=torch.float32, device=depth.device)
-        N = torch.empty((3, h, w), dtype=torch.float32, device=depth.device)
-        V = torch.empty((h, w), dtype=torch.uint8, device=depth.device)
+        if out is not None:
+            P, N, V = out
+            for t, shape, dt in ((P, (3, h, w), torch.float32), (N, (3, h, w), torch.float32),
+                                 (V, (h, w), torch.uint8)):
+                if tuple(t.shape) != shape or t.dtype != dt or not t.is_contiguous():
+                    raise ValueError('out tensors must be contiguous float32 [3, h, w] x 2 '
+                                     'and uint8 [h, w]')
+        else:
+            P = torch.empty((3, h, w), dtype=torch.float32, device=depth.device)
+            N = torch.empty((3, h, w), dtype=torch.float32, device=depth.device)
+            V = torch.empty((h, w), dtype=torch.uint8, device=depth.device)
         k = _intr(K)
         check(self.lib.pm_normals(self._h, _dev(depth, 'depth'), w, h, ctypes.byref(k),
                                   _dev(P, 'P'), _dev(N, 'N'), _dev(V, 'V'), _stream_ptr(stream)))
