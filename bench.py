@@ -990,6 +990,7 @@ def run_case(args):
     named by --case on the given image / batch, `--steps` calls after
     `--warmup` calls.
       stream-u16 / stream-f32: 8192 x 8192 depth, 4 iterations, one per launch
+      normals-f32: pm_normals on an 8192 x 8192 FP32 depth image
       tiles-640x480x64: the fused diffusion of the 64-frame 640x480 batch
       path-640x480x32: the whole path over 32 frames of the 640x480 workload"""
     import torch
@@ -997,6 +998,20 @@ def run_case(args):
     import synth
     dev = torch.device('cuda', 0)
     torch.cuda.set_device(0)
+    if args.case == 'normals-f32':
+        side = 8192
+        g = torch.Generator(device=dev).manual_seed(2)
+        z = 1.0 + 2.0 * torch.rand((side, side), generator=g, device=dev)
+        z[torch.rand((side, side), generator=g, device=dev) < 0.02] = 0.0
+        out = (torch.empty((3, side, side), dtype=torch.float32, device=dev),
+               torch.empty((3, side, side), dtype=torch.float32, device=dev),
+               torch.empty((side, side), dtype=torch.uint8, device=dev))
+        K = (0.6 * side, 0.6 * side, side / 2.0, side / 2.0)
+        with pm.Pipeline(pm.Params(iters=1), side, side, 1) as pipe:
+            for _ in range(args.warmup + args.steps):
+                pipe.normals(z, K, out=out)
+            torch.cuda.synchronize()
+        return 0
     if args.case.startswith('stream-'):
         side = 8192
         g = torch.Generator(device=dev).manual_seed(1)
@@ -1047,7 +1062,7 @@ def main():
                     help='diffusion tiling T,tile_w,tile_h instead of autotuning (e.g. 8,80,48)')
     ap.add_argument('--served-seconds', type=float, default=60.0)
     ap.add_argument('--case', default='',
-                    choices=['', 'stream-u16', 'stream-f32', 'tiles-640x480x64',
+                    choices=['', 'stream-u16', 'stream-f32', 'normals-f32', 'tiles-640x480x64',
                              'path-640x480x32'],
                     help='run one small workload for a profiler capture instead of the benchmark')
     args = ap.parse_args()

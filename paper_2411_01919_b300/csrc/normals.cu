@@ -7,10 +7,13 @@
 // differences of back-projected points (central, or Sobel-weighted (1,2,1)),
 // oriented towards the camera.  One thread per 4 pixels of a row (16-byte
 // loads of the depth rows, 16-byte stores of the outputs).  Outputs SoA
-// points and normals and a validity byte (bit 0 point, bit 1 normal).  Back-projection multiplies by 1/fx and 1/fy (rounded once
-// from FP64) instead of dividing: a few FP32 ulps on the points, no division
-// in the per-pixel work.  The same constant factor on every pixel changes
-// normal directions by about 1e-7 rad.
+// points and normals and a validity byte (bit 0 point, bit 1 normal).
+// Back-projection multiplies by 1/fx and 1/fy (rounded once from FP64)
+// instead of dividing: a few FP32 ulps on the points, no division in the
+// per-pixel work; the factors (u - cx) / fx and (v - cy) / fy are formed once
+// per column and row of a thread's window.  The same constant factor on every
+// pixel changes normal directions by about 1e-7 rad; so does normalising with
+// the hardware reciprocal square root (rsqrtf) instead of 1 / sqrt.
 #define PM_FILE_ID 2
 #include "pm_internal.cuh"
 
@@ -25,23 +28,23 @@ __device__ __forceinline__ bool depth_ok(float z)
     return z > 0.0f && z < __int_as_float(0x7f800000);
 }
 
-__device__ __forceinline__ float3 backproject(float z, int u, int v, const Cam &k)
-{
-    float xt = __fmul_rn(__fsub_rn((float)u, k.cx), k.ifx);
-    float yt = __fmul_rn(__fsub_rn((float)v, k.cy), k.ify);
-    return make_float3(__fmul_rn(z, xt), __fmul_rn(z, yt), z);
-}
-
 // The normal of pixel (u, v) from its 3x3 depth neighbourhood z[dv + 1][du + 1]
 // (central differences read the four edge neighbours, Sobel all eight; the
 // others are ignored): point Pp, unit normal n (0 if invalid), validity byte.
+// xt[c] / yt[r]: the back-projection factors (u - cx) / fx of columns u - 1 ..
+// u + 1 and (v - cy) / fy of rows v - 1 .. v + 1 (bp() multiplies by them).
+__device__ __forceinline__ float3 bp(float z, float xt, float yt)
+{
+    return make_float3(__fmul_rn(z, xt), __fmul_rn(z, yt), z);
+}
+
 template <int STENCIL>
-__device__ __forceinline__ void normal_core(const float (&z)[3][3], int u, int v, int w, int h,
-                                            const Cam &k, float3 &Pp, float3 &n,
-                                            unsigned char &vb)
+__device__ __forceinline__ void normal_core(const float (&z)[3][3], const float *xt,
+                                            const float *yt, int u, int v, int w, int h,
+                                            float3 &Pp, float3 &n, unsigned char &vb)
 {
     const bool ok = depth_ok(z[1][1]);
-    Pp = ok ? backproject(z[1][1], u, v, k) : make_float3(0.f, 0.f, 0.f);
+    Pp = ok ? bp(z[1][1], xt[1], yt[1]) : make_float3(0.f, 0.f, 0.f);
     vb = ok ? 1 : 0;
     n = make_float3(0.f, 0.f, 0.f);
     if (!(ok && u > 0 && v > 0 && u < w - 1 && v < h - 1))
@@ -51,8 +54,8 @@ __device__ __forceinline__ void normal_core(const float (&z)[3][3], int u, int v
     if (STENCIL == 0) {
         const float ze = z[1][2], zw = z[1][0], zs = z[2][1], zn = z[0][1];
         all = depth_ok(ze) && depth_ok(zw) && depth_ok(zs) && depth_ok(zn);
-        float3 a = backproject(ze, u + 1, v, k), b = backproject(zw, u - 1, v, k);
-        float3 c = backproject(zs, u, v + 1, k), d = backproject(zn, u, v - 1, k);
+        float3 a = bp(ze, xt[2], yt[1]), b = bp(zw, xt[0], yt[1]);
+        float3 c = bp(zs, xt[1], yt[2]), d = bp(zn, xt[1], yt[0]);
         tu = make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
         tv = make_float3(c.x - d.x, c.y - d.y, c.z - d.z);
     } else {
@@ -62,8 +65,8 @@ __device__ __forceinline__ void normal_core(const float (&z)[3][3], int u, int v
             const float zr1 = z[1 + j][2], zr0 = z[1 + j][0];
             const float zc1 = z[2][1 + j], zc0 = z[0][1 + j];
             all = all && depth_ok(zr1) && depth_ok(zr0) && depth_ok(zc1) && depth_ok(zc0);
-            float3 a = backproject(zr1, u + 1, v + j, k), b = backproject(zr0, u - 1, v + j, k);
-            float3 c = backproject(zc1, u + j, v + 1, k), d = backproject(zc0, u + j, v - 1, k);
+            float3 a = bp(zr1, xt[2], yt[1 + j]), b = bp(zr0, xt[0], yt[1 + j]);
+            float3 c = bp(zc1, xt[1 + j], yt[2]), d = bp(zc0, xt[1 + j], yt[0]);
             tu.x += wt * (a.x - b.x); tu.y += wt * (a.y - b.y); tu.z += wt * (a.z - b.z);
             tv.x += wt * (c.x - d.x); tv.y += wt * (c.y - d.y); tv.z += wt * (c.z - d.z);
         }
@@ -74,7 +77,7 @@ __device__ __forceinline__ void normal_core(const float (&z)[3][3], int u, int v
         float cz = tu.x * tv.y - tu.y * tv.x;
         float l2 = cx * cx + cy * cy + cz * cz;
         if (l2 > 0.0f && l2 < __int_as_float(0x7f800000)) {
-            float inv = 1.0f / sqrtf(l2);
+            const float inv = rsqrtf(l2);
             n = make_float3(cx * inv, cy * inv, cz * inv);
             if (n.x * Pp.x + n.y * Pp.y + n.z * Pp.z > 0.0f)
                 n = make_float3(-n.x, -n.y, -n.z);
@@ -128,6 +131,14 @@ __device__ __forceinline__ void normals4(const float *__restrict__ depth, int w,
             }
         }
     }
+    // the back-projection factors of the 6 columns and 3 rows, once
+    float xt6[6], yt3[3];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+        xt6[c] = __fmul_rn(__fsub_rn((float)(u0 - 1 + c), k.cx), k.ifx);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        yt3[i] = __fmul_rn(__fsub_rn((float)(v - 1 + i), k.cy), k.ify);
     float3 Pp[4], n[4];
     unsigned char vb[4];
 #pragma unroll
@@ -138,7 +149,7 @@ __device__ __forceinline__ void normals4(const float *__restrict__ depth, int w,
 #pragma unroll
             for (int j = 0; j < 3; ++j)
                 z[i][j] = r[i][q + j];
-        normal_core<STENCIL>(z, u0 + q, v, w, h, k, Pp[q], n[q], vb[q]);
+        normal_core<STENCIL>(z, xt6 + q, yt3, u0 + q, v, w, h, Pp[q], n[q], vb[q]);
     }
     const long long p = (long long)v * w + u0;
     if (vec) {

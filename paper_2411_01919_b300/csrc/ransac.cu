@@ -1035,7 +1035,7 @@ __device__ __forceinline__ void df_merge(float &h, float &l, float h2, float l2)
 // (H, L)[off ..]: no rounding error is dropped, so the covariance
 // E[xx] - E[x]^2 of a thin cluster of inliers far from the moment origin,
 // where the two terms nearly cancel, keeps its precision.
-__device__ __forceinline__ void mom_values(float (&H)[32], float (&L)[32], int off, float x,
+__device__ __forceinline__ void mom_values(float (&H)[2 * NMOM], float (&L)[2 * NMOM], int off, float x,
                                            float y, float z)
 {
     const float a[6] = {x, x, x, y, y, z}, b[6] = {x, y, z, y, z, z};
@@ -1058,30 +1058,63 @@ __device__ __forceinline__ void mom_values(float (&H)[32], float (&L)[32], int o
     }
 }
 
-// Sum over the warp of every one of a lane's 32 double-float values,
-// transposed: lane l returns in (h, l_out) the sum of the lanes' (H[l], L[l]).
-// Five butterfly steps; at the step of offset o each lane keeps the half of
-// its live values selected by its bit o and adds the partner's copy of that
-// half (62 shuffles in all).  The order of the additions is fixed by the
-// lane, not by the data.
-__device__ __forceinline__ void warp_transpose_sum(float (&H)[32], float (&L)[32], int lane,
-                                                   float &h, float &l_out)
+// One halving step of warp_reduce18 at lane offset o: S slots out of 2 S
+// (slots at or beyond n hold zeros), the lane keeping the half its bit o
+// selects and adding the partner's copy of it.
+template <int S>
+__device__ __forceinline__ void reduce_half(const float *H, const float *L, int n, int lane, int o,
+                                            float (&KH)[S], float (&KL)[S])
 {
+    const bool up = (lane & o) != 0;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < o; ++i) {
-            const float sh = up ? H[i] : H[i + o], sl = up ? L[i] : L[i + o];
-            float kh = up ? H[i + o] : H[i], kl = up ? L[i + o] : L[i];
-            df_merge(kh, kl, __shfl_xor_sync(0xffffffffu, sh, o),
-                     __shfl_xor_sync(0xffffffffu, sl, o));
-            H[i] = kh;
-            L[i] = kl;
-        }
+    for (int i = 0; i < S; ++i) {
+        const float ah = H[i], al = L[i];
+        const float bh = S + i < n ? H[S + i] : 0.0f, bl = S + i < n ? L[S + i] : 0.0f;
+        float kh = up ? bh : ah, kl = up ? bl : al;
+        const float sh = up ? ah : bh, sl = up ? al : bl;
+        df_merge(kh, kl, __shfl_xor_sync(0xffffffffu, sh, o), __shfl_xor_sync(0xffffffffu, sl, o));
+        KH[i] = kh;
+        KL[i] = kl;
     }
-    h = H[0];
-    l_out = L[0];
+}
+
+// Sum over the warp of each of a lane's 18 double-float values (the two
+// moment sets): five halving steps, 18 -> 9 -> 5 -> 3 -> 2 -> 1 slots (an odd
+// count padded with a zero slot), 20 merges and 40 shuffles.  Lane l returns
+// the sum of value moment_lane_value(l), or of a padding slot (then < 0).
+// The order of the additions is fixed by the lane, not by the data.
+__device__ __forceinline__ void warp_reduce18(const float (&H)[2 * NMOM], const float (&L)[2 * NMOM],
+                                              int lane, float &h, float &l)
+{
+    static_assert(2 * NMOM == 18, "the halving steps are laid out for 18 values");
+    float h9[9], l9[9], h5[5], l5[5], h3[3], l3[3], h2[2], l2[2], h1[1], l1[1];
+    reduce_half<9>(H, L, 18, lane, 16, h9, l9);
+    reduce_half<5>(h9, l9, 9, lane, 8, h5, l5);
+    reduce_half<3>(h5, l5, 5, lane, 4, h3, l3);
+    reduce_half<2>(h3, l3, 3, lane, 2, h2, l2);
+    reduce_half<1>(h2, l2, 2, lane, 1, h1, l1);
+    h = h1[0];
+    l = l1[0];
+}
+
+// The value whose warp sum lane `lane` holds after warp_reduce18, or -1 for
+// a padding slot: follow the lane's bits down the halving steps.
+__device__ __forceinline__ int moment_lane_value(int lane)
+{
+    const int half[5] = {9, 5, 3, 2, 1};
+    int start = 0, n = 2 * NMOM;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        if (lane & (16 >> k)) {
+            start += half[k];
+            n -= half[k];
+        } else {
+            n = min(n, half[k]);
+        }
+        if (n <= 0)
+            return -1;
+    }
+    return start;
 }
 
 // ---------------------------------------------------------------------------
@@ -1263,6 +1296,7 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
     const int total = cb[n];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nwarps = REMOVE_THREADS >> 5;
+    const int my_v = moment_lane_value(lane);   // the moment value this lane sums
     for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
         const int f = frame_of(cb, n, wi);
         const int c0 = wi - cb[f];
@@ -1278,7 +1312,7 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
         const float4 p0 = st->p0;
         const int cur = round & 1;
         const long long npx = F.npx;
-        // per warp: lane v < 2 NMOM holds the double-float sum of moment value v
+        // per warp: lane l holds the double-float sum of moment value my_v (>= 0)
         // (gated inliers' values 0 .. NMOM-1, the other inliers' NMOM ..);
         // the gated / other counts are warp-uniform (ballots)
         float acc_s = 0.0f, acc_c = 0.0f;
@@ -1329,9 +1363,9 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
                                : make_float3(0.f, 0.f, 0.f);
                 }
                 // this lane's candidates, summed per value in registers
-                float vh[32], vl[32];
+                float vh[2 * NMOM], vl[2 * NMOM];
 #pragma unroll
-                for (int k = 0; k < 32; ++k) {
+                for (int k = 0; k < 2 * NMOM; ++k) {
                     vh[k] = 0.0f;
                     vl[k] = 0.0f;
                 }
@@ -1375,14 +1409,14 @@ __global__ void __launch_bounds__(REMOVE_THREADS) k_remove(RFrame *frames, int n
                                        __fsub_rn(p[u].y, p0.y), __fsub_rn(p[u].z, p0.z));
                 }
                 float th, tl;
-                warp_transpose_sum(vh, vl, lane, th, tl);
-                if (lane < 2 * NMOM)
+                warp_reduce18(vh, vl, lane, th, tl);
+                if (my_v >= 0)
                     df_merge(acc_s, acc_c, th, tl);
             }
         }
-        if (lane < 2 * NMOM) {
-            sh_s[wid][lane] = acc_s;
-            sh_c[wid][lane] = acc_c;
+        if (my_v >= 0) {
+            sh_s[wid][my_v] = acc_s;
+            sh_c[wid][my_v] = acc_c;
         }
         if (lane == 0) {
             sh_n[wid][0] = cnt_g;
