@@ -197,6 +197,33 @@ def test_normals_match_oracle(name, stencil):
     assert np.abs(P.astype(np.float64) - Po).max() <= 1e-5
 
 
+@pytest.mark.parametrize('stencil', [0, 1])
+@pytest.mark.parametrize('shape', [(480, 640), (37, 61), (5, 130), (64, 4)])
+def test_normals_vector_and_element_paths_are_bit_identical(shape, stencil):
+    """The normals kernel reads and writes 4 pixels with 16-byte accesses when
+    the width is a multiple of 4 and the arrays are aligned, with element
+    accesses otherwise: a depth image one float off 16-byte alignment takes
+    the element path, and both give the same bits; ragged widths (element
+    path) against the oracle."""
+    h, w = shape
+    rng = np.random.default_rng(h * 7 + w)
+    z = (1.0 + 0.3 * rng.random((h, w)) + 0.002 * np.arange(w)[None, :]).astype(np.float32)
+    z[rng.random((h, w)) < 0.03] = 0.0
+    K = (0.9 * w, 0.9 * w, w / 2.0, h / 2.0)
+    with Pipeline(params('c1', stencil=stencil), w, h) as pipe:
+        a = [t.cpu().numpy() for t in pipe.normals(to_dev(z), K)]
+        buf = torch.zeros(h * w + 1, dtype=torch.float32, device=DEV)
+        buf[1:] = to_dev(z).reshape(-1)
+        b = [t.cpu().numpy() for t in pipe.normals(buf[1:].view(h, w), K)]
+    for x, y in zip(a, b):
+        assert np.array_equal(x.view(np.uint8), y.view(np.uint8))
+    Po, No, Vo = oracle.normals(z.astype(np.float64), K, stencil)
+    assert np.array_equal(a[2], Vo)
+    ok = (a[2] & 2) > 0
+    if ok.any():
+        assert ang_deg(a[1][:, ok].astype(np.float64), No[:, ok]).max() <= NORMAL_TOL_DEG
+
+
 @functools.lru_cache(maxsize=None)
 def high_noise(mode):
     """Three times the noise of the 640x480 workload (sigma = 0.006 z^2)."""
