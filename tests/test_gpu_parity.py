@@ -496,6 +496,35 @@ def test_batch_and_graph_equal_single_frames():
                 assert torch.equal(labs[i], singles[i].labels)
 
 
+def test_odd_sized_batch_stage_by_stage_and_alone():
+    """Frames of odd width and height in one batch: the candidate order's last
+    strip is a single row and every frame ends in a ragged chunk.  Each frame
+    is checked stage by stage against the oracle (teacher forcing: every plane
+    round's winner, counts and labels exactly) and equals the frame alone."""
+    sizes = [(641, 479), (333, 211), (197, 123)]
+    frames = [synth.frame_straight(40 + i, w, h) for i, (w, h) in enumerate(sizes)]
+    p = Params(iters=20, hypotheses=512, max_planes=8, min_inliers=100, seed=5)
+    mw, mh = max(w for w, _ in sizes), max(h for _, h in sizes)
+    dev = [to_dev(f.encoded) for f in frames]
+    with Pipeline(p, mw, mh, len(frames)) as pipe:
+        labs = [torch.empty((f.h, f.w), dtype=torch.int16, device=DEV) for f in frames]
+        outs = [torch.empty((f.h, f.w), dtype=torch.float32, device=DEV) for f in frames]
+        res = pipe.process_batch([dict(depth=dev[i], K=f.cam.intrinsics, frame_idx=7 + i,
+                                       labels=labs[i], depth_out=outs[i])
+                                  for i, f in enumerate(frames)], use_graph=True)
+        geo = [[t.cpu().numpy() for t in pipe.frame_geometry(i, f.w, f.h)]
+               for i, f in enumerate(frames)]
+        singles = [pipe.process_frame(dev[i], f.cam.intrinsics, frame_idx=7 + i)
+                   for i, f in enumerate(frames)]
+    for i, f in enumerate(frames):
+        assert np.array_equal(res[i].planes, singles[i].planes)
+        assert torch.equal(labs[i], singles[i].labels)
+        job = chain_job(f, p, p.iters, 7 + i, outs[i].cpu().numpy(), *geo[i])
+        n = check_chain(oracle_chain(job), res[i], labs[i].cpu().numpy(), DIFF_TOL,
+                        '%dx%d' % (f.w, f.h))
+        assert n >= 2
+
+
 def test_resume_in_a_fresh_context_is_bit_identical():
     """The only state of a stream is (seed, frame index): a frame processed
     again in a new context, after other frames went through the old one,
