@@ -664,7 +664,8 @@ def run_served(torch, pm, args, c2_frames, c2_dev):
     out['capacity_mix'] = summarize(cap, srv.elapsed)
     srv.close()
     # 640x480 only: three lanes of 16 frames hold 1.1 GiB
-    srv = Server(p, budget_bytes=4 << 30, max_batch=16, n_lanes=3, max_w=640, max_h=480)
+    srv = Server(p, budget_bytes=4 << 30, max_batch=args.served_batch, n_lanes=3, max_w=640,
+                 max_h=480)
     h2 = [torch.from_numpy(f.encoded).pin_memory() for f in c2_frames]
     def c2_reqs():
         return [Request(i % 16, i, 0.0, h2[i % len(h2)], c2_frames[0].cam.intrinsics,
@@ -1061,6 +1062,8 @@ def main():
     ap.add_argument('--tiling', default='',
                     help='diffusion tiling T,tile_w,tile_h instead of autotuning (e.g. 8,80,48)')
     ap.add_argument('--served-seconds', type=float, default=60.0)
+    ap.add_argument('--served-batch', type=int, default=16,
+                    help='frames per batch of the 640x480 server (three lanes)')
     ap.add_argument('--case', default='',
                     choices=['', 'stream-u16', 'stream-f32', 'normals-f32', 'tiles-640x480x64',
                              'path-640x480x32'],
